@@ -1,0 +1,226 @@
+"""ctypes wrapper of the plain-C FP64 oracle (fempic_oracle.c).
+
+TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline).  Parity status
+of every function is stated in fempic_oracle.c's header and pinned by
+tests/test_oracle_*.py against closed forms, invariants and brute force.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fempic_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libfempic_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, FP64, -O2)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build_oracle())
+        lib.or_mesh_create.restype = C.c_void_p
+        lib.or_mesh_create.argtypes = [C.c_int64, _d, C.c_int64, _i32, _d, _d, C.POINTER(C.c_int32)]
+        lib.or_mesh_destroy.argtypes = [C.c_void_p]
+        lib.or_mesh_sizes.argtypes = [C.c_void_p, _i64]
+        lib.or_mesh_tables.argtypes = [C.c_void_p] + [_i32] * 6
+        lib.or_bary.argtypes = [C.c_void_p, C.c_int32, _d, _d]
+        lib.or_grad_bary.argtypes = [C.c_void_p, C.c_int32, _d]
+        lib.or_locate_brute_one.restype = C.c_int32
+        lib.or_locate_brute_one.argtypes = [C.c_void_p, _d]
+        lib.or_locate.argtypes = [C.c_void_p, C.c_int64, _d, _d, _d, _i32, _u8, C.c_int32]
+        lib.or_whitney1.argtypes = [C.c_void_p, C.c_int32, _d, _d]
+        lib.or_whitney2.argtypes = [C.c_void_p, C.c_int32, _d, _d]
+        lib.or_gather.argtypes = [C.c_void_p, C.c_int32, _d, _d, _d, _d, _d]
+        lib.or_push_step.restype = C.c_int
+        lib.or_push_step.argtypes = ([C.c_void_p, C.c_int64] + [_d] * 6 +
+                                     [_i32, _u8, C.c_void_p, C.c_int32, _i64, _d, _d, _d, _d, _d,
+                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                      C.c_int32, _d])
+        lib.or_nodal_charge.argtypes = [C.c_void_p, C.c_int64, _d, _d, _d, _i32, C.c_int32, _i64, _d,
+                                        _d, _d]
+        lib.or_edge_divergence.argtypes = [C.c_void_p, _d, _d]
+        lib.or_face_circulation.argtypes = [C.c_void_p, _d, _d]
+        lib.or_envelope_frame.argtypes = [C.c_int64, _d, C.c_double, C.c_double, _d]
+        lib.or_kinetic_energy.restype = C.c_double
+        lib.or_kinetic_energy.argtypes = [C.c_int64, _d, _d, _d, C.c_void_p, C.c_int32, _i64, _d, _d]
+        _lib = lib
+        return lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleMesh:
+    """Mesh tables derived by the oracle from raw nodes and tets."""
+
+    def __init__(self, nodes, tets, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+        lib = _load()
+        nodes = _f64(nodes)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        err = C.c_int32(0)
+        self._h = lib.or_mesh_create(nodes.shape[0], nodes.reshape(-1), tets.shape[0], tets.reshape(-1),
+                                     _f64(lo), _f64(hi), C.byref(err))
+        if not self._h:
+            raise ValueError(f"oracle mesh rejected (code {err.value})")
+        sz = np.zeros(4, dtype=np.int64)
+        lib.or_mesh_sizes(self._h, sz)
+        self.n_nodes, self.n_edges, self.n_faces, self.n_tets = (int(v) for v in sz)
+        self.lib = lib
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.or_mesh_destroy(h)
+            self._h = None
+
+    @property
+    def h(self):
+        return self._h
+
+    def tables(self):
+        nt, ne, nf = self.n_tets, self.n_edges, self.n_faces
+        tn = np.zeros((nt, 4), np.int32); en = np.zeros((ne, 2), np.int32)
+        fn = np.zeros((nf, 3), np.int32); te = np.zeros((nt, 6), np.int32)
+        tf = np.zeros((nt, 4), np.int32); nb = np.zeros((nt, 4), np.int32)
+        self.lib.or_mesh_tables(self._h, tn.reshape(-1), en.reshape(-1), fn.reshape(-1), te.reshape(-1),
+                                tf.reshape(-1), nb.reshape(-1))
+        return dict(tet_nodes=tn, edge_nodes=en, face_nodes=fn, tet_edges=te, tet_faces=tf, tet_nbr=nb)
+
+    def bary(self, t, r):
+        lam = np.zeros(4)
+        self.lib.or_bary(self._h, int(t), _f64(r), lam)
+        return lam
+
+    def grad_bary(self, t):
+        g = np.zeros(12)
+        self.lib.or_grad_bary(self._h, int(t), g)
+        return g.reshape(4, 3)
+
+    def whitney1(self, t, r):
+        W = np.zeros(18)
+        self.lib.or_whitney1(self._h, int(t), _f64(r), W)
+        return W.reshape(6, 3)
+
+    def whitney2(self, t, r):
+        W = np.zeros(12)
+        self.lib.or_whitney2(self._h, int(t), _f64(r), W)
+        return W.reshape(4, 3)
+
+    def gather(self, t, r, e_dof, b_dof):
+        """Complex envelope fields (E~, B~) at r in tet t."""
+        Et = np.zeros(6); Bt = np.zeros(6)
+        e = np.ascontiguousarray(e_dof, np.complex128).view(np.float64)
+        b = np.ascontiguousarray(b_dof, np.complex128).view(np.float64)
+        assert e.shape[0] == 2 * self.n_edges and b.shape[0] == 2 * self.n_faces
+        self.lib.or_gather(self._h, int(t), _f64(r), e, b, Et, Bt)
+        return Et[:3] + 1j * Et[3:], Bt[:3] + 1j * Bt[3:]
+
+    def locate(self, x, y, z, brute=False):
+        n = len(x)
+        tet = np.zeros(n, np.int32); st = np.zeros(n, np.uint8)
+        self.lib.or_locate(self._h, n, _f64(x), _f64(y), _f64(z), tet, st, 1 if brute else 0)
+        return tet, st
+
+    def locate_brute_one(self, r):
+        return int(self.lib.or_locate_brute_one(self._h, _f64(r)))
+
+    def nodal_charge(self, x, y, z, tet, species_begin, q, w):
+        rho = np.zeros(self.n_nodes)
+        self.lib.or_nodal_charge(self._h, len(x), _f64(x), _f64(y), _f64(z),
+                                 np.ascontiguousarray(tet, np.int32), len(q),
+                                 np.ascontiguousarray(species_begin, np.int64), _f64(q), _f64(w), rho)
+        return rho
+
+    def edge_divergence(self, G):
+        out = np.zeros(self.n_nodes)
+        self.lib.or_edge_divergence(self._h, _f64(G), out)
+        return out
+
+    def face_circulation(self, v):
+        out = np.zeros(self.n_faces)
+        self.lib.or_face_circulation(self._h, _f64(v), out)
+        return out
+
+
+class OracleState:
+    """Particle SoA held as FP64 numpy arrays for the oracle."""
+
+    def __init__(self, parts, tet=None):
+        self.x = _f64(parts.x).copy(); self.y = _f64(parts.y).copy(); self.z = _f64(parts.z).copy()
+        self.vx = _f64(parts.vx).copy(); self.vy = _f64(parts.vy).copy(); self.vz = _f64(parts.vz).copy()
+        n = self.x.shape[0]
+        self.tet = np.full(n, -1, np.int32) if tet is None else np.ascontiguousarray(tet, np.int32).copy()
+        self.status = np.zeros(n, np.uint8)
+        self.n_cross = np.zeros(n, np.int32)
+        self.species_begin = np.ascontiguousarray(parts.species_begin, np.int64)
+        self.q = _f64(parts.q); self.m = _f64(parts.m); self.w = _f64(parts.w)
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+    def copy(self):
+        c = object.__new__(OracleState)
+        for k, v in self.__dict__.items():
+            c.__dict__[k] = v.copy() if isinstance(v, np.ndarray) else v
+        return c
+
+
+def push_step(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, t, dt, dG,
+              max_crossings=4096, wall_mode=0):
+    """One oracle particle step; accumulates into dG (float64 [Ne])."""
+    e = _f64(np.ascontiguousarray(e_dof, np.complex128).view(np.float64))
+    b = _f64(np.ascontiguousarray(b_dof, np.complex128).view(np.float64))
+    assert dG.dtype == np.float64 and dG.flags.c_contiguous and dG.shape[0] == mesh.n_edges
+    mesh.lib.or_push_step(mesh.h, st.n, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.tet, st.status,
+                          st.n_cross.ctypes.data_as(C.c_void_p), len(st.q), st.species_begin, st.q,
+                          st.m, st.w, e, b, float(amp), float(omega0), float(t), float(dt),
+                          int(max_crossings), int(wall_mode), dG)
+
+
+def envelope_frame(G, omega0, t):
+    lib = _load()
+    G = _f64(G)
+    out = np.zeros(2 * G.shape[0])
+    lib.or_envelope_frame(G.shape[0], G, float(omega0), float(t), out)
+    return out.view(np.complex128)
+
+
+def kinetic_energy(st: OracleState):
+    lib = _load()
+    return float(lib.or_kinetic_energy(st.n, st.vx, st.vy, st.vz, st.tet.ctypes.data_as(C.c_void_p),
+                                       len(st.q), st.species_begin, st.m, st.w))
+
+
+def run(mesh: OracleMesh, wl, st: OracleState, steps: int, max_crossings=4096, step0: int = 0):
+    """Run `steps` oracle steps of workload `wl`; returns (state, G_cum)."""
+    G = np.zeros(mesh.n_edges)
+    for n in range(step0, step0 + steps):
+        t = n * wl.dt
+        push_step(mesh, st, wl.e_tilde, wl.b_tilde, wl.amp(t), wl.omega0, t, wl.dt, G,
+                  max_crossings=max_crossings, wall_mode=wl.wall_mode)
+    return st, G
