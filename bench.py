@@ -1,0 +1,412 @@
+"""Benchmark of the envelope-tracking FEMPIC particle step on GB300.
+
+Workload: unit cube as 48^3 hexes x 6 Kuhn tets (663,552 tets), 10M electrons
+at 5 eV (uniform, Maxwellian), TE101 cavity envelope at 10 kV/m, dt = 0.5 ns;
+synthetic inputs generated from fixed seeds.  One step = gather + carrier +
+push + track + deposit for every particle (fempic_push_step) and the deposit
+finalize (fempic_deposit).  The FP32-mixed form is the headline value; the
+FP64 form is measured side by side.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own 10M-particle replica (weak scaling)
+and the per-step edge deposit dG is summed over ranks.  Rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+track+deposit), FP32-mixed vs FP64, % HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "push_mixed_cube48_10M.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2208_12795_gb300", "csrc", f)
+                  for f in ("fempic_env.cu", "fempic_internal.h")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--particles", type=int, default=10_000_000)
+    ap.add_argument("--sort-every", type=int, default=20)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the side-by-side FP64 form")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-particles", type=int, default=1_000_000)
+    ap.add_argument("--cpu-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def bytes_alg_per_step(n_p, counts, form):
+    """Algorithmic bytes of one step: particle state read + written, mesh
+    tables (4 node, 4 neighbour, 6 edge, 4 face ids per tet), node
+    coordinates, complex DoFs and the dG write."""
+    s_p = 52 if form == "fp64" else 40
+    s_dof = 16 if form == "fp64" else 8
+    nn, ne, nf, nt = counts
+    return n_p * 2 * s_p + 72 * nt + 24 * nn + (s_dof + 8) * ne + s_dof * nf
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_p):
+    """DRAM bytes per launch of the mixed push kernel from the committed ncu
+    summary, scaled to n_p particles; None when absent or when the kernel
+    source changed since the capture."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    kv = {}
+    for line in open(PROFILE_SUMMARY):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    try:
+        if kv.get("kernel_source_sha") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_particle"]) * n_p
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_2208_12795_gb300 import build, inputs as I
+    from paper_2208_12795_gb300.env import FempicEnv, ParticleState
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    n_p = args.particles
+    wl = I.te101_cavity(48, n_p, 5.0, 1e4, 100, 2 + 100 * rank, name="cube48_10M_te101")
+    mesh = wl.mesh
+    stream = torch.cuda.current_stream()
+
+    def timed_form(form):
+        prec = 1 if form == "mixed" else 0
+        env = FempicEnv.from_mesh(mesh, precision=prec)
+        st = ParticleState.from_host(wl.particles, prec, track_crossings=False)
+        env.locate(st)
+        scratch = st.empty_like()
+        env.sort(st, scratch)                 # initial tet-sorted layout (untimed)
+        e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+        b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+        dG = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+        counts = (env.n_nodes, env.n_edges, env.n_faces, env.n_tets)
+
+        def step(n):
+            t = n * wl.dt
+            env.push_step(st, e, b, wl.amp(t), wl.omega0, t, wl.dt)
+            env.deposit(wl.omega0, t + wl.dt, dG_out=dG if world > 1 else None)
+            if world > 1:
+                dist.all_reduce(dG)
+            if args.sort_every > 0 and (n + 1) % args.sort_every == 0:
+                env.sort(st, scratch)
+
+        for n in range(args.warmup):
+            step(n)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.2)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        env.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for n in range(args.warmup, args.warmup + args.steps):
+            step(n)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        env.profile(False)
+        if world > 1:
+            dist.barrier()
+        ck = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        prof = env.profile_read()
+        stats = env.stats()
+        res = dict(ms=ms, prof=prof, stats=stats, counts=counts, clocks=ck, env=env, st=st, e=e, b=b,
+                   scratch=scratch)
+        return res
+
+    out = {}
+    mixed = timed_form("mixed")
+    out["mixed"] = mixed
+    if not args.no_fp64:
+        f64 = timed_form("fp64")
+        out["fp64"] = f64
+        f64["env"].close()
+
+    # e2e through the public API with host buffers: per step, the envelope
+    # DoFs arrive from pinned host memory (the field solver's output) and the
+    # step's edge deposit dG goes back to pinned host memory.
+    env, st = mixed["env"], mixed["st"]
+    e_host = torch.from_numpy(wl.e_tilde).to(torch.complex64).pin_memory()
+    b_host = torch.from_numpy(wl.b_tilde).to(torch.complex64).pin_memory()
+    e_dev, b_dev = torch.empty_like(e_host, device="cuda"), torch.empty_like(b_host, device="cuda")
+    dG_dev = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+    dG_host = torch.zeros(env.n_edges, dtype=torch.float64).pin_memory()
+    h2d = e_host.numel() * 8 + b_host.numel() * 8
+    d2h = dG_host.numel() * 8
+    k0 = args.warmup + args.steps
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for n in range(k0, k0 + args.steps):
+        t = n * wl.dt
+        e_dev.copy_(e_host, non_blocking=True)
+        b_dev.copy_(b_host, non_blocking=True)
+        env.push_step(st, e_dev, b_dev, wl.amp(t), wl.omega0, t, wl.dt)
+        env.deposit(wl.omega0, t + wl.dt, dG_out=dG_dev)
+        if world > 1:
+            dist.all_reduce(dG_dev)
+        dG_host.copy_(dG_dev, non_blocking=True)
+        if args.sort_every > 0 and (n + 1) % args.sort_every == 0:
+            env.sort(st, mixed["scratch"])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    mixed["e2e_s"] = e2e_s
+    mixed["h2d"], mixed["d2h"] = h2d, d2h
+    env.close()
+
+    if rank == 0:
+        cpu = None if (args.no_cpu or world > 1) else cpu_baseline(wl, args.cpu_particles, args.cpu_steps)
+        report(args, world, n_p, out, cpu)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, n_sample, steps):
+    """The FP64 oracle as it stands, single thread, on the first n_sample
+    particles of the same workload."""
+    from oracle.oracle import OracleMesh, OracleState, push_step as oracle_push
+    om = OracleMesh(wl.mesh.nodes, wl.mesh.tets)
+    P = wl.particles.subset(n_sample)
+    tet, _ = om.locate(P.x, P.y, P.z)
+    st = OracleState(P, tet)
+    G = np.zeros(om.n_edges)
+    t0 = time.perf_counter()
+    for n in range(steps):
+        oracle_push(om, st, wl.e_tilde, wl.b_tilde, wl.amp(n * wl.dt), wl.omega0, n * wl.dt, wl.dt, G)
+    el = time.perf_counter() - t0
+    return {"value": n_sample * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_sample} of the 10M particles, {steps} steps, FP64 C oracle, 1 thread "
+                      f"({el:.1f} s)"}
+
+
+def report(args, world, n_p, out, cpu):
+    peak, peak_src = measured_peaks()
+    m = out["mixed"]
+    K = args.steps
+    total = n_p * world * K
+    value = total / (m["ms"] / 1e3)
+    push = m["prof"]["push"]
+    t_push = push["ms"] / max(push["launches"], 1) / 1e3
+    b_alg = bytes_alg_per_step(n_p, m["counts"], "mixed")
+    achieved = b_alg / t_push / 1e9
+    launches = sum(v["launches"] for v in m["prof"].values())
+    traffic = profiled_traffic(n_p)
+    rec = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "particle-steps/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": m["ms"] / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64 mixed (FP32 gather/carrier/Boris; FP64 positions; int64 exact deposit)",
+        "data": "synthetic (seeded): Kuhn cube mesh, TE101 envelope DoFs, uniform Maxwellian electrons",
+        "config": {
+            "workload": "cube48_10M_te101: 48^3x6 Kuhn cube (663,552 tets), 10M electrons at 5 eV, "
+                        "TE101 10 kV/m, dt 0.5 ns",
+            "form": "mixed",
+            "particles_per_gpu": n_p,
+            "n_tets": m["counts"][3],
+            "sort_every": args.sort_every,
+            "l2": "inputs larger than L2 (particle SoA 400 MB per GPU per step)",
+            "parallelism": f"particle replicas x{world}, dG summed over ranks" if world > 1 else "1 GPU",
+        },
+        "roofline": {
+            "kernel": "k_push_mixed",
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_source": f"{peak_src} copy bandwidth",
+            "algorithmic_bytes_per_launch": b_alg,
+            "avg_launch_ms": t_push * 1e3,
+        },
+        "e2e": {"value": total / m["e2e_s"], "unit": "particle-steps/s",
+                "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]},
+        "gpu_launches": launches,
+        "kernel_ms": {k: v["ms"] for k, v in m["prof"].items() if v["launches"]},
+        "crossings_per_particle_step": m["stats"]["crossings"] / max(1, n_p * (K + args.warmup)),
+        "clocks": m["clocks"],
+    }
+    if "fp64" in out:
+        f = out["fp64"]
+        fp = f["prof"]["push"]
+        tf = fp["ms"] / max(fp["launches"], 1) / 1e3
+        bf = bytes_alg_per_step(n_p, f["counts"], "fp64")
+        rec["fp64_form"] = {"value": total / (f["ms"] / 1e3), "ms_per_step": f["ms"] / K,
+                            "push_avg_launch_ms": tf * 1e3, "hbm_frac": bf / tf / 1e9 / peak,
+                            "clocks": f["clocks"]}
+    if cpu is not None:
+        rec["cpu_baseline"] = cpu
+    print(json.dumps(rec), flush=True)
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle timed as it stands on the host cores: each step is one
+    oracle step over a bounded sample of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.oracle import OracleMesh, OracleState, push_step as oracle_push
+    from paper_2208_12795_gb300 import inputs as I
+    n_s = 20_000
+    wl = I.te101_cavity(48, n_s, 5.0, 1e4, 100, 2, name="cube48_10M_te101")
+    om = OracleMesh(wl.mesh.nodes, wl.mesh.tets)
+    P = wl.particles
+    tet, _ = om.locate(P.x, P.y, P.z)
+    st = OracleState(P, tet)
+    G = np.zeros(om.n_edges)
+    for n in range(args.warmup):
+        oracle_push(om, st, wl.e_tilde, wl.b_tilde, wl.amp(n * wl.dt), wl.omega0, n * wl.dt, wl.dt, G)
+    t0 = time.perf_counter()
+    for n in range(args.warmup, args.warmup + args.steps):
+        oracle_push(om, st, wl.e_tilde, wl.b_tilde, wl.amp(n * wl.dt), wl.omega0, n * wl.dt, wl.dt, G)
+    el = time.perf_counter() - t0
+    value = n_s * args.steps / el
+    sample = f"{n_s} particles of the same workload per step, FP64 C oracle, 1 thread"
+    rec = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded)",
+           "config": {"workload": "cube48_10M_te101: 48^3x6 Kuhn cube (663,552 tets), 5 eV electrons, "
+                                  "TE101 10 kV/m, dt 0.5 ns", "form": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,218 @@
+/*
+ * fempic_env.h -- C ABI of the GB300 (sm_103a) particle hot path of the
+ * envelope-tracking EM-FEMPIC method (Ramachandran et al., "An Envelope
+ * Tracking Approach for Particle in Cell Simulations").
+ *
+ * One particle step, per particle, in order:
+ *   (a) locate   carry the particle's tet; initial location = smallest-id tet
+ *                whose four barycentrics are all >= 0;
+ *   (b) gather   E~(r) = sum_e e~_e W1_e(r), B~(r) = sum_f b~_f W2_f(r)
+ *                (Sec. III-A, Whitney expansion of the envelope fields);
+ *   (c) carrier  E = Re{a(t) e^{j omega0 t} E~}, B = Re{a(t) e^{j omega0 t} B~}
+ *                (Sec. III, envelope ansatz; Sec. III-D, Lorentz force with the
+ *                fast carrier restored analytically);
+ *   (d) push     Boris leapfrog, fields at (r^n, t_n), non-relativistic
+ *                (Sec. III-D);
+ *   (e) track    split r^n -> r^{n+1} at face crossings; reflecting (or
+ *                absorbing) axis-aligned walls;
+ *   (f) deposit  exact W1-tested path integral per in-tet segment,
+ *                g_ij = q w (l_i(a) l_j(b) - l_j(a) l_i(b)), accumulated into
+ *                the edge array dG (Sec. II eq. g_def; Sec. III-D eq.
+ *                G_integral split into fine steps), and mapped into the
+ *                envelope frame e^{-j omega0 t} G for the field solve
+ *                (Sec. III-A, forcing term of eq. maxwell_semi).
+ *
+ * Conventions shared by every entry point
+ *  - Mesh numbering: tet nodes are sorted by global id; edges [Ne][2] and
+ *    faces [Nf][3] are numbered lexicographically by their sorted node tuples.
+ *    Local edge e of a tet joins sorted local nodes (0,1),(0,2),(0,3),(1,2),
+ *    (1,3),(2,3); local face k is opposite local node k.  Edge orientation is
+ *    low -> high node id; face orientation (x_j - x_i) x (x_k - x_i), i<j<k.
+ *  - Device pointers are CUDA global-memory pointers on the current device;
+ *    host pointers are plain CPU memory.  Each field says which.
+ *  - All calls taking a stream are asynchronous and stream-ordered on that
+ *    cudaStream_t (passed as void*; NULL = legacy default stream) unless the
+ *    comment says the call synchronizes.
+ *  - Return value: FEMPIC_OK (0) or a negative FEMPIC_E* code; the message of
+ *    the last failure on the calling thread is fempic_last_error().  No entry
+ *    point traps or asserts on the device: bad particles get a status code.
+ */
+#ifndef FEMPIC_ENV_H
+#define FEMPIC_ENV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define FEMPIC_OK 0
+#define FEMPIC_EINVAL (-1)   /* bad argument (NULL, size, dtype/precision mismatch) */
+#define FEMPIC_ECUDA (-2)    /* a CUDA runtime call failed */
+#define FEMPIC_EMESH (-3)    /* degenerate (zero-volume) or non-conforming mesh */
+#define FEMPIC_ENOMEM (-4)   /* host or device allocation failed */
+
+/* ---- precision forms ---- */
+#define FEMPIC_FP64 0   /* every step in FP64; velocities f64, DoFs complex128 */
+#define FEMPIC_MIXED 1  /* gather, carrier product and push in FP32; velocities f32,
+                           DoFs complex64; FP64 positions, exit parameter and
+                           crossing point; deposit exactly charge conserving */
+
+/* ---- per-particle status (uint8) ---- */
+#define FEMPIC_P_OK 0
+#define FEMPIC_P_CAP 1        /* more than max_crossings face crossings in one step */
+#define FEMPIC_P_ABSORBED 2   /* left through a wall in absorb mode (or a non axis-aligned boundary) */
+#define FEMPIC_P_NONFINITE 3  /* the push produced a non-finite velocity or position */
+#define FEMPIC_P_LOST 4       /* no containing tet, or tet id out of range */
+/* A frozen particle keeps its last tet T as tet = -2 - T; tet = -1 = no tet.
+ * Particles with tet < 0 are skipped by every step. */
+
+/* ---- wall modes ---- */
+#define FEMPIC_WALL_REFLECT 0
+#define FEMPIC_WALL_ABSORB 1
+
+typedef struct fempic_env fempic_env;   /* opaque; owns derived mesh tables,
+                                           accumulators and scratch on the device */
+
+typedef struct {
+  int64_t n_nodes;
+  int64_t n_tets;
+  const double* nodes_xyz;   /* host [n_nodes][3], copied at create */
+  const int32_t* tet_nodes;  /* host [n_tets][4], any node order, copied at create */
+  double bbox_lo[3];         /* axis-aligned walls: boundary faces lying in one of */
+  double bbox_hi[3];         /* these six planes reflect (or absorb) particles     */
+} fempic_mesh_desc;
+
+typedef struct {
+  int32_t precision;         /* FEMPIC_FP64 or FEMPIC_MIXED */
+  int32_t max_crossings;     /* face crossings allowed per particle per step, 0 .. 2^20 */
+  int32_t wall_mode;         /* FEMPIC_WALL_REFLECT or FEMPIC_WALL_ABSORB */
+  int32_t reserved;          /* must be 0 */
+} fempic_options;
+
+typedef struct {
+  int64_t n;                 /* number of particles */
+  double* x;                 /* device f64 [n] positions (m) */
+  double* y;
+  double* z;
+  void* vx;                  /* device velocities (m/s): f64 [n] (FP64 form) or f32 [n] (mixed) */
+  void* vy;
+  void* vz;
+  int32_t* tet;              /* device i32 [n] current tet (see status convention) */
+  uint8_t* status;           /* device u8 [n] FEMPIC_P_* */
+  int32_t* n_cross;          /* device i32 [n] cumulative crossings, or NULL */
+  int32_t n_species;         /* 1 .. 8 contiguous species ranges */
+  const int64_t* species_begin; /* host [n_species+1], species s = [begin[s], begin[s+1]) */
+  const double* q;           /* host [n_species] charge per physical particle (C) */
+  const double* m;           /* host [n_species] mass (kg) */
+  const double* w;           /* host [n_species] macro-particle weight */
+} fempic_particles;
+
+typedef struct {
+  const void* e_tilde;       /* device complex [Ne] edge DoFs (interleaved re,im):
+                                complex128 (FP64 form) or complex64 (mixed) */
+  const void* b_tilde;       /* device complex [Nf] face DoFs, same dtype */
+  double amp;                /* host scalar: slow envelope amplitude a(t) at this step */
+} fempic_envelope;
+
+/* Derive the mesh tables (sorted tet nodes, edges, faces, neighbours, wall
+ * codes, FP64 barycentric geometry, point-location grid) on the host and
+ * upload them to the current device; allocate the edge accumulators dG and
+ * G_cum (zeroed).  Mesh: Sec. III-A / App. A sets N, E, F, T.
+ * Errors: EINVAL (NULL, sizes, options), EMESH (zero-volume tet, a face in
+ * more than two tets), ENOMEM, ECUDA.  Synchronizes the device. */
+int fempic_env_create(const fempic_mesh_desc* mesh, const fempic_options* opts, fempic_env** out);
+
+/* Sizes and tables of the derived numbering (host outputs; any may be NULL).
+ * counts4 = {n_nodes, n_edges, n_faces, n_tets}.  tet_nbr: neighbour tet
+ * across local face k, or a wall code -1-(2*axis+side) (side 0 = lo, 1 = hi),
+ * or -7 for a boundary face off the bbox planes. */
+int fempic_env_query(const fempic_env* env, int64_t* counts4, int32_t* tet_nodes /*[Nt][4]*/,
+                     int32_t* edge_nodes /*[Ne][2]*/, int32_t* face_nodes /*[Nf][3]*/,
+                     int32_t* tet_edges /*[Nt][6]*/, int32_t* tet_faces /*[Nt][4]*/,
+                     int32_t* tet_nbr /*[Nt][4]*/);
+
+/* (a) Initial location: tet[p] = smallest-id tet with all barycentrics >= 0
+ * (FP64, fixed operation order), else tet = -1 and status = FEMPIC_P_LOST;
+ * status = FEMPIC_P_OK for located particles.  Reads x, y, z; writes tet and
+ * status.  Errors: EINVAL, ECUDA. */
+int fempic_locate(fempic_env* env, const fempic_particles* p, void* stream);
+
+/* (b)-(f) One fused particle step from t to t + dt for every particle with
+ * tet >= 0: gather, carrier restore c = amp e^{j omega0 t} (phase and c in
+ * FP64 on the host), Boris push, face tracking, and deposit of the path
+ * integral into the env's dG accumulator (added to, not cleared).  Updates
+ * x, y, z, v, tet, status and n_cross in place.  Velocities are v^{n-1/2} on
+ * entry and v^{n+1/2} on exit.  Errors: EINVAL (precision/dtype mismatch,
+ * species ranges), ECUDA. */
+int fempic_push_step(fempic_env* env, const fempic_particles* p, const fempic_envelope* envl,
+                     double omega0, double t, double dt, void* stream);
+
+/* Finalize the deposit of one step (Sec. III-D, eq. G_integral; forcing term
+ * e^{-j omega0 t} G of Sec. III-A): G_cum += dG; then, when non-NULL,
+ *   dG_out    <- dG                               (device f64 [Ne])
+ *   G_cum_out <- G_cum                            (device f64 [Ne])
+ *   G_env_out <- e^{-j omega0 t_next} G_cum       (device complex128 [Ne])
+ * and dG is zeroed.  Errors: EINVAL, ECUDA. */
+int fempic_deposit(fempic_env* env, double omega0, double t_next, double* dG_out, double* G_cum_out,
+                   void* G_env_out, void* stream);
+
+/* Zero dG and G_cum (start of a run).  Errors: ECUDA. */
+int fempic_reset_deposit(fempic_env* env, void* stream);
+
+/* Whitney-0 nodal charge rho_n = sum_p q w lambda_n(r_p) (Sec. III-B,
+ * discrete Gauss law: charge on nodes) over particles with a known tet,
+ * written to rho (device f64 [Nn], overwritten).  Used with the edge
+ * divergence to check charge conservation D^T G_cum = rho^n - rho^0.
+ * Errors: EINVAL, ECUDA. */
+int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, double* rho, void* stream);
+
+/* Host-side counters accumulated by push_step since create / the last call:
+ * out3 = {face crossings, particles frozen (any non-OK status), steps}.
+ * Synchronizes the stream.  Errors: EINVAL, ECUDA. */
+int fempic_stats(fempic_env* env, int64_t* out3, void* stream);
+
+/* Keep the particle SoA ordered for coalesced, tet-local access (the
+ * particle state of Sec. III-D in a GPU layout; no counterpart in the
+ * paper's method): out = in permuted so that each species range stays in
+ * place and, inside it, particles are ordered by tet id, with particles of
+ * tet < 0 (frozen or unlocated) last.  Order inside one tet is unspecified.
+ * in and out are two caller-owned particle sets with the same n, velocity
+ * dtype and species table, and must not overlap; n_cross may be NULL in both
+ * (else in both).  The counting scratch (one int32 counter per (species,
+ * tet) key) is owned by the env and grown on demand.  Stream-ordered.
+ * Errors: EINVAL (mismatch), ENOMEM, ECUDA. */
+int fempic_sort(fempic_env* env, const fempic_particles* in, const fempic_particles* out, void* stream);
+
+/* Kernel ids of the per-kernel timing below. */
+#define FEMPIC_K_LOCATE 0
+#define FEMPIC_K_FIELD 1      /* per-tet carrier restore + affine field coefficients */
+#define FEMPIC_K_PUSH 2       /* fused gather/push/track/deposit */
+#define FEMPIC_K_FINALIZE 3   /* deposit finalize */
+#define FEMPIC_K_CHARGE 4     /* nodal charge */
+#define FEMPIC_K_SORT 5       /* particle sort by tet */
+#define FEMPIC_K_COUNT 8
+
+/* Measurement support (no counterpart in the paper): while enabled, every
+ * kernel the env launches is bracketed by two CUDA events recorded on its
+ * launch stream.  enable != 0 clears earlier records and starts recording;
+ * 0 stops.  At most 65536 launches are recorded per enable.  Errors: EINVAL. */
+int fempic_profile_enable(fempic_env* env, int32_t enable);
+
+/* Per kernel id: summed event durations (ms_out[FEMPIC_K_COUNT]) and launch
+ * counts (launches_out[FEMPIC_K_COUNT]) since the last enable; synchronizes
+ * on the recorded events.  Errors: EINVAL, ECUDA. */
+int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* launches_out);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* fempic_last_error(void);
+
+/* Free everything the env owns.  Safe on NULL. */
+void fempic_env_destroy(fempic_env* env);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEMPIC_ENV_H */

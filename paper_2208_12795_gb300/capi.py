@@ -1,0 +1,161 @@
+"""ctypes binding of the C ABI in include/fempic_env.h (argument marshalling only).
+
+Function names match the C entry points.  The library is loaded from the
+package directory; when it is missing the import of any entry point raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfempic_env.so")
+
+FEMPIC_OK = 0
+FEMPIC_EINVAL = -1
+FEMPIC_ECUDA = -2
+FEMPIC_EMESH = -3
+FEMPIC_ENOMEM = -4
+FEMPIC_FP64 = 0
+FEMPIC_MIXED = 1
+FEMPIC_P_OK, FEMPIC_P_CAP, FEMPIC_P_ABSORBED, FEMPIC_P_NONFINITE, FEMPIC_P_LOST = range(5)
+FEMPIC_WALL_REFLECT = 0
+FEMPIC_WALL_ABSORB = 1
+
+# Every function declared in include/fempic_env.h.
+EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step",
+           "fempic_deposit", "fempic_reset_deposit", "fempic_nodal_charge", "fempic_stats",
+           "fempic_sort", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
+FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT = range(6)
+FEMPIC_K_COUNT = 8
+
+
+class fempic_mesh_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("nodes_xyz", C.c_void_p),
+                ("tet_nodes", C.c_void_p), ("bbox_lo", C.c_double * 3), ("bbox_hi", C.c_double * 3)]
+
+
+class fempic_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_crossings", C.c_int32), ("wall_mode", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class fempic_particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("tet", C.c_void_p),
+                ("status", C.c_void_p), ("n_cross", C.c_void_p), ("n_species", C.c_int32),
+                ("species_begin", C.c_void_p), ("q", C.c_void_p), ("m", C.c_void_p), ("w", C.c_void_p)]
+
+
+class fempic_envelope(C.Structure):
+    _fields_ = [("e_tilde", C.c_void_p), ("b_tilde", C.c_void_p), ("amp", C.c_double)]
+
+
+class FempicError(RuntimeError):
+    pass
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FempicError(f"{path} is missing: build it with paper_2208_12795_gb300.build.build()")
+        lib = C.CDLL(path)
+        P = C.POINTER
+        lib.fempic_env_create.argtypes = [P(fempic_mesh_desc), P(fempic_options), P(C.c_void_p)]
+        lib.fempic_env_query.argtypes = [C.c_void_p] + [C.c_void_p] * 7
+        lib.fempic_locate.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p]
+        lib.fempic_push_step.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_envelope), C.c_double,
+                                         C.c_double, C.c_double, C.c_void_p]
+        lib.fempic_deposit.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
+        lib.fempic_reset_deposit.argtypes = [C.c_void_p, C.c_void_p]
+        lib.fempic_nodal_charge.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p, C.c_void_p]
+        lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_sort.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
+        lib.fempic_profile_enable.argtypes = [C.c_void_p, C.c_int32]
+        lib.fempic_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_last_error.restype = C.c_char_p
+        lib.fempic_last_error.argtypes = []
+        lib.fempic_env_destroy.argtypes = [C.c_void_p]
+        lib.fempic_env_destroy.restype = None
+        for name in EXPORTS:
+            if name not in ("fempic_last_error", "fempic_env_destroy"):
+                getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def check(rc: int, what: str):
+    if rc != FEMPIC_OK:
+        msg = load().fempic_last_error().decode(errors="replace")
+        raise FempicError(f"{what} failed ({rc}): {msg}")
+
+
+# Same-named thin wrappers ------------------------------------------------
+def fempic_env_create(mesh: fempic_mesh_desc, opts: fempic_options) -> int:
+    h = C.c_void_p()
+    check(load().fempic_env_create(C.byref(mesh), C.byref(opts), C.byref(h)), "fempic_env_create")
+    return h.value
+
+
+def fempic_env_query(env, counts4, tet_nodes=0, edge_nodes=0, face_nodes=0, tet_edges=0, tet_faces=0,
+                     tet_nbr=0):
+    check(load().fempic_env_query(env, counts4, tet_nodes, edge_nodes, face_nodes, tet_edges, tet_faces,
+                                  tet_nbr), "fempic_env_query")
+
+
+def fempic_locate(env, parts: fempic_particles, stream=0):
+    check(load().fempic_locate(env, C.byref(parts), stream), "fempic_locate")
+
+
+def fempic_push_step(env, parts: fempic_particles, envl: fempic_envelope, omega0, t, dt, stream=0):
+    check(load().fempic_push_step(env, C.byref(parts), C.byref(envl), float(omega0), float(t), float(dt),
+                                  stream), "fempic_push_step")
+
+
+def fempic_deposit(env, omega0, t_next, dG_out=0, G_cum_out=0, G_env_out=0, stream=0):
+    check(load().fempic_deposit(env, float(omega0), float(t_next), dG_out, G_cum_out, G_env_out, stream),
+          "fempic_deposit")
+
+
+def fempic_reset_deposit(env, stream=0):
+    check(load().fempic_reset_deposit(env, stream), "fempic_reset_deposit")
+
+
+def fempic_nodal_charge(env, parts: fempic_particles, rho, stream=0):
+    check(load().fempic_nodal_charge(env, C.byref(parts), rho, stream), "fempic_nodal_charge")
+
+
+def fempic_stats(env, out3, stream=0):
+    check(load().fempic_stats(env, out3, stream), "fempic_stats")
+
+
+def fempic_sort(env, parts_in: fempic_particles, parts_out: fempic_particles, stream=0):
+    check(load().fempic_sort(env, C.byref(parts_in), C.byref(parts_out), stream), "fempic_sort")
+
+
+def fempic_profile_enable(env, enable: bool):
+    check(load().fempic_profile_enable(env, 1 if enable else 0), "fempic_profile_enable")
+
+
+def fempic_profile_read(env, ms_out, launches_out):
+    check(load().fempic_profile_read(env, ms_out, launches_out), "fempic_profile_read")
+
+
+def fempic_last_error() -> str:
+    return load().fempic_last_error().decode(errors="replace")
+
+
+def fempic_env_destroy(env):
+    if env:
+        load().fempic_env_destroy(env)

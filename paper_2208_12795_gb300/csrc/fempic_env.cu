@@ -1,0 +1,1431 @@
+// fempic_env.cu -- sm_103a kernels and the C ABI of the envelope-tracking
+// FEMPIC particle step (include/fempic_env.h).
+//
+// Data layout on the device (per tet, indexed by tet id):
+//   geom64  double[12]  x0, grad l1, grad l2, grad l3        (96 B, FP64 form + location)
+//   x0v     double2 x2  x0 and padding                       (32 B, mixed form)
+//   g32     float[12]   grad l1..l3 in FP32, padded          (48 B, mixed form)
+//   tn      int4        sorted global node ids
+//   nb      int4        neighbour across local face k, or wall code
+//   te      int4 x 2    6 global edge ids, padded to 8
+//   tf      int4        4 global face ids
+//   field   per step: the affine envelope field of the tet after the carrier
+//           is restored, E(r) = E0 + (r - x0) x W, B(r) = B0 + beta (r - x0):
+//           double[10] (FP64 form) or float[12] (mixed form).
+// Whitney-1 fields are affine with an antisymmetric gradient and Whitney-2
+// fields are affine with an isotropic gradient, so these 10 numbers carry the
+// whole gather of Sec. III-A for every particle in the tet; they are built
+// once per step from the 10 complex DoFs of the tet by k_field_*.
+//
+// Particle SoA (caller owned): x, y, z f64; vx, vy, vz f64 (FP64 form) or f32
+// (mixed); tet i32; status u8; n_cross i32 (optional).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "fempic_internal.h"
+
+using namespace fempic;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define FEMPIC_CUDA(call)                                                                      \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(FEMPIC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
+  } while (0)
+
+constexpr int kThreads = 256;
+constexpr int kQBits = 24;                       // fixed-point barycentrics of the mixed form
+constexpr float kQScale = 16777216.0f;           // 2^24
+constexpr int32_t kQOne = 1 << kQBits;
+constexpr float kQClamp = 32.0f;
+constexpr int32_t kMaxCrossingsLimit = 1 << 20;
+
+// Local topology of a tet with sorted nodes, usable in device code: edge e
+// joins (le0(e), le1(e)) in the order 01,02,03,12,13,23; face f is opposite
+// node f and its i-th node (ascending) is lf(f, i).
+__host__ __device__ constexpr int le0(int e) { return e < 3 ? 0 : (e < 5 ? 1 : 2); }
+__host__ __device__ constexpr int le1(int e) { return e < 3 ? e + 1 : (e == 3 ? 2 : 3); }
+__host__ __device__ constexpr int lf(int f, int i) { return i < f ? i : i + 1; }
+
+struct Species {
+  int32_t ns;
+  int64_t begin[kMaxSpecies + 1];
+  double kq[kMaxSpecies];   // (q/m) dt / 2
+  double qw[kMaxSpecies];   // q w
+};
+
+struct PushArgs {
+  int64_t n;
+  double* x;
+  double* y;
+  double* z;
+  void* vx;
+  void* vy;
+  void* vz;
+  int32_t* tet;
+  uint8_t* status;
+  int32_t* ncross;
+  Species sp;
+  double dt;
+  int32_t max_cross;
+  int32_t wall_mode;
+  double lo[3], hi[3];
+  int64_t nt, ne;
+  const double* geom64;
+  const double2* x0v;
+  const float4* g32;
+  const int4* tn;
+  const int4* nb;
+  const int4* te;
+  const void* field;
+  double* dG;                   // FP64 form accumulator [Ne]
+  unsigned long long* dGq;      // mixed form accumulators [ns][Ne], units of 2^-48 (q w)
+  unsigned long long* stats;    // [0] crossings, [1] frozen
+};
+
+__device__ __forceinline__ int species_of(const Species& sp, int64_t p) {
+  int s = 0;
+#pragma unroll 1
+  while (s + 1 < sp.ns && p >= sp.begin[s + 1]) s++;
+  return s;
+}
+
+// ---------------------------------------------------------------- location
+// Barycentrics with the fixed FP64 operation order (no contraction), so that
+// point location reproduces exactly across implementations.
+__device__ __forceinline__ void bary_exact(const double* __restrict__ g, double rx, double ry, double rz,
+                                           double lam[4]) {
+  const double dx = __dsub_rn(rx, g[0]), dy = __dsub_rn(ry, g[1]), dz = __dsub_rn(rz, g[2]);
+#pragma unroll
+  for (int k = 1; k < 4; k++) {
+    const double* gk = g + 3 * k;
+    lam[k] = __dadd_rn(__dadd_rn(__dmul_rn(gk[0], dx), __dmul_rn(gk[1], dy)), __dmul_rn(gk[2], dz));
+  }
+  lam[0] = __dsub_rn(__dsub_rn(__dsub_rn(1.0, lam[1]), lam[2]), lam[3]);
+}
+
+__device__ __forceinline__ int grid_cell_dev(double x, double lo, double ginv, int gd) {
+  double f = floor(__dmul_rn(__dsub_rn(x, lo), ginv));
+  if (!(f >= 0.0)) return 0;
+  if (f > (double)(gd - 1)) return gd - 1;
+  return (int)f;
+}
+
+struct LocateArgs {
+  int64_t n;
+  const double* x;
+  const double* y;
+  const double* z;
+  int32_t* tet;
+  uint8_t* status;
+  const double* geom64;
+  const int64_t* gstart;
+  const int32_t* gtet;
+  int gd[3];
+  double ginv[3];
+  double lo[3];
+};
+
+__global__ void __launch_bounds__(kThreads) k_locate(LocateArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.n) return;
+  const double rx = A.x[p], ry = A.y[p], rz = A.z[p];
+  int32_t found = -1;
+  if (isfinite(rx) && isfinite(ry) && isfinite(rz)) {
+    const int ci = grid_cell_dev(rx, A.lo[0], A.ginv[0], A.gd[0]);
+    const int cj = grid_cell_dev(ry, A.lo[1], A.ginv[1], A.gd[1]);
+    const int ck = grid_cell_dev(rz, A.lo[2], A.ginv[2], A.gd[2]);
+    const int64_t c = ci + (int64_t)A.gd[0] * (cj + (int64_t)A.gd[1] * ck);
+    const int64_t e = A.gstart[c + 1];
+    for (int64_t i = A.gstart[c]; i < e; i++) {
+      const int32_t t = A.gtet[i];
+      double lam[4];
+      bary_exact(A.geom64 + 12 * (int64_t)t, rx, ry, rz, lam);
+      if (lam[0] >= 0.0 && lam[1] >= 0.0 && lam[2] >= 0.0 && lam[3] >= 0.0) {
+        found = t;
+        break;
+      }
+    }
+  }
+  A.tet[p] = found;
+  A.status[p] = found < 0 ? FEMPIC_P_LOST : FEMPIC_P_OK;
+}
+
+// ------------------------------------------------------- field pre-pass
+// Per tet: restore the carrier on the 10 DoFs (Re{c e~}), then express the
+// Whitney expansion as an affine field about x0:
+//   E(r) = E0 + d x W,  E0 = sum_j eps_0j g_j,  W = sum_{i<j} eps_ij (g_j x g_i)
+//   B(r) = B0 + beta d, B0 = 2 (b1 g2 x g3 + b2 g1 x g3 + b3 g1 x g2),
+//                       beta = 2 sum_f b_f det[g_f0, g_f1, g_f2]
+// with d = r - x0 and g_0 = -(g_1 + g_2 + g_3).
+template <typename R>
+struct V3 {
+  R x, y, z;
+};
+template <typename R>
+__device__ __forceinline__ V3<R> vcross(V3<R> a, V3<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ R vdot(V3<R> a, V3<R> b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+
+template <typename R, typename C2>
+__device__ __forceinline__ void field_coeffs(const V3<R> g[4], const C2* __restrict__ edof,
+                                             const C2* __restrict__ fdof, const int32_t* eid,
+                                             const int32_t* fid, R cre, R cim, R out[10]) {
+  R eps[6], bet[4];
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const C2 d = edof[eid[e]];
+    eps[e] = cre * d.x - cim * d.y;
+  }
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    const C2 d = fdof[fid[f]];
+    bet[f] = cre * d.x - cim * d.y;
+  }
+  V3<R> E0 = {eps[0] * g[1].x + eps[1] * g[2].x + eps[2] * g[3].x,
+              eps[0] * g[1].y + eps[1] * g[2].y + eps[2] * g[3].y,
+              eps[0] * g[1].z + eps[1] * g[2].z + eps[2] * g[3].z};
+  V3<R> W = {0, 0, 0};
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const V3<R> c = vcross(g[le1(e)], g[le0(e)]);
+    W.x += eps[e] * c.x;
+    W.y += eps[e] * c.y;
+    W.z += eps[e] * c.z;
+  }
+  const V3<R> c23 = vcross(g[2], g[3]), c13 = vcross(g[1], g[3]), c12 = vcross(g[1], g[2]);
+  V3<R> B0 = {R(2) * (bet[1] * c23.x + bet[2] * c13.x + bet[3] * c12.x),
+              R(2) * (bet[1] * c23.y + bet[2] * c13.y + bet[3] * c12.y),
+              R(2) * (bet[1] * c23.z + bet[2] * c13.z + bet[3] * c12.z)};
+  R beta = 0;
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    const V3<R> a = g[lf(f, 0)], b = g[lf(f, 1)], c = g[lf(f, 2)];
+    beta += bet[f] * vdot(a, vcross(b, c));
+  }
+  beta *= R(2);
+  out[0] = E0.x; out[1] = E0.y; out[2] = E0.z;
+  out[3] = W.x;  out[4] = W.y;  out[5] = W.z;
+  out[6] = B0.x; out[7] = B0.y; out[8] = B0.z;
+  out[9] = beta;
+}
+
+__global__ void __launch_bounds__(kThreads) k_field_fp64(int64_t nt, const double* __restrict__ geom64,
+                                                          const int4* __restrict__ te, const int4* __restrict__ tf,
+                                                          const double2* __restrict__ edof,
+                                                          const double2* __restrict__ fdof, double cre, double cim,
+                                                          double* __restrict__ field) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double* G = geom64 + 12 * t;
+  V3<double> g[4];
+  g[1] = {G[3], G[4], G[5]};
+  g[2] = {G[6], G[7], G[8]};
+  g[3] = {G[9], G[10], G[11]};
+  g[0] = {-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z)};
+  const int4 e0 = te[2 * t], e1 = te[2 * t + 1], f = tf[t];
+  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
+  const int32_t fid[4] = {f.x, f.y, f.z, f.w};
+  double out[10];
+  field_coeffs<double, double2>(g, edof, fdof, eid, fid, cre, cim, out);
+  double2* o = reinterpret_cast<double2*>(field + 10 * t);
+#pragma unroll
+  for (int i = 0; i < 5; i++) o[i] = make_double2(out[2 * i], out[2 * i + 1]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, const float4* __restrict__ g32,
+                                                         const int4* __restrict__ te, const int4* __restrict__ tf,
+                                                         const float2* __restrict__ edof,
+                                                         const float2* __restrict__ fdof, float cre, float cim,
+                                                         float4* __restrict__ field) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const float4 a = g32[3 * t], b = g32[3 * t + 1], c = g32[3 * t + 2];
+  V3<float> g[4];
+  g[1] = {a.x, a.y, a.z};
+  g[2] = {a.w, b.x, b.y};
+  g[3] = {b.z, b.w, c.x};
+  g[0] = {-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z)};
+  const int4 e0 = te[2 * t], e1 = te[2 * t + 1], f = tf[t];
+  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
+  const int32_t fid[4] = {f.x, f.y, f.z, f.w};
+  float out[10];
+  field_coeffs<float, float2>(g, edof, fdof, eid, fid, cre, cim, out);
+  field[3 * t] = make_float4(out[0], out[1], out[2], out[3]);
+  field[3 * t + 1] = make_float4(out[4], out[5], out[6], out[7]);
+  field[3 * t + 2] = make_float4(out[8], out[9], 0.f, 0.f);
+}
+
+// ------------------------------------------------------------ FP64 push
+__device__ __forceinline__ void bary64(const double* __restrict__ g, const double r[3], double lam[4]) {
+  const double dx = r[0] - g[0], dy = r[1] - g[1], dz = r[2] - g[2];
+#pragma unroll
+  for (int k = 1; k < 4; k++) {
+    const double* gk = g + 3 * k;
+    lam[k] = fma(gk[2], dz, fma(gk[1], dy, gk[0] * dx));
+  }
+  lam[0] = __dsub_rn(__dsub_rn(__dsub_rn(1.0, lam[1]), lam[2]), lam[3]);
+}
+
+__device__ __forceinline__ void deposit64(const PushArgs& A, int32_t T, const double la[4], const double lb[4],
+                                          double qw) {
+  const int4 e0 = __ldg(&A.te[2 * (int64_t)T]), e1 = __ldg(&A.te[2 * (int64_t)T + 1]);
+  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const int i = le0(e), j = le1(e);
+    const double g = qw * fma(la[i], lb[j], -(la[j] * lb[i]));
+    atomicAdd(A.dG + eid[e], g);
+  }
+}
+
+__device__ __forceinline__ int4 ldg_int4(const int4* p) { return __ldg(p); }
+
+__global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned ncr = 0, nfrz = 0;
+  if (p < A.n) {
+    int32_t T = A.tet[p];
+    if (T >= A.nt) {
+      A.tet[p] = -1;
+      A.status[p] = FEMPIC_P_LOST;
+      nfrz = 1;
+    } else if (T >= 0) {
+      const int s = species_of(A.sp, p);
+      const double kq = A.sp.kq[s], qw = A.sp.qw[s];
+      double* vxp = static_cast<double*>(A.vx);
+      double* vyp = static_cast<double*>(A.vy);
+      double* vzp = static_cast<double*>(A.vz);
+      double a[3] = {A.x[p], A.y[p], A.z[p]};
+      const double v[3] = {vxp[p], vyp[p], vzp[p]};
+      const double* G = A.geom64 + 12 * (int64_t)T;
+      const double2* F = reinterpret_cast<const double2*>(static_cast<const double*>(A.field) + 10 * (int64_t)T);
+      const double2 f0 = __ldg(F), f1 = __ldg(F + 1), f2 = __ldg(F + 2), f3 = __ldg(F + 3), f4 = __ldg(F + 4);
+      const double dx = a[0] - __ldg(G), dy = a[1] - __ldg(G + 1), dz = a[2] - __ldg(G + 2);
+      // (b)+(c) gather with the carrier already restored per tet
+      const double Wx = f1.y, Wy = f2.x, Wz = f2.y;
+      const double Ex = f0.x + (dy * Wz - dz * Wy);
+      const double Ey = f0.y + (dz * Wx - dx * Wz);
+      const double Ez = f1.x + (dx * Wy - dy * Wx);
+      const double beta = f4.y;
+      const double Bx = f3.x + beta * dx, By = f3.y + beta * dy, Bz = f4.x + beta * dz;
+      // (d) Boris
+      const double vmx = v[0] + kq * Ex, vmy = v[1] + kq * Ey, vmz = v[2] + kq * Ez;
+      const double tx = kq * Bx, ty = kq * By, tz = kq * Bz;
+      const double t2 = tx * tx + ty * ty + tz * tz;
+      const double f = 2.0 / (1.0 + t2);
+      const double sx = f * tx, sy = f * ty, sz = f * tz;
+      const double vpx = vmx + (vmy * tz - vmz * ty);
+      const double vpy = vmy + (vmz * tx - vmx * tz);
+      const double vpz = vmz + (vmx * ty - vmy * tx);
+      double vn[3] = {vmx + (vpy * sz - vpz * sy) + kq * Ex, vmy + (vpz * sx - vpx * sz) + kq * Ey,
+                      vmz + (vpx * sy - vpy * sx) + kq * Ez};
+      double b[3] = {a[0] + A.dt * vn[0], a[1] + A.dt * vn[1], a[2] + A.dt * vn[2]};
+      if (!(isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]) && isfinite(b[0]) && isfinite(b[1]) &&
+            isfinite(b[2]))) {
+        A.status[p] = FEMPIC_P_NONFINITE;
+        A.tet[p] = -2 - T;
+        nfrz = 1;
+      } else {
+        // (e) track + (f) deposit
+        double la[4], lb[4], lp[4];
+        bary64(G, a, la);
+        int entry = -1;
+        int32_t nc = 0;
+        uint8_t st = FEMPIC_P_OK;
+        for (;;) {
+          bary64(A.geom64 + 12 * (int64_t)T, b, lb);
+          int kx = -1;
+          double smin = INFINITY;
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            if (k == entry || !(lb[k] < 0.0)) continue;
+            double sk = la[k] / (la[k] - lb[k]);
+            if (sk < 0.0) sk = 0.0;
+            if (sk < smin) {
+              smin = sk;
+              kx = k;
+            }
+          }
+          if (kx < 0) {
+            deposit64(A, T, la, lb, qw);
+            a[0] = b[0];
+            a[1] = b[1];
+            a[2] = b[2];
+            break;
+          }
+#pragma unroll
+          for (int i = 0; i < 4; i++) lp[i] = (i == kx) ? 0.0 : fma(smin, lb[i] - la[i], la[i]);
+          deposit64(A, T, la, lp, qw);
+          nc++;
+#pragma unroll
+          for (int c = 0; c < 3; c++) a[c] = fma(smin, b[c] - a[c], a[c]);
+          if (nc > A.max_cross) {
+            st = FEMPIC_P_CAP;
+            break;
+          }
+          const int4 nbv = ldg_int4(&A.nb[T]);
+          const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+          if (nbt >= 0) {
+            const int4 o4 = ldg_int4(&A.tn[T]), n4 = ldg_int4(&A.tn[nbt]);
+            const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nn[4] = {n4.x, n4.y, n4.z, n4.w};
+            int ent = 0;
+#pragma unroll
+            for (int i2 = 0; i2 < 4; i2++) {
+              int hit = -1;
+#pragma unroll
+              for (int i = 0; i < 4; i++)
+                if (on[i] == nn[i2]) hit = i;
+              double val = 0.0;
+#pragma unroll
+              for (int i = 0; i < 4; i++)
+                if (i == hit) val = lp[i];
+              la[i2] = val;
+              if (hit < 0) ent = i2;
+            }
+            T = nbt;
+            entry = ent;
+          } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
+            const int code = -1 - nbt, ax = code >> 1, side = code & 1;
+            const double L = side ? A.hi[ax] : A.lo[ax];
+            b[ax] = 2.0 * L - b[ax];
+            vn[ax] = -vn[ax];
+#pragma unroll
+            for (int i = 0; i < 4; i++) la[i] = lp[i];
+            entry = kx;
+          } else {
+            st = FEMPIC_P_ABSORBED;
+            break;
+          }
+        }
+        A.x[p] = a[0];
+        A.y[p] = a[1];
+        A.z[p] = a[2];
+        vxp[p] = vn[0];
+        vyp[p] = vn[1];
+        vzp[p] = vn[2];
+        if (st != FEMPIC_P_OK) {
+          A.status[p] = st;
+          T = -2 - T;
+          nfrz = 1;
+        }
+        A.tet[p] = T;
+        if (A.ncross) A.ncross[p] += nc;
+        ncr = (unsigned)nc;
+      }
+    }
+  }
+  ncr = __reduce_add_sync(0xffffffffu, ncr);
+  nfrz = __reduce_add_sync(0xffffffffu, nfrz);
+  if ((threadIdx.x & 31) == 0) {
+    if (ncr) atomicAdd(A.stats, (unsigned long long)ncr);
+    if (nfrz) atomicAdd(A.stats + 1, (unsigned long long)nfrz);
+  }
+}
+
+// ------------------------------------------------------------ mixed push
+// FP32 gather, carrier product and Boris; FP64 positions.  Barycentrics for
+// tracking and deposit are FP32 values fixed to 24-bit integers Q with
+// Q_0 = 2^24 - Q_1 - Q_2 - Q_3, so sum(Q) = 2^24 exactly and the per-segment
+// deposit g_ij = Qa_i Qb_j - Qa_j Qb_i is exact in int64: its edge divergence
+// is exactly 2^24 (Qb - Qa) at the nodes, so charge is conserved exactly.
+__device__ __forceinline__ void bary_q(const float4* __restrict__ g32, int64_t T, float dx, float dy, float dz,
+                                       int32_t Q[4]) {
+  const float4 a = __ldg(g32 + 3 * T), b = __ldg(g32 + 3 * T + 1), c = __ldg(g32 + 3 * T + 2);
+  const float l1 = __fmaf_rn(a.z, dz, __fmaf_rn(a.y, dy, __fmul_rn(a.x, dx)));
+  const float l2 = __fmaf_rn(b.y, dz, __fmaf_rn(b.x, dy, __fmul_rn(a.w, dx)));
+  const float l3 = __fmaf_rn(c.x, dz, __fmaf_rn(b.w, dy, __fmul_rn(b.z, dx)));
+  // |lambda| <= 32 keeps Q_0 = 2^24 - Q_1 - Q_2 - Q_3 inside int32 for points
+  // up to 32 tet diameters away (a clamped point still tracks cell by cell).
+  Q[1] = __float2int_rn(__fmul_rn(fminf(fmaxf(l1, -kQClamp), kQClamp), kQScale));
+  Q[2] = __float2int_rn(__fmul_rn(fminf(fmaxf(l2, -kQClamp), kQClamp), kQScale));
+  Q[3] = __float2int_rn(__fmul_rn(fminf(fmaxf(l3, -kQClamp), kQClamp), kQScale));
+  Q[0] = kQOne - Q[1] - Q[2] - Q[3];
+}
+
+struct X0 {
+  double x, y, z;
+};
+
+// x0v holds 2 double2 per tet: (x0x, x0y), (x0z, 0)
+__device__ __forceinline__ X0 ld_x0(const double2* x0v, int64_t T) {
+  const double2 a = __ldg(x0v + 2 * T), b = __ldg(x0v + 2 * T + 1);
+  return X0{a.x, a.y, b.x};
+}
+
+__device__ __forceinline__ void dpos(const X0& x0, const double r[3], float& dx, float& dy, float& dz) {
+  dx = __double2float_rn(__dsub_rn(r[0], x0.x));
+  dy = __double2float_rn(__dsub_rn(r[1], x0.y));
+  dz = __double2float_rn(__dsub_rn(r[2], x0.z));
+}
+
+__device__ __forceinline__ void gq(const int32_t a[4], const int32_t b[4], long long g[6]) {
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const int i = le0(e), j = le1(e);
+    g[e] = (long long)a[i] * b[j] - (long long)a[j] * b[i];
+  }
+}
+
+__device__ __forceinline__ void depositq_atomic(const PushArgs& A, int32_t T, int s, const long long g[6]) {
+  const int4 e0 = __ldg(&A.te[2 * (int64_t)T]), e1 = __ldg(&A.te[2 * (int64_t)T + 1]);
+  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
+  unsigned long long* base = A.dGq + (int64_t)s * A.ne;
+#pragma unroll
+  for (int e = 0; e < 6; e++)
+    if (g[e]) atomicAdd(base + eid[e], (unsigned long long)g[e]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  unsigned ncr = 0, nfrz = 0;
+  long long gh[6] = {0, 0, 0, 0, 0, 0};  // deposit of the first segment (home tet), reduced per warp
+  int32_t key = -1 - lane;               // (home tet, species) run key; negative = no deposit
+  int32_t Thome = 0;
+  int shome = 0;
+  if (p < A.n) {
+    int32_t T = A.tet[p];
+    if (T >= A.nt) {
+      A.tet[p] = -1;
+      A.status[p] = FEMPIC_P_LOST;
+      nfrz = 1;
+    } else if (T >= 0) {
+      const int s = species_of(A.sp, p);
+      const float kq = (float)A.sp.kq[s];
+      float* vxp = static_cast<float*>(A.vx);
+      float* vyp = static_cast<float*>(A.vy);
+      float* vzp = static_cast<float*>(A.vz);
+      double a[3] = {A.x[p], A.y[p], A.z[p]};
+      const float v0 = vxp[p], v1 = vyp[p], v2 = vzp[p];
+      const X0 x0 = ld_x0(A.x0v, T);
+      float dx, dy, dz;
+      dpos(x0, a, dx, dy, dz);
+      const float4* F = static_cast<const float4*>(A.field) + 3 * (int64_t)T;
+      const float4 f0 = __ldg(F), f1 = __ldg(F + 1), f2 = __ldg(F + 2);
+      // f0 = (E0x, E0y, E0z, Wx), f1 = (Wy, Wz, B0x, B0y), f2 = (B0z, beta, -, -)
+      const float Ex = f0.x + (dy * f1.y - dz * f1.x);
+      const float Ey = f0.y + (dz * f0.w - dx * f1.y);
+      const float Ez = f0.z + (dx * f1.x - dy * f0.w);
+      const float Bx = f1.z + f2.y * dx, By = f1.w + f2.y * dy, Bz = f2.x + f2.y * dz;
+      const float vmx = v0 + kq * Ex, vmy = v1 + kq * Ey, vmz = v2 + kq * Ez;
+      const float tx = kq * Bx, ty = kq * By, tz = kq * Bz;
+      const float t2 = tx * tx + ty * ty + tz * tz;
+      const float f = 2.0f / (1.0f + t2);
+      const float sx = f * tx, sy = f * ty, sz = f * tz;
+      const float vpx = vmx + (vmy * tz - vmz * ty);
+      const float vpy = vmy + (vmz * tx - vmx * tz);
+      const float vpz = vmz + (vmx * ty - vmy * tx);
+      float vn[3] = {vmx + (vpy * sz - vpz * sy) + kq * Ex, vmy + (vpz * sx - vpx * sz) + kq * Ey,
+                     vmz + (vpx * sy - vpy * sx) + kq * Ez};
+      const float dt32 = (float)A.dt;
+      double b[3] = {__dadd_rn(a[0], (double)(dt32 * vn[0])), __dadd_rn(a[1], (double)(dt32 * vn[1])),
+                     __dadd_rn(a[2], (double)(dt32 * vn[2]))};
+      if (!(isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]) && isfinite(b[0]) && isfinite(b[1]) &&
+            isfinite(b[2]))) {
+        A.status[p] = FEMPIC_P_NONFINITE;
+        A.tet[p] = -2 - T;
+        nfrz = 1;
+      } else {
+        int32_t Qa[4], Qb[4], Qp[4];
+        bary_q(A.g32, T, dx, dy, dz, Qa);
+        float bx, by, bz;
+        dpos(x0, b, bx, by, bz);
+        bary_q(A.g32, T, bx, by, bz, Qb);
+        Thome = T;
+        shome = s;
+        bool first = true;
+        int entry = -1;
+        int32_t nc = 0;
+        uint8_t st = FEMPIC_P_OK;
+        for (;;) {
+          int kx = -1;
+          float smin = INFINITY;
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            if (k == entry || Qb[k] >= 0) continue;
+            const int32_t den = Qa[k] - Qb[k];
+            float sk = den > 0 ? (float)Qa[k] / (float)den : 0.0f;
+            if (sk < 0.0f) sk = 0.0f;
+            if (sk < smin) {
+              smin = sk;
+              kx = k;
+            }
+          }
+          const int32_t* Qend = Qb;
+          if (kx >= 0) {
+            // crossing point barycentrics: exact zero on the exit face, sum kept at 2^24
+            int last = -1;
+            int32_t acc = 0;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              if (i == kx) {
+                Qp[i] = 0;
+              } else {
+                Qp[i] = Qa[i] + __float2int_rn(smin * (float)(Qb[i] - Qa[i]));
+                acc += Qp[i];
+                last = i;
+              }
+            }
+            Qp[last] += kQOne - acc;
+            Qend = Qp;
+          }
+          long long g[6];
+          gq(Qa, Qend, g);
+          if (first) {
+#pragma unroll
+            for (int e = 0; e < 6; e++) gh[e] = g[e];
+            first = false;
+          } else {
+            depositq_atomic(A, T, s, g);
+          }
+          if (kx < 0) {
+            a[0] = b[0];
+            a[1] = b[1];
+            a[2] = b[2];
+            break;
+          }
+          nc++;
+          const double sd = (double)smin;
+#pragma unroll
+          for (int c = 0; c < 3; c++) a[c] = fma(sd, b[c] - a[c], a[c]);
+          if (nc > A.max_cross) {
+            st = FEMPIC_P_CAP;
+            break;
+          }
+          const int4 nbv = __ldg(&A.nb[T]);
+          const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+          if (nbt >= 0) {
+            const int4 o4 = __ldg(&A.tn[T]), n4 = __ldg(&A.tn[nbt]);
+            const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nnd[4] = {n4.x, n4.y, n4.z, n4.w};
+            int ent = 0;
+#pragma unroll
+            for (int i2 = 0; i2 < 4; i2++) {
+              int32_t val = 0;
+              bool hit = false;
+#pragma unroll
+              for (int i = 0; i < 4; i++)
+                if (on[i] == nnd[i2]) {
+                  val = Qp[i];
+                  hit = true;
+                }
+              Qa[i2] = val;
+              if (!hit) ent = i2;
+            }
+            T = nbt;
+            entry = ent;
+          } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
+            const int code = -1 - nbt, ax = code >> 1, side = code & 1;
+            const double L = side ? A.hi[ax] : A.lo[ax];
+            b[ax] = 2.0 * L - b[ax];
+            vn[ax] = -vn[ax];
+#pragma unroll
+            for (int i = 0; i < 4; i++) Qa[i] = Qp[i];
+            entry = kx;
+          } else {
+            st = FEMPIC_P_ABSORBED;
+            break;
+          }
+          const X0 xc = ld_x0(A.x0v, T);
+          float ex, ey, ez;
+          dpos(xc, b, ex, ey, ez);
+          bary_q(A.g32, T, ex, ey, ez, Qb);
+        }
+        key = Thome * kMaxSpecies + shome;
+        A.x[p] = a[0];
+        A.y[p] = a[1];
+        A.z[p] = a[2];
+        vxp[p] = vn[0];
+        vyp[p] = vn[1];
+        vzp[p] = vn[2];
+        if (st != FEMPIC_P_OK) {
+          A.status[p] = st;
+          T = -2 - T;
+          nfrz = 1;
+        }
+        A.tet[p] = T;
+        if (A.ncross) A.ncross[p] += nc;
+        ncr = (unsigned)nc;
+      }
+    }
+  }
+  // Warp segmented reduction of the home-tet deposit over runs of equal keys
+  // (particles are sorted by tet, so neighbouring lanes usually share one).
+  const unsigned full = 0xffffffffu;
+  const int32_t prev = __shfl_up_sync(full, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(full, head);
+  const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
+  const int run_end = above ? (__ffs(above) - 2) : 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+      const long long o = __shfl_down_sync(full, gh[e], off);
+      if (lane + off <= run_end) gh[e] += o;
+    }
+  }
+  if (head && key >= 0) {
+    const int4 e0 = __ldg(&A.te[2 * (int64_t)Thome]), e1 = __ldg(&A.te[2 * (int64_t)Thome + 1]);
+    const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
+    unsigned long long* base = A.dGq + (int64_t)shome * A.ne;
+#pragma unroll
+    for (int e = 0; e < 6; e++)
+      if (gh[e]) atomicAdd(base + eid[e], (unsigned long long)gh[e]);
+  }
+  ncr = __reduce_add_sync(full, ncr);
+  nfrz = __reduce_add_sync(full, nfrz);
+  if (lane == 0) {
+    if (ncr) atomicAdd(A.stats, (unsigned long long)ncr);
+    if (nfrz) atomicAdd(A.stats + 1, (unsigned long long)nfrz);
+  }
+}
+
+// ------------------------------------------------------- deposit finalize
+struct FinalizeArgs {
+  int64_t ne;
+  int32_t mixed;
+  int32_t ns;
+  double qwscale[kMaxSpecies];   // q w 2^-48 per species (mixed form)
+  double* dG;
+  unsigned long long* dGq;
+  double* Gcum;
+  double* dG_out;
+  double* Gcum_out;
+  double2* Genv_out;
+  double c, s;                   // cos, sin of omega0 t_next
+};
+
+__global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= A.ne) return;
+  double d;
+  if (A.mixed) {
+    d = 0.0;
+    for (int s = 0; s < A.ns; s++) {
+      const long long q = (long long)A.dGq[(int64_t)s * A.ne + e];
+      d += A.qwscale[s] * (double)q;
+      A.dGq[(int64_t)s * A.ne + e] = 0ull;
+    }
+  } else {
+    d = A.dG[e];
+    A.dG[e] = 0.0;
+  }
+  const double g = A.Gcum[e] + d;
+  A.Gcum[e] = g;
+  if (A.dG_out) A.dG_out[e] = d;
+  if (A.Gcum_out) A.Gcum_out[e] = g;
+  if (A.Genv_out) A.Genv_out[e] = make_double2(A.c * g, -(A.s * g));
+}
+
+// ------------------------------------------------------------ nodal charge
+struct ChargeArgs {
+  int64_t n;
+  const double* x;
+  const double* y;
+  const double* z;
+  const int32_t* tet;
+  Species sp;
+  int64_t nt;
+  int32_t mixed;
+  const double* geom64;
+  const double2* x0v;
+  const float4* g32;
+  const int4* tn;
+  double* rho;
+};
+
+__global__ void __launch_bounds__(kThreads) k_nodal_charge(ChargeArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.n) return;
+  int32_t T = A.tet[p];
+  if (T == -1) return;
+  if (T < 0) T = -2 - T;
+  if (T >= A.nt) return;
+  const int s = species_of(A.sp, p);
+  const double qw = A.sp.qw[s];
+  const double r[3] = {A.x[p], A.y[p], A.z[p]};
+  double lam[4];
+  if (A.mixed) {
+    float dx, dy, dz;
+    dpos(ld_x0(A.x0v, T), r, dx, dy, dz);
+    int32_t Q[4];
+    bary_q(A.g32, T, dx, dy, dz, Q);
+    for (int i = 0; i < 4; i++) lam[i] = (double)Q[i] * (1.0 / (double)kQOne);
+  } else {
+    bary64(A.geom64 + 12 * (int64_t)T, r, lam);
+  }
+  const int4 n4 = A.tn[T];
+  atomicAdd(A.rho + n4.x, qw * lam[0]);
+  atomicAdd(A.rho + n4.y, qw * lam[1]);
+  atomicAdd(A.rho + n4.z, qw * lam[2]);
+  atomicAdd(A.rho + n4.w, qw * lam[3]);
+}
+
+
+// ------------------------------------------------------------ particle sort
+// Counting sort by key = species * (nt + 1) + (0 <= tet < nt ? tet : nt).
+__device__ __forceinline__ int32_t sort_key(const Species& sp, int64_t p, int32_t T, int64_t nt) {
+  const int s = species_of(sp, p);
+  return (int32_t)(s * (nt + 1) + ((T >= 0 && T < nt) ? (int64_t)T : nt));
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_hist(int64_t n, const int32_t* __restrict__ tet, Species sp,
+                                                         int64_t nt, int32_t* __restrict__ counts) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool act = p < n;
+  const int32_t key = act ? sort_key(sp, p, tet[p], nt) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  if (act && lane == __ffs(peers) - 1) atomicAdd(counts + key, __popc(peers));
+}
+
+// Exclusive scan over `k` int32 counts in tiles of 2 * kScan; tile totals go
+// to `sums`, scanned by one block, then added back.
+constexpr int kScan = 1024;
+
+__device__ __forceinline__ int32_t block_excl_scan(int32_t v, int32_t* sh, int32_t* total) {
+  // Hillis-Steele inclusive scan in shared memory over blockDim.x entries
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < blockDim.x; off <<= 1) {
+    const int32_t o = t >= off ? sh[t - off] : 0;
+    __syncthreads();
+    sh[t] += o;
+    __syncthreads();
+  }
+  const int32_t incl = sh[t];
+  *total = sh[blockDim.x - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(kScan) k_scan_tiles(int64_t k, const int32_t* __restrict__ in,
+                                                      int32_t* __restrict__ out, int32_t* __restrict__ sums) {
+  __shared__ int32_t sh[kScan];
+  const int64_t base = blockIdx.x * (int64_t)(2 * kScan);
+  const int64_t i0 = base + 2 * threadIdx.x;
+  const int32_t a = i0 < k ? in[i0] : 0, b = i0 + 1 < k ? in[i0 + 1] : 0;
+  int32_t total;
+  const int32_t ex = block_excl_scan(a + b, sh, &total);
+  if (i0 < k) out[i0] = ex;
+  if (i0 + 1 < k) out[i0 + 1] = ex + a;
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScan) k_scan_sums(int64_t m, int32_t* __restrict__ sums) {
+  __shared__ int32_t sh[kScan];
+  int32_t carry = 0;
+  for (int64_t c = 0; c < m; c += kScan) {
+    const int64_t i = c + threadIdx.x;
+    const int32_t v = i < m ? sums[i] : 0;
+    int32_t total;
+    const int32_t ex = block_excl_scan(v, sh, &total);
+    if (i < m) sums[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_add(int64_t k, int32_t* __restrict__ out,
+                                                        const int32_t* __restrict__ sums) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < k) out[i] += sums[i / (2 * kScan)];
+}
+
+struct SortArgs {
+  int64_t n;
+  Species sp;
+  int64_t nt;
+  int32_t vbytes;               // 8 (FP64 form) or 4 (mixed)
+  const double *x, *y, *z;
+  const void *vx, *vy, *vz;
+  const int32_t* tet;
+  const uint8_t* status;
+  const int32_t* ncross;
+  double *ox, *oy, *oz;
+  void *ovx, *ovy, *ovz;
+  int32_t* otet;
+  uint8_t* ostatus;
+  int32_t* oncross;
+  const int32_t* offsets;
+  int32_t* cursor;
+};
+
+__global__ void __launch_bounds__(kThreads) k_sort_scatter(SortArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool act = p < A.n;
+  const int32_t T = act ? A.tet[p] : 0;
+  const int32_t key = act ? sort_key(A.sp, p, T, A.nt) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int32_t base = 0;
+  if (act && lane == leader) base = atomicAdd(A.cursor + key, __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (!act) return;
+  const int64_t q = (int64_t)A.offsets[key] + base + __popc(peers & ((1u << lane) - 1u));
+  A.ox[q] = A.x[p];
+  A.oy[q] = A.y[p];
+  A.oz[q] = A.z[p];
+  if (A.vbytes == 8) {
+    static_cast<double*>(A.ovx)[q] = static_cast<const double*>(A.vx)[p];
+    static_cast<double*>(A.ovy)[q] = static_cast<const double*>(A.vy)[p];
+    static_cast<double*>(A.ovz)[q] = static_cast<const double*>(A.vz)[p];
+  } else {
+    static_cast<float*>(A.ovx)[q] = static_cast<const float*>(A.vx)[p];
+    static_cast<float*>(A.ovy)[q] = static_cast<const float*>(A.vy)[p];
+    static_cast<float*>(A.ovz)[q] = static_cast<const float*>(A.vz)[p];
+  }
+  A.otet[q] = T;
+  A.ostatus[q] = A.status[p];
+  if (A.oncross) A.oncross[q] = A.ncross[p];
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+}
+
+}  // namespace
+
+// =================================================================== ABI
+struct fempic_env {
+  int device = 0;
+  fempic_options opt{};
+  HostMesh h;
+  double* geom64 = nullptr;
+  double2* x0v = nullptr;
+  float4* g32 = nullptr;
+  int4* tn = nullptr;
+  int4* nb = nullptr;
+  int4* te = nullptr;
+  int4* tf = nullptr;
+  void* field = nullptr;
+  double* dG = nullptr;
+  unsigned long long* dGq = nullptr;
+  int32_t dGq_species = 0;
+  double* Gcum = nullptr;
+  unsigned long long* stats = nullptr;
+  int64_t* gstart = nullptr;
+  int32_t* gtet = nullptr;
+  double qw_last[kMaxSpecies] = {0};
+  int32_t ns_last = 0;
+  int64_t steps = 0;
+  // per-kernel event timing (measurement support)
+  struct Rec {
+    int kid;
+    cudaEvent_t a, b;
+  };
+  int32_t* sort_counts = nullptr;   // [sort_cap] per-key counters, then cursors
+  int32_t* sort_offsets = nullptr;  // [sort_cap]
+  int32_t* sort_sums = nullptr;     // [sort_cap / 2048 + 1]
+  int64_t sort_cap = 0;
+  bool profiling = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+namespace {
+constexpr size_t kMaxRecords = 65536;
+
+// Brackets one kernel launch with events when profiling is on.
+struct LaunchTimer {
+  fempic_env* e;
+  cudaStream_t st;
+  int kid;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEvent_t take() {
+    if (e->pool_used == e->pool.size()) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+      e->pool.push_back(ev);
+    }
+    return e->pool[e->pool_used++];
+  }
+  LaunchTimer(fempic_env* env, cudaStream_t s, int k) : e(env), st(s), kid(k) {
+    if (!e->profiling || e->recs.size() >= kMaxRecords) return;
+    a = take();
+    b = take();
+    if (a && b) cudaEventRecord(a, st);
+  }
+  ~LaunchTimer() {
+    if (a && b) {
+      cudaEventRecord(b, st);
+      e->recs.push_back({kid, a, b});
+    }
+  }
+};
+}  // namespace
+
+static void free_env(fempic_env* e) {
+  if (!e) return;
+  for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
+  void* ptrs[] = {e->geom64, e->x0v, e->g32, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete e;
+}
+
+extern "C" const char* fempic_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" void fempic_env_destroy(fempic_env* env) { free_env(env); }
+
+static int upload(fempic_env* e) {
+  const HostMesh& m = e->h;
+  const int64_t nt = m.nt;
+  std::vector<double2> x0(2 * nt);
+  std::vector<float4> g(3 * nt);
+  std::vector<int4> tn(nt), nb(nt), te(2 * nt), tf(nt);
+  for (int64_t t = 0; t < nt; t++) {
+    const double* G = &m.geom[12 * t];
+    x0[2 * t] = make_double2(G[0], G[1]);
+    x0[2 * t + 1] = make_double2(G[2], 0.0);
+    float gf[12];
+    for (int i = 0; i < 9; i++) gf[i] = (float)G[3 + i];
+    gf[9] = gf[10] = gf[11] = 0.f;
+    g[3 * t] = make_float4(gf[0], gf[1], gf[2], gf[3]);
+    g[3 * t + 1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
+    g[3 * t + 2] = make_float4(gf[8], gf[9], gf[10], gf[11]);
+    tn[t] = make_int4(m.tn[4 * t], m.tn[4 * t + 1], m.tn[4 * t + 2], m.tn[4 * t + 3]);
+    nb[t] = make_int4(m.nb[4 * t], m.nb[4 * t + 1], m.nb[4 * t + 2], m.nb[4 * t + 3]);
+    te[2 * t] = make_int4(m.te[6 * t], m.te[6 * t + 1], m.te[6 * t + 2], m.te[6 * t + 3]);
+    te[2 * t + 1] = make_int4(m.te[6 * t + 4], m.te[6 * t + 5], 0, 0);
+    tf[t] = make_int4(m.tf[4 * t], m.tf[4 * t + 1], m.tf[4 * t + 2], m.tf[4 * t + 3]);
+  }
+  FEMPIC_CUDA(dalloc(&e->geom64, 12 * nt));
+  FEMPIC_CUDA(dalloc(&e->x0v, 2 * nt));
+  FEMPIC_CUDA(dalloc(&e->g32, 3 * nt));
+  FEMPIC_CUDA(dalloc(&e->tn, nt));
+  FEMPIC_CUDA(dalloc(&e->nb, nt));
+  FEMPIC_CUDA(dalloc(&e->te, 2 * nt));
+  FEMPIC_CUDA(dalloc(&e->tf, nt));
+  FEMPIC_CUDA(cudaMemcpy(e->geom64, m.geom.data(), 12 * nt * sizeof(double), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->x0v, x0.data(), 2 * nt * sizeof(double2), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->g32, g.data(), 3 * nt * sizeof(float4), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->tn, tn.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->nb, nb.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->te, te.data(), 2 * nt * sizeof(int4), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->tf, tf.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
+  if (e->opt.precision == FEMPIC_FP64) {
+    FEMPIC_CUDA(dalloc(reinterpret_cast<double**>(&e->field), 10 * nt));
+    FEMPIC_CUDA(dalloc(&e->dG, m.ne));
+    FEMPIC_CUDA(cudaMemset(e->dG, 0, m.ne * sizeof(double)));
+  } else {
+    FEMPIC_CUDA(dalloc(reinterpret_cast<float4**>(&e->field), 3 * nt));
+  }
+  FEMPIC_CUDA(dalloc(&e->Gcum, m.ne));
+  FEMPIC_CUDA(cudaMemset(e->Gcum, 0, m.ne * sizeof(double)));
+  FEMPIC_CUDA(dalloc(&e->stats, 4));
+  FEMPIC_CUDA(cudaMemset(e->stats, 0, 4 * sizeof(unsigned long long)));
+  FEMPIC_CUDA(dalloc(&e->gstart, m.gstart.size()));
+  FEMPIC_CUDA(dalloc(&e->gtet, m.gtet.size() + 1));
+  FEMPIC_CUDA(cudaMemcpy(e->gstart, m.gstart.data(), m.gstart.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  if (!m.gtet.empty())
+    FEMPIC_CUDA(cudaMemcpy(e->gtet, m.gtet.data(), m.gtet.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaDeviceSynchronize());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_env_create(const fempic_mesh_desc* mesh, const fempic_options* opts, fempic_env** out) {
+  g_last_error.clear();
+  if (!mesh || !opts || !out) return fail(FEMPIC_EINVAL, "env_create: NULL argument");
+  *out = nullptr;
+  if ((opts->precision != FEMPIC_FP64 && opts->precision != FEMPIC_MIXED) || opts->max_crossings < 0 ||
+      opts->max_crossings > kMaxCrossingsLimit ||
+      (opts->wall_mode != FEMPIC_WALL_REFLECT && opts->wall_mode != FEMPIC_WALL_ABSORB) || opts->reserved != 0)
+    return fail(FEMPIC_EINVAL, "env_create: bad options");
+  fempic_env* e = new (std::nothrow) fempic_env();
+  if (!e) return fail(FEMPIC_ENOMEM, "env_create: host allocation");
+  e->opt = *opts;
+  if (cudaGetDevice(&e->device) != cudaSuccess) {
+    delete e;
+    return fail(FEMPIC_ECUDA, "env_create: no CUDA device");
+  }
+  std::string err;
+  int rc = build_host_mesh(*mesh, &e->h, &err);
+  if (rc != FEMPIC_OK) {
+    delete e;
+    return fail(rc, err);
+  }
+  rc = upload(e);
+  if (rc != FEMPIC_OK) {
+    free_env(e);
+    return rc;
+  }
+  *out = e;
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_env_query(const fempic_env* env, int64_t* counts4, int32_t* tet_nodes, int32_t* edge_nodes,
+                                int32_t* face_nodes, int32_t* tet_edges, int32_t* tet_faces, int32_t* tet_nbr) {
+  if (!env) return fail(FEMPIC_EINVAL, "env_query: NULL env");
+  const HostMesh& m = env->h;
+  if (counts4) {
+    counts4[0] = m.nn;
+    counts4[1] = m.ne;
+    counts4[2] = m.nf;
+    counts4[3] = m.nt;
+  }
+  if (tet_nodes) std::memcpy(tet_nodes, m.tn.data(), m.tn.size() * sizeof(int32_t));
+  if (edge_nodes) std::memcpy(edge_nodes, m.en.data(), m.en.size() * sizeof(int32_t));
+  if (face_nodes) std::memcpy(face_nodes, m.fn.data(), m.fn.size() * sizeof(int32_t));
+  if (tet_edges) std::memcpy(tet_edges, m.te.data(), m.te.size() * sizeof(int32_t));
+  if (tet_faces) std::memcpy(tet_faces, m.tf.data(), m.tf.size() * sizeof(int32_t));
+  if (tet_nbr) std::memcpy(tet_nbr, m.nb.data(), m.nb.size() * sizeof(int32_t));
+  return FEMPIC_OK;
+}
+
+static int check_particles(const fempic_particles* p, bool need_v) {
+  if (!p) return fail(FEMPIC_EINVAL, "particles: NULL");
+  if (p->n < 0) return fail(FEMPIC_EINVAL, "particles: negative count");
+  if (p->n == 0) return FEMPIC_OK;
+  if (!p->x || !p->y || !p->z || !p->tet || !p->status)
+    return fail(FEMPIC_EINVAL, "particles: NULL position/tet/status array");
+  if (need_v && (!p->vx || !p->vy || !p->vz)) return fail(FEMPIC_EINVAL, "particles: NULL velocity array");
+  return FEMPIC_OK;
+}
+
+static int fill_species(const fempic_particles* p, double dt, Species* sp) {
+  if (p->n_species < 1 || p->n_species > kMaxSpecies || !p->species_begin || !p->q || !p->m || !p->w)
+    return fail(FEMPIC_EINVAL, "particles: species table (1..8 ranges, q, m, w)");
+  sp->ns = p->n_species;
+  if (p->species_begin[0] != 0 || p->species_begin[p->n_species] != p->n)
+    return fail(FEMPIC_EINVAL, "particles: species ranges must cover [0, n)");
+  for (int s = 0; s <= p->n_species; s++) {
+    sp->begin[s] = p->species_begin[s];
+    if (s > 0 && sp->begin[s] < sp->begin[s - 1]) return fail(FEMPIC_EINVAL, "particles: species ranges decrease");
+  }
+  for (int s = p->n_species + 1; s <= kMaxSpecies; s++) sp->begin[s] = p->n;
+  for (int s = 0; s < p->n_species; s++) {
+    if (!(p->m[s] > 0.0)) return fail(FEMPIC_EINVAL, "particles: mass must be > 0");
+    sp->kq[s] = ((p->q[s] / p->m[s]) * dt) * 0.5;
+    sp->qw[s] = p->q[s] * p->w[s];
+  }
+  for (int s = p->n_species; s < kMaxSpecies; s++) sp->kq[s] = sp->qw[s] = 0.0;
+  return FEMPIC_OK;
+}
+
+static unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+extern "C" int fempic_locate(fempic_env* env, const fempic_particles* p, void* stream) {
+  if (!env) return fail(FEMPIC_EINVAL, "locate: NULL env");
+  int rc = check_particles(p, false);
+  if (rc) return rc;
+  if (p->n == 0) return FEMPIC_OK;
+  LocateArgs A{};
+  A.n = p->n;
+  A.x = p->x;
+  A.y = p->y;
+  A.z = p->z;
+  A.tet = p->tet;
+  A.status = p->status;
+  A.geom64 = env->geom64;
+  A.gstart = env->gstart;
+  A.gtet = env->gtet;
+  for (int a = 0; a < 3; a++) {
+    A.gd[a] = env->h.gd[a];
+    A.ginv[a] = env->h.ginv[a];
+    A.lo[a] = env->h.lo[a];
+  }
+  {
+    LaunchTimer lt(env, (cudaStream_t)stream, FEMPIC_K_LOCATE);
+    k_locate<<<blocks_for(p->n), kThreads, 0, (cudaStream_t)stream>>>(A);
+  }
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
+  if (env->dGq && env->dGq_species >= ns) return FEMPIC_OK;
+  // The integer accumulators hold one step only; a larger species count
+  // reallocates them, so a step must be finalized (fempic_deposit) before the
+  // species table grows.
+  unsigned long long* nq = nullptr;
+  FEMPIC_CUDA(dalloc(&nq, (size_t)ns * env->h.ne));
+  FEMPIC_CUDA(cudaMemsetAsync(nq, 0, (size_t)ns * env->h.ne * sizeof(unsigned long long), st));
+  if (env->dGq) {
+    FEMPIC_CUDA(cudaStreamSynchronize(st));
+    cudaFree(env->dGq);
+  }
+  env->dGq = nq;
+  env->dGq_species = ns;
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, const fempic_envelope* envl,
+                                double omega0, double t, double dt, void* stream) {
+  if (!env || !envl) return fail(FEMPIC_EINVAL, "push_step: NULL env/envelope");
+  int rc = check_particles(p, true);
+  if (rc) return rc;
+  if (!envl->e_tilde || !envl->b_tilde) return fail(FEMPIC_EINVAL, "push_step: NULL DoF arrays");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(omega0) || !std::isfinite(t) ||
+      !std::isfinite(envl->amp))
+    return fail(FEMPIC_EINVAL, "push_step: non-finite or non-positive scalar");
+  cudaStream_t st = (cudaStream_t)stream;
+  PushArgs A{};
+  rc = fill_species(p, dt, &A.sp);
+  if (rc) return rc;
+  const bool mixed = env->opt.precision == FEMPIC_MIXED;
+  if (mixed) {
+    rc = ensure_mixed_accumulators(env, p->n_species, st);
+    if (rc) return rc;
+  }
+  // (c) carrier: phase and c in FP64 on the host
+  const double phi = omega0 * t;
+  const double cre = envl->amp * std::cos(phi), cim = envl->amp * std::sin(phi);
+  const int64_t nt = env->h.nt;
+  {
+  LaunchTimer lt(env, st, FEMPIC_K_FIELD);
+  if (mixed) {
+    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->g32, env->te, env->tf,
+                                                      static_cast<const float2*>(envl->e_tilde),
+                                                      static_cast<const float2*>(envl->b_tilde), (float)cre,
+                                                      (float)cim, static_cast<float4*>(env->field));
+  } else {
+    k_field_fp64<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf,
+                                                       static_cast<const double2*>(envl->e_tilde),
+                                                       static_cast<const double2*>(envl->b_tilde), cre, cim,
+                                                       static_cast<double*>(env->field));
+  }
+  }
+  FEMPIC_CUDA(cudaGetLastError());
+  env->ns_last = p->n_species;
+  for (int s = 0; s < kMaxSpecies; s++) env->qw_last[s] = A.sp.qw[s];
+  env->steps++;
+  if (p->n == 0) return FEMPIC_OK;
+  A.n = p->n;
+  A.x = p->x;
+  A.y = p->y;
+  A.z = p->z;
+  A.vx = p->vx;
+  A.vy = p->vy;
+  A.vz = p->vz;
+  A.tet = p->tet;
+  A.status = p->status;
+  A.ncross = p->n_cross;
+  A.dt = dt;
+  A.max_cross = env->opt.max_crossings;
+  A.wall_mode = env->opt.wall_mode;
+  for (int a = 0; a < 3; a++) {
+    A.lo[a] = env->h.lo[a];
+    A.hi[a] = env->h.hi[a];
+  }
+  A.nt = nt;
+  A.ne = env->h.ne;
+  A.geom64 = env->geom64;
+  A.x0v = env->x0v;
+  A.g32 = env->g32;
+  A.tn = env->tn;
+  A.nb = env->nb;
+  A.te = env->te;
+  A.field = env->field;
+  A.dG = env->dG;
+  A.dGq = env->dGq;
+  A.stats = env->stats;
+  {
+    LaunchTimer lt(env, st, FEMPIC_K_PUSH);
+    if (mixed)
+      k_push_mixed<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+    else
+      k_push_fp64<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  }
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, double* dG_out, double* G_cum_out,
+                              void* G_env_out, void* stream) {
+  if (!env) return fail(FEMPIC_EINVAL, "deposit: NULL env");
+  if (!std::isfinite(omega0) || !std::isfinite(t_next)) return fail(FEMPIC_EINVAL, "deposit: non-finite scalar");
+  const bool mixed = env->opt.precision == FEMPIC_MIXED;
+  FinalizeArgs A{};
+  A.ne = env->h.ne;
+  A.mixed = mixed;
+  A.ns = mixed ? (env->dGq ? env->ns_last : 0) : 0;
+  for (int s = 0; s < kMaxSpecies; s++) A.qwscale[s] = env->qw_last[s] * 0x1p-48;
+  A.dG = env->dG;
+  A.dGq = env->dGq;
+  A.Gcum = env->Gcum;
+  A.dG_out = dG_out;
+  A.Gcum_out = G_cum_out;
+  A.Genv_out = static_cast<double2*>(G_env_out);
+  const double phi = omega0 * t_next;
+  A.c = std::cos(phi);
+  A.s = std::sin(phi);
+  {
+    LaunchTimer lt(env, (cudaStream_t)stream, FEMPIC_K_FINALIZE);
+    k_deposit_finalize<<<blocks_for(A.ne), kThreads, 0, (cudaStream_t)stream>>>(A);
+  }
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_reset_deposit(fempic_env* env, void* stream) {
+  if (!env) return fail(FEMPIC_EINVAL, "reset_deposit: NULL env");
+  cudaStream_t st = (cudaStream_t)stream;
+  FEMPIC_CUDA(cudaMemsetAsync(env->Gcum, 0, env->h.ne * sizeof(double), st));
+  if (env->dG) FEMPIC_CUDA(cudaMemsetAsync(env->dG, 0, env->h.ne * sizeof(double), st));
+  if (env->dGq)
+    FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)env->dGq_species * env->h.ne * sizeof(unsigned long long), st));
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, double* rho, void* stream) {
+  if (!env || !rho) return fail(FEMPIC_EINVAL, "nodal_charge: NULL env/rho");
+  int rc = check_particles(p, false);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  FEMPIC_CUDA(cudaMemsetAsync(rho, 0, env->h.nn * sizeof(double), st));
+  if (p->n == 0) return FEMPIC_OK;
+  ChargeArgs A{};
+  rc = fill_species(p, 1.0, &A.sp);
+  if (rc) return rc;
+  A.n = p->n;
+  A.x = p->x;
+  A.y = p->y;
+  A.z = p->z;
+  A.tet = p->tet;
+  A.nt = env->h.nt;
+  A.mixed = env->opt.precision == FEMPIC_MIXED;
+  A.geom64 = env->geom64;
+  A.x0v = env->x0v;
+  A.g32 = env->g32;
+  A.tn = env->tn;
+  A.rho = rho;
+  {
+    LaunchTimer lt(env, st, FEMPIC_K_CHARGE);
+    k_nodal_charge<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  }
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_stats(fempic_env* env, int64_t* out3, void* stream) {
+  if (!env || !out3) return fail(FEMPIC_EINVAL, "stats: NULL argument");
+  unsigned long long h[2] = {0, 0};
+  cudaStream_t st = (cudaStream_t)stream;
+  FEMPIC_CUDA(cudaMemcpyAsync(h, env->stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  FEMPIC_CUDA(cudaStreamSynchronize(st));
+  out3[0] = (int64_t)h[0];
+  out3[1] = (int64_t)h[1];
+  out3[2] = env->steps;
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_profile_enable(fempic_env* env, int32_t enable) {
+  if (!env) return fail(FEMPIC_EINVAL, "profile_enable: NULL env");
+  if (enable) {
+    env->recs.clear();
+    env->pool_used = 0;
+  }
+  env->profiling = enable != 0;
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* launches_out) {
+  if (!env || !ms_out || !launches_out) return fail(FEMPIC_EINVAL, "profile_read: NULL argument");
+  for (int k = 0; k < FEMPIC_K_COUNT; k++) {
+    ms_out[k] = 0.0;
+    launches_out[k] = 0;
+  }
+  for (const auto& r : env->recs) {
+    FEMPIC_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    FEMPIC_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    if (r.kid >= 0 && r.kid < FEMPIC_K_COUNT) {
+      ms_out[r.kid] += ms;
+      launches_out[r.kid]++;
+    }
+  }
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_sort(fempic_env* env, const fempic_particles* in, const fempic_particles* out, void* stream) {
+  if (!env || !in || !out) return fail(FEMPIC_EINVAL, "sort: NULL argument");
+  int rc = check_particles(in, true);
+  if (rc) return rc;
+  rc = check_particles(out, true);
+  if (rc) return rc;
+  if (in->n != out->n || in->n_species != out->n_species || (!in->n_cross) != (!out->n_cross))
+    return fail(FEMPIC_EINVAL, "sort: in/out particle sets differ in size, species or n_cross");
+  if (in->n == 0) return FEMPIC_OK;
+  if (in->x == out->x || in->tet == out->tet) return fail(FEMPIC_EINVAL, "sort: in and out overlap");
+  SortArgs A{};
+  rc = fill_species(in, 1.0, &A.sp);
+  if (rc) return rc;
+  for (int s = 0; s <= in->n_species; s++)
+    if (in->species_begin[s] != out->species_begin[s]) return fail(FEMPIC_EINVAL, "sort: species tables differ");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nt = env->h.nt;
+  const int64_t k = (int64_t)in->n_species * (nt + 1);
+  if (k >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "sort: too many (species, tet) keys");
+  if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "sort: more than 2^31 particles");
+  if (env->sort_cap < k) {
+    if (env->sort_counts) {
+      FEMPIC_CUDA(cudaStreamSynchronize(st));
+      cudaFree(env->sort_counts);
+      cudaFree(env->sort_offsets);
+      cudaFree(env->sort_sums);
+      env->sort_counts = env->sort_offsets = env->sort_sums = nullptr;
+      env->sort_cap = 0;
+    }
+    FEMPIC_CUDA(dalloc(&env->sort_counts, k));
+    FEMPIC_CUDA(dalloc(&env->sort_offsets, k));
+    FEMPIC_CUDA(dalloc(&env->sort_sums, k / (2 * kScan) + 1));
+    env->sort_cap = k;
+  }
+  const int64_t tiles = (k + 2 * kScan - 1) / (2 * kScan);
+  LaunchTimer lt(env, st, FEMPIC_K_SORT);
+  FEMPIC_CUDA(cudaMemsetAsync(env->sort_counts, 0, k * sizeof(int32_t), st));
+  k_sort_hist<<<blocks_for(in->n), kThreads, 0, st>>>(in->n, in->tet, A.sp, nt, env->sort_counts);
+  k_scan_tiles<<<(unsigned)tiles, kScan, 0, st>>>(k, env->sort_counts, env->sort_offsets, env->sort_sums);
+  k_scan_sums<<<1, kScan, 0, st>>>(tiles, env->sort_sums);
+  k_scan_add<<<blocks_for(k), kThreads, 0, st>>>(k, env->sort_offsets, env->sort_sums);
+  FEMPIC_CUDA(cudaMemsetAsync(env->sort_counts, 0, k * sizeof(int32_t), st));
+  A.n = in->n;
+  A.nt = nt;
+  A.vbytes = env->opt.precision == FEMPIC_FP64 ? 8 : 4;
+  A.x = in->x;
+  A.y = in->y;
+  A.z = in->z;
+  A.vx = in->vx;
+  A.vy = in->vy;
+  A.vz = in->vz;
+  A.tet = in->tet;
+  A.status = in->status;
+  A.ncross = in->n_cross;
+  A.ox = out->x;
+  A.oy = out->y;
+  A.oz = out->z;
+  A.ovx = out->vx;
+  A.ovy = out->vy;
+  A.ovz = out->vz;
+  A.otet = out->tet;
+  A.ostatus = out->status;
+  A.oncross = out->n_cross;
+  A.offsets = env->sort_offsets;
+  A.cursor = env->sort_counts;
+  k_sort_scatter<<<blocks_for(in->n), kThreads, 0, st>>>(A);
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}

@@ -1,0 +1,195 @@
+"""Thin PyTorch-facing wrapper over the C ABI: device memory and streams only.
+
+Every step of the particle path runs in the CUDA library (capi.py loads it
+and raises when it is missing); this module only allocates torch tensors and
+passes their device pointers and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import capi
+from .capi import FEMPIC_FP64, FEMPIC_MIXED  # noqa: F401
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class ParticleState:
+    """Particle SoA on the device: x, y, z (f64), vx, vy, vz (f64 or f32), tet
+    (i32), status (u8), n_cross (i32), plus the host species table."""
+
+    def __init__(self, x, y, z, vx, vy, vz, species_begin, q, m, w, tet=None, track_crossings=True):
+        self.x, self.y, self.z = x, y, z
+        self.vx, self.vy, self.vz = vx, vy, vz
+        n = x.shape[0]
+        dev = x.device
+        self.tet = tet if tet is not None else torch.full((n,), -1, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(n, dtype=torch.uint8, device=dev)
+        self.n_cross = torch.zeros(n, dtype=torch.int32, device=dev) if track_crossings else None
+        self.species_begin = np.ascontiguousarray(species_begin, dtype=np.int64)
+        self.q = np.ascontiguousarray(q, dtype=np.float64)
+        self.m = np.ascontiguousarray(m, dtype=np.float64)
+        self.w = np.ascontiguousarray(w, dtype=np.float64)
+
+    @classmethod
+    def from_host(cls, parts, precision: int, device="cuda", track_crossings=True, pin=False):
+        vdt = torch.float64 if precision == FEMPIC_FP64 else torch.float32
+
+        def d(a, dt):
+            t = torch.from_numpy(np.ascontiguousarray(a)).to(dt)
+            if pin:
+                t = t.pin_memory()
+            return t.to(device, non_blocking=pin)
+
+        return cls(d(parts.x, torch.float64), d(parts.y, torch.float64), d(parts.z, torch.float64),
+                   d(parts.vx, vdt), d(parts.vy, vdt), d(parts.vz, vdt), parts.species_begin, parts.q,
+                   parts.m, parts.w, track_crossings=track_crossings)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def cstruct(self) -> capi.fempic_particles:
+        p = capi.fempic_particles()
+        p.n = self.n
+        p.x, p.y, p.z = _ptr(self.x), _ptr(self.y), _ptr(self.z)
+        p.vx, p.vy, p.vz = _ptr(self.vx), _ptr(self.vy), _ptr(self.vz)
+        p.tet, p.status, p.n_cross = _ptr(self.tet), _ptr(self.status), _ptr(self.n_cross)
+        p.n_species = len(self.q)
+        p.species_begin = self.species_begin.ctypes.data
+        p.q, p.m, p.w = self.q.ctypes.data, self.m.ctypes.data, self.w.ctypes.data
+        return p
+
+    def empty_like(self) -> "ParticleState":
+        """Second buffer of the same shape and dtypes (the sort's output)."""
+        e = lambda t: None if t is None else torch.empty_like(t)
+        o = ParticleState(e(self.x), e(self.y), e(self.z), e(self.vx), e(self.vy), e(self.vz),
+                          self.species_begin, self.q, self.m, self.w, tet=e(self.tet),
+                          track_crossings=self.n_cross is not None)
+        return o
+
+    def swap(self, other: "ParticleState"):
+        """Exchange the device buffers of two states (after a sort into `other`)."""
+        for k in ("x", "y", "z", "vx", "vy", "vz", "tet", "status", "n_cross"):
+            a, b = getattr(self, k), getattr(other, k)
+            setattr(self, k, b)
+            setattr(other, k, a)
+
+    def to_numpy(self) -> dict:
+        out = {k: getattr(self, k).cpu().numpy() for k in ("x", "y", "z", "vx", "vy", "vz", "tet", "status")}
+        out["n_cross"] = None if self.n_cross is None else self.n_cross.cpu().numpy()
+        return out
+
+
+class FempicEnv:
+    """Owner of one fempic_env handle (mesh tables and edge accumulators)."""
+
+    def __init__(self, nodes: np.ndarray, tets: np.ndarray, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+                 precision: int = FEMPIC_FP64, max_crossings: int = 4096, wall_mode: int = 0):
+        nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        desc = capi.fempic_mesh_desc()
+        desc.n_nodes, desc.n_tets = nodes.shape[0], tets.shape[0]
+        desc.nodes_xyz, desc.tet_nodes = nodes.ctypes.data, tets.ctypes.data
+        for a in range(3):
+            desc.bbox_lo[a], desc.bbox_hi[a] = float(lo[a]), float(hi[a])
+        opt = capi.fempic_options(precision, max_crossings, wall_mode, 0)
+        torch.cuda.init()
+        self.precision = precision
+        self.h = capi.fempic_env_create(desc, opt)
+        counts = np.zeros(4, np.int64)
+        capi.fempic_env_query(self.h, counts.ctypes.data)
+        self.n_nodes, self.n_edges, self.n_faces, self.n_tets = (int(c) for c in counts)
+
+    @classmethod
+    def from_mesh(cls, mesh, **kw):
+        return cls(mesh.nodes, mesh.tets, mesh.lo, mesh.hi, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.fempic_env_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dof_dtype(self):
+        return torch.complex128 if self.precision == FEMPIC_FP64 else torch.complex64
+
+    def query(self) -> dict:
+        nt, ne, nf = self.n_tets, self.n_edges, self.n_faces
+        out = dict(tet_nodes=np.zeros((nt, 4), np.int32), edge_nodes=np.zeros((ne, 2), np.int32),
+                   face_nodes=np.zeros((nf, 3), np.int32), tet_edges=np.zeros((nt, 6), np.int32),
+                   tet_faces=np.zeros((nt, 4), np.int32), tet_nbr=np.zeros((nt, 4), np.int32))
+        counts = np.zeros(4, np.int64)
+        capi.fempic_env_query(self.h, counts.ctypes.data, *(out[k].ctypes.data for k in
+                                                            ("tet_nodes", "edge_nodes", "face_nodes",
+                                                             "tet_edges", "tet_faces", "tet_nbr")))
+        return out
+
+    def locate(self, st: ParticleState, stream=None):
+        capi.fempic_locate(self.h, st.cstruct(), _stream(stream))
+
+    def push_step(self, st: ParticleState, e_dof: torch.Tensor, b_dof: torch.Tensor, amp: float, omega0: float,
+                  t: float, dt: float, stream=None):
+        if e_dof.dtype != self.dof_dtype or b_dof.dtype != self.dof_dtype:
+            raise capi.FempicError(f"DoFs must be {self.dof_dtype} for this precision form")
+        if e_dof.numel() != self.n_edges or b_dof.numel() != self.n_faces or not e_dof.is_cuda:
+            raise capi.FempicError("DoF arrays must be device tensors of length n_edges / n_faces")
+        vdt = torch.float64 if self.precision == FEMPIC_FP64 else torch.float32
+        if st.vx.dtype != vdt:
+            raise capi.FempicError(f"velocities must be {vdt} for this precision form")
+        envl = capi.fempic_envelope(_ptr(e_dof), _ptr(b_dof), float(amp))
+        capi.fempic_push_step(self.h, st.cstruct(), envl, omega0, t, dt, _stream(stream))
+
+    def deposit(self, omega0: float, t_next: float, dG_out=None, G_cum_out=None, G_env_out=None, stream=None):
+        capi.fempic_deposit(self.h, omega0, t_next, _ptr(dG_out), _ptr(G_cum_out), _ptr(G_env_out),
+                            _stream(stream))
+
+    def reset_deposit(self, stream=None):
+        capi.fempic_reset_deposit(self.h, _stream(stream))
+
+    def nodal_charge(self, st: ParticleState, stream=None) -> torch.Tensor:
+        rho = torch.empty(self.n_nodes, dtype=torch.float64, device=st.x.device)
+        capi.fempic_nodal_charge(self.h, st.cstruct(), _ptr(rho), _stream(stream))
+        return rho
+
+    def sort(self, st: ParticleState, scratch: ParticleState, stream=None):
+        """Sort `st` by (species, tet) through `scratch`, then swap buffers so
+        `st` holds the sorted particles."""
+        capi.fempic_sort(self.h, st.cstruct(), scratch.cstruct(), _stream(stream))
+        st.swap(scratch)
+
+    def stats(self, stream=None) -> dict:
+        out = np.zeros(3, np.int64)
+        capi.fempic_stats(self.h, out.ctypes.data, _stream(stream))
+        return dict(crossings=int(out[0]), frozen=int(out[1]), steps=int(out[2]))
+
+    def profile(self, enable: bool):
+        """Start (clearing earlier records) or stop per-kernel event timing."""
+        capi.fempic_profile_enable(self.h, enable)
+
+    def profile_read(self) -> dict:
+        """Summed event time (ms) and launch count per kernel since profile(True)."""
+        ms = np.zeros(capi.FEMPIC_K_COUNT, np.float64)
+        cnt = np.zeros(capi.FEMPIC_K_COUNT, np.int64)
+        capi.fempic_profile_read(self.h, ms.ctypes.data, cnt.ctypes.data)
+        names = ("locate", "field", "push", "finalize", "charge", "sort")
+        return {nm: dict(ms=float(ms[i]), launches=int(cnt[i])) for i, nm in enumerate(names)}

@@ -1,0 +1,66 @@
+"""Host-side checks of the C ABI: the library builds, loads without a GPU,
+exports every function the header declares, and rejects bad arguments on the
+host before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2208_12795_gb300 import build, capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.load()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fempic_env.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fempic_\w+)\s*\(", txt)))
+
+
+def test_header_declares_what_binding_exports():
+    assert sorted(capi.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_null_arguments_rejected_on_host(lib):
+    assert lib.fempic_env_create(None, None, None) == capi.FEMPIC_EINVAL
+    assert "NULL" in capi.fempic_last_error()
+    assert lib.fempic_locate(None, None, None) == capi.FEMPIC_EINVAL
+    assert lib.fempic_push_step(None, None, None, 0.0, 0.0, 1e-9, None) == capi.FEMPIC_EINVAL
+    assert lib.fempic_deposit(None, 0.0, 0.0, None, None, None, None) == capi.FEMPIC_EINVAL
+    assert lib.fempic_stats(None, None, None) == capi.FEMPIC_EINVAL
+    lib.fempic_env_destroy(None)   # safe on NULL
+
+
+def test_bad_options_rejected_before_device(lib):
+    nodes = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    tets = np.array([[0, 1, 2, 3]], np.int32)
+    d = capi.fempic_mesh_desc(4, 1, nodes.ctypes.data, tets.ctypes.data, (C.c_double * 3)(0, 0, 0),
+                              (C.c_double * 3)(1, 1, 1))
+    h = C.c_void_p()
+    for opt in (capi.fempic_options(7, 10, 0, 0), capi.fempic_options(0, -1, 0, 0),
+                capi.fempic_options(0, 10, 5, 0), capi.fempic_options(0, 10, 0, 3)):
+        assert lib.fempic_env_create(C.byref(d), C.byref(opt), C.byref(h)) == capi.FEMPIC_EINVAL
+        assert not h.value
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(capi.FempicError):
+        capi._lib_backup = capi._lib
+        try:
+            capi._lib = None
+            capi.load(str(tmp_path / "nope.so"))
+        finally:
+            capi._lib = capi._lib_backup
