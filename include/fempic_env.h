@@ -186,6 +186,31 @@ int fempic_stats(fempic_env* env, int64_t* out3, void* stream);
  * Errors: EINVAL (mismatch), ENOMEM, ECUDA. */
 int fempic_sort(fempic_env* env, const fempic_particles* in, const fempic_particles* out, void* stream);
 
+/* Same sort as fempic_sort, for callers that must not allocate device
+ * memory once they are running (the paper has no counterpart; this is an
+ * integration entry point).  Examples: an application whose device memory is
+ * all handed out up front to its own pool allocator, so a cudaMalloc would
+ * fail or fragment that pool; a time-critical loop that cannot afford the
+ * device-wide synchronization cudaFree implies.  fempic_sort grows its
+ * counting scratch with cudaMalloc/cudaFree on demand; this entry point
+ * instead uses a fixed scratch area compiled into the library (about 16 MB
+ * of device memory that every GPU which loads the library keeps until the
+ * process exits), and calls no allocating routine.
+ *   Limit: n_species * (n_tets + 1) <= FEMPIC_SORT_NOALLOC_MAX_KEYS, else
+ *   FEMPIC_EINVAL with a message; n < 2^31.
+ *   Set-up: the first call on each device (with that device current) looks
+ *   up the scratch area's device address once; make that first call before
+ *   any stream capture.
+ *   Sharing: all calls in the process use the same scratch area, which keeps
+ *   the contents of the last call; each call clears what it needs.  Calls
+ *   whose work overlaps on the GPU (different streams, or different threads
+ *   without ordering) race on that area and give wrong results: order them.
+ * in, out, env, ordering and errors are as for fempic_sort; this call records
+ * no per-kernel timing. */
+#define FEMPIC_SORT_NOALLOC_MAX_KEYS (1 << 21)
+int fempic_sort_noalloc(fempic_env* env, const fempic_particles* in, const fempic_particles* out,
+                        void* stream);
+
 /* Kernel ids of the per-kernel timing below. */
 #define FEMPIC_K_LOCATE 0
 #define FEMPIC_K_FIELD 1      /* per-tet carrier restore + affine field coefficients */

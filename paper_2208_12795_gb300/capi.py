@@ -27,9 +27,10 @@ FEMPIC_WALL_ABSORB = 1
 # Every function declared in include/fempic_env.h.
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step",
            "fempic_deposit", "fempic_reset_deposit", "fempic_nodal_charge", "fempic_stats",
-           "fempic_sort", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
+           "fempic_sort", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
 FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT = range(6)
 FEMPIC_K_COUNT = 8
+FEMPIC_SORT_NOALLOC_MAX_KEYS = 1 << 21
 
 
 class fempic_mesh_desc(C.Structure):
@@ -82,6 +83,7 @@ def load(path: str = LIB_PATH):
         lib.fempic_nodal_charge.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p, C.c_void_p]
         lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_sort.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
+        lib.fempic_sort_noalloc.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
         lib.fempic_profile_enable.argtypes = [C.c_void_p, C.c_int32]
         lib.fempic_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_last_error.restype = C.c_char_p
@@ -142,6 +144,11 @@ def fempic_stats(env, out3, stream=0):
 
 def fempic_sort(env, parts_in: fempic_particles, parts_out: fempic_particles, stream=0):
     check(load().fempic_sort(env, C.byref(parts_in), C.byref(parts_out), stream), "fempic_sort")
+
+
+def fempic_sort_noalloc(env, parts_in: fempic_particles, parts_out: fempic_particles, stream=0):
+    check(load().fempic_sort_noalloc(env, C.byref(parts_in), C.byref(parts_out), stream),
+          "fempic_sort_noalloc")
 
 
 def fempic_profile_enable(env, enable: bool):

@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "fempic_internal.h"
@@ -1425,6 +1426,105 @@ extern "C" int fempic_sort(fempic_env* env, const fempic_particles* in, const fe
   A.oncross = out->n_cross;
   A.offsets = env->sort_offsets;
   A.cursor = env->sort_counts;
+  k_sort_scatter<<<blocks_for(in->n), kThreads, 0, st>>>(A);
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+// ------------------------------------------------- sort without allocation
+// Fixed scratch for fempic_sort_noalloc: per-key counters, per-key offsets
+// and per-tile sums, sized for FEMPIC_SORT_NOALLOC_MAX_KEYS keys.
+namespace {
+constexpr int64_t kNoAllocKeys = FEMPIC_SORT_NOALLOC_MAX_KEYS;
+constexpr int64_t kNoAllocTiles = kNoAllocKeys / (2 * kScan) + 1;
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) int32_t g_sort_noalloc_scratch[2 * kNoAllocKeys + kNoAllocTiles];
+
+namespace {
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code
+// the symbol names a host-side shadow, so the address must come from
+// cudaGetSymbolAddress, once per device, with that device current.
+int noalloc_scratch(int32_t** out) {
+  int dev = 0;
+  FEMPIC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(FEMPIC_EINVAL, "sort_noalloc: device index too large");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    FEMPIC_CUDA(cudaGetSymbolAddress(&p, g_sort_noalloc_scratch));
+    g_noalloc_addr[dev] = static_cast<int32_t*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return FEMPIC_OK;
+}
+}  // namespace
+
+extern "C" int fempic_sort_noalloc(fempic_env* env, const fempic_particles* in, const fempic_particles* out,
+                                   void* stream) {
+  if (!env || !in || !out) return fail(FEMPIC_EINVAL, "sort_noalloc: NULL argument");
+  int rc = check_particles(in, true);
+  if (rc) return rc;
+  rc = check_particles(out, true);
+  if (rc) return rc;
+  if (in->n != out->n || in->n_species != out->n_species || (!in->n_cross) != (!out->n_cross))
+    return fail(FEMPIC_EINVAL, "sort_noalloc: in/out particle sets differ in size, species or n_cross");
+  if (in->n == 0) return FEMPIC_OK;
+  if (in->x == out->x || in->tet == out->tet) return fail(FEMPIC_EINVAL, "sort_noalloc: in and out overlap");
+  SortArgs A{};
+  rc = fill_species(in, 1.0, &A.sp);
+  if (rc) return rc;
+  for (int s = 0; s <= in->n_species; s++)
+    if (in->species_begin[s] != out->species_begin[s])
+      return fail(FEMPIC_EINVAL, "sort_noalloc: species tables differ");
+  const int64_t nt = env->h.nt;
+  const int64_t k = (int64_t)in->n_species * (nt + 1);
+  if (k > kNoAllocKeys)
+    return fail(FEMPIC_EINVAL, "sort_noalloc: n_species * (n_tets + 1) = " + std::to_string(k) +
+                                   " exceeds the fixed scratch of " + std::to_string(kNoAllocKeys) +
+                                   " keys; use fempic_sort");
+  if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "sort_noalloc: more than 2^31 particles");
+  int32_t* base = nullptr;
+  rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  int32_t* counts = base;
+  int32_t* offsets = base + kNoAllocKeys;
+  int32_t* sums = base + 2 * kNoAllocKeys;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t tiles = (k + 2 * kScan - 1) / (2 * kScan);
+  FEMPIC_CUDA(cudaMemsetAsync(counts, 0, k * sizeof(int32_t), st));
+  k_sort_hist<<<blocks_for(in->n), kThreads, 0, st>>>(in->n, in->tet, A.sp, nt, counts);
+  k_scan_tiles<<<(unsigned)tiles, kScan, 0, st>>>(k, counts, offsets, sums);
+  k_scan_sums<<<1, kScan, 0, st>>>(tiles, sums);
+  k_scan_add<<<blocks_for(k), kThreads, 0, st>>>(k, offsets, sums);
+  FEMPIC_CUDA(cudaMemsetAsync(counts, 0, k * sizeof(int32_t), st));
+  A.n = in->n;
+  A.nt = nt;
+  A.vbytes = env->opt.precision == FEMPIC_FP64 ? 8 : 4;
+  A.x = in->x;
+  A.y = in->y;
+  A.z = in->z;
+  A.vx = in->vx;
+  A.vy = in->vy;
+  A.vz = in->vz;
+  A.tet = in->tet;
+  A.status = in->status;
+  A.ncross = in->n_cross;
+  A.ox = out->x;
+  A.oy = out->y;
+  A.oz = out->z;
+  A.ovx = out->vx;
+  A.ovy = out->vy;
+  A.ovz = out->vz;
+  A.otet = out->tet;
+  A.ostatus = out->status;
+  A.oncross = out->n_cross;
+  A.offsets = offsets;
+  A.cursor = counts;
   k_sort_scatter<<<blocks_for(in->n), kThreads, 0, st>>>(A);
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
