@@ -3,8 +3,7 @@
 //
 // Data layout on the device (per tet, indexed by tet id):
 //   geom64  double[12]  x0, grad l1, grad l2, grad l3        (96 B, FP64 form + location)
-//   x0v     double2 x2  x0 and padding                       (32 B, mixed form)
-//   g32     float[12]   grad l1..l3 in FP32, padded          (48 B, mixed form)
+//   geo32   float4 x4   x0 as an FP32 pair + grad l1..l3     (64 B, mixed form)
 //   tn      int4        sorted global node ids
 //   nb      int4        neighbour across local face k, or wall code
 //   te      int4 x 2    6 global edge ids, padded to 8
@@ -21,6 +20,7 @@
 // (mixed); tet i32; status u8; n_cross i32 (optional).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -86,8 +86,7 @@ struct PushArgs {
   double lo[3], hi[3];
   int64_t nt, ne;
   const double* geom64;
-  const double2* x0v;
-  const float4* g32;
+  const float4* geo32;
   const int4* tn;
   const int4* nb;
   const int4* te;
@@ -95,6 +94,8 @@ struct PushArgs {
   double* dG;                   // FP64 form accumulator [Ne]
   unsigned long long* dGq;      // mixed form accumulators [ns][Ne], units of 2^-48 (q w)
   unsigned long long* stats;    // [0] crossings, [1] frozen
+  int32_t* queue;               // mixed form: particles leaving their tet this step
+  int32_t* qcount;              // mixed form: queue length
 };
 
 __device__ __forceinline__ int species_of(const Species& sp, int64_t p) {
@@ -251,18 +252,18 @@ __global__ void __launch_bounds__(kThreads) k_field_fp64(int64_t nt, const doubl
   for (int i = 0; i < 5; i++) o[i] = make_double2(out[2 * i], out[2 * i + 1]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, const float4* __restrict__ g32,
+__global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, const float4* __restrict__ geo32,
                                                          const int4* __restrict__ te, const int4* __restrict__ tf,
                                                          const float2* __restrict__ edof,
                                                          const float2* __restrict__ fdof, float cre, float cim,
                                                          float4* __restrict__ field) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
-  const float4 a = g32[3 * t], b = g32[3 * t + 1], c = g32[3 * t + 2];
+  const float4 a = geo32[4 * t + 1], b = geo32[4 * t + 2], c = geo32[4 * t + 3];
   V3<float> g[4];
-  g[1] = {a.x, a.y, a.z};
-  g[2] = {a.w, b.x, b.y};
-  g[3] = {b.z, b.w, c.x};
+  g[1] = {a.z, a.w, b.x};
+  g[2] = {b.y, b.z, b.w};
+  g[3] = {c.x, c.y, c.z};
   g[0] = {-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z)};
   const int4 e0 = te[2 * t], e1 = te[2 * t + 1], f = tf[t];
   const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
@@ -405,9 +406,13 @@ __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
             entry = ent;
           } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
             const int code = -1 - nbt, ax = code >> 1, side = code & 1;
-            const double L = side ? A.hi[ax] : A.lo[ax];
-            b[ax] = 2.0 * L - b[ax];
-            vn[ax] = -vn[ax];
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+              if (c == ax) {
+                const double L = side ? A.hi[c] : A.lo[c];
+                b[c] = 2.0 * L - b[c];
+                vn[c] = -vn[c];
+              }
 #pragma unroll
             for (int i = 0; i < 4; i++) la[i] = lp[i];
             entry = kx;
@@ -447,12 +452,58 @@ __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
 // Q_0 = 2^24 - Q_1 - Q_2 - Q_3, so sum(Q) = 2^24 exactly and the per-segment
 // deposit g_ij = Qa_i Qb_j - Qa_j Qb_i is exact in int64: its edge divergence
 // is exactly 2^24 (Qb - Qa) at the nodes, so charge is conserved exactly.
-__device__ __forceinline__ void bary_q(const float4* __restrict__ g32, int64_t T, float dx, float dy, float dz,
-                                       int32_t Q[4]) {
-  const float4 a = __ldg(g32 + 3 * T), b = __ldg(g32 + 3 * T + 1), c = __ldg(g32 + 3 * T + 2);
-  const float l1 = __fmaf_rn(a.z, dz, __fmaf_rn(a.y, dy, __fmul_rn(a.x, dx)));
-  const float l2 = __fmaf_rn(b.y, dz, __fmaf_rn(b.x, dy, __fmul_rn(a.w, dx)));
-  const float l3 = __fmaf_rn(c.x, dz, __fmaf_rn(b.w, dy, __fmul_rn(b.z, dx)));
+//
+// GB300 issues FP64 at 1/64 of the FP32 rate, so the only FP64 arithmetic on
+// the common path is the position update r + dt v.  r - x0 is formed in FP32
+// from an exact split of each FP64 coordinate into a 24-bit head and the
+// rest (integer bit operations), minus the tet origin held as an FP32 pair.
+//
+// Mixed per-tet record geo32 (4 x float4 = 64 B):
+//   (x0h.x, x0h.y, x0h.z, x0l.x), (x0l.y, x0l.z, g1.x, g1.y),
+//   (g1.z, g2.x, g2.y, g2.z), (g3.x, g3.y, g3.z, 0)
+// with x0 = x0h + x0l and g_k = grad lambda_k.
+struct FF {
+  float hi, lo;
+};
+
+// r = hi + lo: hi keeps the leading 24 bits of the FP64 significand
+// (truncated, so exactly a float), lo the remaining 29 bits rounded to FP32.
+// |r| outside [2^-126, 2^128) maps to 0 (positions are never that small or
+// large; non-finite values are rejected before this is called).
+__device__ __forceinline__ FF split_f64(double r) {
+  const unsigned hi = (unsigned)__double2hiint(r), lo = (unsigned)__double2loint(r);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e < 897u || e > 1150u) return FF{0.f, 0.f};
+  const unsigned sign = hi & 0x80000000u;
+  const float fhi = __uint_as_float(sign | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  const float scale = e > 948u ? __uint_as_float((e - 948u) << 23) : 0.f;   // 2^(e - 1075)
+  const float flo = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), scale);
+  return FF{fhi, sign ? -flo : flo};
+}
+
+__device__ __forceinline__ bool finite_f64(double r) {
+  return (((unsigned)__double2hiint(r) >> 20) & 0x7ffu) != 0x7ffu;
+}
+
+struct Geo32 {
+  float4 a, b, c, d;
+};
+
+__device__ __forceinline__ Geo32 ld_geo(const float4* __restrict__ geo, int64_t T) {
+  return Geo32{__ldg(geo + 4 * T), __ldg(geo + 4 * T + 1), __ldg(geo + 4 * T + 2), __ldg(geo + 4 * T + 3)};
+}
+
+// d = r - x0 in FP32 from the split position and the split tet origin.
+__device__ __forceinline__ void dpos32(const Geo32& G, const FF r[3], float& dx, float& dy, float& dz) {
+  dx = __fadd_rn(__fsub_rn(r[0].hi, G.a.x), __fsub_rn(r[0].lo, G.a.w));
+  dy = __fadd_rn(__fsub_rn(r[1].hi, G.a.y), __fsub_rn(r[1].lo, G.b.x));
+  dz = __fadd_rn(__fsub_rn(r[2].hi, G.a.z), __fsub_rn(r[2].lo, G.b.y));
+}
+
+__device__ __forceinline__ void bary_q(const Geo32& G, float dx, float dy, float dz, int32_t Q[4]) {
+  const float l1 = __fmaf_rn(G.c.x, dz, __fmaf_rn(G.b.w, dy, __fmul_rn(G.b.z, dx)));
+  const float l2 = __fmaf_rn(G.c.w, dz, __fmaf_rn(G.c.z, dy, __fmul_rn(G.c.y, dx)));
+  const float l3 = __fmaf_rn(G.d.z, dz, __fmaf_rn(G.d.y, dy, __fmul_rn(G.d.x, dx)));
   // |lambda| <= 32 keeps Q_0 = 2^24 - Q_1 - Q_2 - Q_3 inside int32 for points
   // up to 32 tet diameters away (a clamped point still tracks cell by cell).
   Q[1] = __float2int_rn(__fmul_rn(fminf(fmaxf(l1, -kQClamp), kQClamp), kQScale));
@@ -461,20 +512,15 @@ __device__ __forceinline__ void bary_q(const float4* __restrict__ g32, int64_t T
   Q[0] = kQOne - Q[1] - Q[2] - Q[3];
 }
 
-struct X0 {
-  double x, y, z;
-};
-
-// x0v holds 2 double2 per tet: (x0x, x0y), (x0z, 0)
-__device__ __forceinline__ X0 ld_x0(const double2* x0v, int64_t T) {
-  const double2 a = __ldg(x0v + 2 * T), b = __ldg(x0v + 2 * T + 1);
-  return X0{a.x, a.y, b.x};
-}
-
-__device__ __forceinline__ void dpos(const X0& x0, const double r[3], float& dx, float& dy, float& dz) {
-  dx = __double2float_rn(__dsub_rn(r[0], x0.x));
-  dy = __double2float_rn(__dsub_rn(r[1], x0.y));
-  dz = __double2float_rn(__dsub_rn(r[2], x0.z));
+// Barycentric integers of the FP64 point r in tet T (shared with the nodal
+// charge so that the charge assignment is the very function the deposit uses).
+__device__ __forceinline__ void bary_q_at(const float4* __restrict__ geo, int64_t T, const double r[3],
+                                          int32_t Q[4]) {
+  const Geo32 G = ld_geo(geo, T);
+  const FF s[3] = {split_f64(r[0]), split_f64(r[1]), split_f64(r[2])};
+  float dx, dy, dz;
+  dpos32(G, s, dx, dy, dz);
+  bary_q(G, dx, dy, dz, Q);
 }
 
 __device__ __forceinline__ void gq(const int32_t a[4], const int32_t b[4], long long g[6]) {
@@ -494,16 +540,30 @@ __device__ __forceinline__ void depositq_atomic(const PushArgs& A, int32_t T, in
     if (g[e]) atomicAdd(base + eid[e], (unsigned long long)g[e]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A) {
+// Position after the push: the one FP64 operation of the common path.  Both
+// mixed kernels form it with this exact sequence, so the crossing kernel can
+// rebuild b from the stored start point and velocity bit for bit.
+__device__ __forceinline__ double advance(double a, float dt32, float v) {
+  return __dadd_rn(a, (double)__fmul_rn(dt32, v));
+}
+
+// Common path: gather, carrier, Boris, position update and the barycentric
+// integers of both ends in the home tet.  A particle that stays in its tet
+// deposits its one segment (warp-reduced) and is done; a particle that leaves
+// it stores its new velocity, keeps its start point, and is queued for
+// k_cross_mixed, which tracks it densely (about 1 in 8 particles per step on
+// the thermal cavity load, but nearly every warp holds one).
+__global__ void __launch_bounds__(kThreads, 4) k_push_mixed(PushArgs A) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  unsigned ncr = 0, nfrz = 0;
-  long long gh[6] = {0, 0, 0, 0, 0, 0};  // deposit of the first segment (home tet), reduced per warp
+  unsigned nfrz = 0;
+  long long gh[6] = {0, 0, 0, 0, 0, 0};
   int32_t key = -1 - lane;               // (home tet, species) run key; negative = no deposit
   int32_t Thome = 0;
   int shome = 0;
+  bool queue = false;
   if (p < A.n) {
-    int32_t T = A.tet[p];
+    const int32_t T = A.tet[p];
     if (T >= A.nt) {
       A.tet[p] = -1;
       A.status[p] = FEMPIC_P_LOST;
@@ -514,11 +574,12 @@ __global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A) {
       float* vxp = static_cast<float*>(A.vx);
       float* vyp = static_cast<float*>(A.vy);
       float* vzp = static_cast<float*>(A.vz);
-      double a[3] = {A.x[p], A.y[p], A.z[p]};
+      const double a[3] = {A.x[p], A.y[p], A.z[p]};
       const float v0 = vxp[p], v1 = vyp[p], v2 = vzp[p];
-      const X0 x0 = ld_x0(A.x0v, T);
+      const Geo32 G = ld_geo(A.geo32, T);
+      const FF rs[3] = {split_f64(a[0]), split_f64(a[1]), split_f64(a[2])};
       float dx, dy, dz;
-      dpos(x0, a, dx, dy, dz);
+      dpos32(G, rs, dx, dy, dz);
       const float4* F = static_cast<const float4*>(A.field) + 3 * (int64_t)T;
       const float4 f0 = __ldg(F), f1 = __ldg(F + 1), f2 = __ldg(F + 2);
       // f0 = (E0x, E0y, E0z, Wx), f1 = (Wy, Wz, B0x, B0y), f2 = (B0z, beta, -, -)
@@ -534,142 +595,52 @@ __global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A) {
       const float vpx = vmx + (vmy * tz - vmz * ty);
       const float vpy = vmy + (vmz * tx - vmx * tz);
       const float vpz = vmz + (vmx * ty - vmy * tx);
-      float vn[3] = {vmx + (vpy * sz - vpz * sy) + kq * Ex, vmy + (vpz * sx - vpx * sz) + kq * Ey,
-                     vmz + (vpx * sy - vpy * sx) + kq * Ez};
+      const float vn0 = vmx + (vpy * sz - vpz * sy) + kq * Ex;
+      const float vn1 = vmy + (vpz * sx - vpx * sz) + kq * Ey;
+      const float vn2 = vmz + (vpx * sy - vpy * sx) + kq * Ez;
       const float dt32 = (float)A.dt;
-      double b[3] = {__dadd_rn(a[0], (double)(dt32 * vn[0])), __dadd_rn(a[1], (double)(dt32 * vn[1])),
-                     __dadd_rn(a[2], (double)(dt32 * vn[2]))};
-      if (!(isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]) && isfinite(b[0]) && isfinite(b[1]) &&
-            isfinite(b[2]))) {
+      const double b0 = advance(a[0], dt32, vn0), b1 = advance(a[1], dt32, vn1), b2 = advance(a[2], dt32, vn2);
+      if (!(isfinite(vn0) && isfinite(vn1) && isfinite(vn2) && finite_f64(b0) && finite_f64(b1) &&
+            finite_f64(b2))) {
         A.status[p] = FEMPIC_P_NONFINITE;
         A.tet[p] = -2 - T;
         nfrz = 1;
       } else {
-        int32_t Qa[4], Qb[4], Qp[4];
-        bary_q(A.g32, T, dx, dy, dz, Qa);
+        int32_t Qa[4], Qb[4];
+        bary_q(G, dx, dy, dz, Qa);
+        const FF bs[3] = {split_f64(b0), split_f64(b1), split_f64(b2)};
         float bx, by, bz;
-        dpos(x0, b, bx, by, bz);
-        bary_q(A.g32, T, bx, by, bz, Qb);
-        Thome = T;
-        shome = s;
-        bool first = true;
-        int entry = -1;
-        int32_t nc = 0;
-        uint8_t st = FEMPIC_P_OK;
-        for (;;) {
-          int kx = -1;
-          float smin = INFINITY;
-#pragma unroll
-          for (int k = 0; k < 4; k++) {
-            if (k == entry || Qb[k] >= 0) continue;
-            const int32_t den = Qa[k] - Qb[k];
-            float sk = den > 0 ? (float)Qa[k] / (float)den : 0.0f;
-            if (sk < 0.0f) sk = 0.0f;
-            if (sk < smin) {
-              smin = sk;
-              kx = k;
-            }
-          }
-          const int32_t* Qend = Qb;
-          if (kx >= 0) {
-            // crossing point barycentrics: exact zero on the exit face, sum kept at 2^24
-            int last = -1;
-            int32_t acc = 0;
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-              if (i == kx) {
-                Qp[i] = 0;
-              } else {
-                Qp[i] = Qa[i] + __float2int_rn(smin * (float)(Qb[i] - Qa[i]));
-                acc += Qp[i];
-                last = i;
-              }
-            }
-            Qp[last] += kQOne - acc;
-            Qend = Qp;
-          }
-          long long g[6];
-          gq(Qa, Qend, g);
-          if (first) {
-#pragma unroll
-            for (int e = 0; e < 6; e++) gh[e] = g[e];
-            first = false;
-          } else {
-            depositq_atomic(A, T, s, g);
-          }
-          if (kx < 0) {
-            a[0] = b[0];
-            a[1] = b[1];
-            a[2] = b[2];
-            break;
-          }
-          nc++;
-          const double sd = (double)smin;
-#pragma unroll
-          for (int c = 0; c < 3; c++) a[c] = fma(sd, b[c] - a[c], a[c]);
-          if (nc > A.max_cross) {
-            st = FEMPIC_P_CAP;
-            break;
-          }
-          const int4 nbv = __ldg(&A.nb[T]);
-          const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
-          if (nbt >= 0) {
-            const int4 o4 = __ldg(&A.tn[T]), n4 = __ldg(&A.tn[nbt]);
-            const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nnd[4] = {n4.x, n4.y, n4.z, n4.w};
-            int ent = 0;
-#pragma unroll
-            for (int i2 = 0; i2 < 4; i2++) {
-              int32_t val = 0;
-              bool hit = false;
-#pragma unroll
-              for (int i = 0; i < 4; i++)
-                if (on[i] == nnd[i2]) {
-                  val = Qp[i];
-                  hit = true;
-                }
-              Qa[i2] = val;
-              if (!hit) ent = i2;
-            }
-            T = nbt;
-            entry = ent;
-          } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
-            const int code = -1 - nbt, ax = code >> 1, side = code & 1;
-            const double L = side ? A.hi[ax] : A.lo[ax];
-            b[ax] = 2.0 * L - b[ax];
-            vn[ax] = -vn[ax];
-#pragma unroll
-            for (int i = 0; i < 4; i++) Qa[i] = Qp[i];
-            entry = kx;
-          } else {
-            st = FEMPIC_P_ABSORBED;
-            break;
-          }
-          const X0 xc = ld_x0(A.x0v, T);
-          float ex, ey, ez;
-          dpos(xc, b, ex, ey, ez);
-          bary_q(A.g32, T, ex, ey, ez, Qb);
+        dpos32(G, bs, bx, by, bz);
+        bary_q(G, bx, by, bz, Qb);
+        vxp[p] = vn0;
+        vyp[p] = vn1;
+        vzp[p] = vn2;
+        if ((Qb[0] | Qb[1] | Qb[2] | Qb[3]) < 0) {
+          queue = true;        // leaves its tet: start point kept, tracked by k_cross_mixed
+        } else {
+          gq(Qa, Qb, gh);
+          key = T * kMaxSpecies + s;
+          Thome = T;
+          shome = s;
+          A.x[p] = b0;
+          A.y[p] = b1;
+          A.z[p] = b2;
         }
-        key = Thome * kMaxSpecies + shome;
-        A.x[p] = a[0];
-        A.y[p] = a[1];
-        A.z[p] = a[2];
-        vxp[p] = vn[0];
-        vyp[p] = vn[1];
-        vzp[p] = vn[2];
-        if (st != FEMPIC_P_OK) {
-          A.status[p] = st;
-          T = -2 - T;
-          nfrz = 1;
-        }
-        A.tet[p] = T;
-        if (A.ncross) A.ncross[p] += nc;
-        ncr = (unsigned)nc;
       }
     }
   }
-  // Warp segmented reduction of the home-tet deposit over runs of equal keys
-  // (particles are sorted by tet, so neighbouring lanes usually share one).
   const unsigned full = 0xffffffffu;
+  // warp-aggregated append to the crossing queue
+  const unsigned qmask = __ballot_sync(full, queue);
+  if (qmask) {
+    const int leader = __ffs(qmask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(A.qcount, __popc(qmask));
+    base = __shfl_sync(full, base, leader);
+    if (queue) A.queue[base + __popc(qmask & ((1u << lane) - 1u))] = (int32_t)p;
+  }
+  // Warp segmented reduction of the one-segment deposits over runs of equal
+  // keys (particles are sorted by tet, so neighbouring lanes usually share one).
   const int32_t prev = __shfl_up_sync(full, key, 1);
   const bool head = lane == 0 || prev != key;
   const unsigned heads = __ballot_sync(full, head);
@@ -691,6 +662,164 @@ __global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A) {
     for (int e = 0; e < 6; e++)
       if (gh[e]) atomicAdd(base + eid[e], (unsigned long long)gh[e]);
   }
+  nfrz = __reduce_add_sync(full, nfrz);
+  if (lane == 0 && nfrz) atomicAdd(A.stats + 1, (unsigned long long)nfrz);
+}
+
+// Crossing path, one queued particle per thread (grid-stride over the queue
+// filled by k_push_mixed in the same step): rebuild b, split the segment at
+// every face it crosses, deposit each in-tet piece, reflect or absorb at walls.
+__global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int32_t count = *A.qcount;
+  unsigned ncr = 0, nfrz = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const int64_t p = A.queue[i];
+    int32_t T = A.tet[p];
+    const int s = species_of(A.sp, p);
+    float* vxp = static_cast<float*>(A.vx);
+    float* vyp = static_cast<float*>(A.vy);
+    float* vzp = static_cast<float*>(A.vz);
+    double a0[3] = {A.x[p], A.y[p], A.z[p]};   // start of the current straight piece
+    float vn[3] = {vxp[p], vyp[p], vzp[p]};
+    const float dt32 = (float)A.dt;
+    double b[3] = {advance(a0[0], dt32, vn[0]), advance(a0[1], dt32, vn[1]), advance(a0[2], dt32, vn[2])};
+    int32_t Qa[4], Qb[4], Qp[4];
+    FF bs[3] = {split_f64(b[0]), split_f64(b[1]), split_f64(b[2])};
+    {
+      const Geo32 G = ld_geo(A.geo32, T);
+      const FF rs[3] = {split_f64(a0[0]), split_f64(a0[1]), split_f64(a0[2])};
+      float dx, dy, dz;
+      dpos32(G, rs, dx, dy, dz);
+      bary_q(G, dx, dy, dz, Qa);
+      dpos32(G, bs, dx, dy, dz);
+      bary_q(G, dx, dy, dz, Qb);
+    }
+    int entry = -1;
+    int32_t nc = 0;
+    uint8_t st = FEMPIC_P_OK;
+    float sacc = 0.f;          // current piece start = a0 + sacc (b - a0)
+    bool moved = true;         // false once frozen at a crossing point
+    bool reflected = false;
+    for (;;) {
+      int kx = -1;
+      float smin = INFINITY;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        if (k == entry || Qb[k] >= 0) continue;
+        const int32_t den = Qa[k] - Qb[k];
+        float sk = den > 0 ? (float)Qa[k] / (float)den : 0.0f;
+        if (sk < 0.0f) sk = 0.0f;
+        if (sk < smin) {
+          smin = sk;
+          kx = k;
+        }
+      }
+      long long g[6];
+      if (kx < 0) {
+        gq(Qa, Qb, g);
+        depositq_atomic(A, T, s, g);
+        break;
+      }
+      // crossing point barycentrics: exact zero on the exit face, sum kept at 2^24
+      const int last = kx == 3 ? 2 : 3;
+      int32_t acc = 0;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        if (j == kx) {
+          Qp[j] = 0;
+        } else {
+          Qp[j] = Qa[j] + __float2int_rn(smin * (float)(Qb[j] - Qa[j]));
+          acc += Qp[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (j == last) Qp[j] += kQOne - acc;
+      gq(Qa, Qp, g);
+      depositq_atomic(A, T, s, g);
+      nc++;
+      sacc = __fmaf_rn(smin, 1.0f - sacc, sacc);
+      if (nc > A.max_cross) {
+        st = FEMPIC_P_CAP;
+        moved = false;
+        break;
+      }
+      const int4 nbv = __ldg(&A.nb[T]);
+      const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+      if (nbt >= 0) {
+        const int4 o4 = __ldg(&A.tn[T]), n4 = __ldg(&A.tn[nbt]);
+        const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nnd[4] = {n4.x, n4.y, n4.z, n4.w};
+        int ent = 0;
+#pragma unroll
+        for (int i2 = 0; i2 < 4; i2++) {
+          int32_t val = 0;
+          bool hit = false;
+#pragma unroll
+          for (int j = 0; j < 4; j++)
+            if (on[j] == nnd[i2]) {
+              val = Qp[j];
+              hit = true;
+            }
+          Qa[i2] = val;
+          if (!hit) ent = i2;
+        }
+        T = nbt;
+        entry = ent;
+      } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
+        // materialize the wall point in FP64, mirror the rest of the step
+        const double sd = (double)sacc;
+#pragma unroll
+        for (int c = 0; c < 3; c++) a0[c] = fma(sd, b[c] - a0[c], a0[c]);
+        sacc = 0.f;
+        const int code = -1 - nbt, ax = code >> 1, side = code & 1;
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+          if (c == ax) {
+            const double L = side ? A.hi[c] : A.lo[c];
+            b[c] = 2.0 * L - b[c];
+            vn[c] = -vn[c];
+            bs[c] = split_f64(b[c]);
+          }
+        reflected = true;
+#pragma unroll
+        for (int j = 0; j < 4; j++) Qa[j] = Qp[j];
+        entry = kx;
+      } else {
+        st = FEMPIC_P_ABSORBED;
+        moved = false;
+        break;
+      }
+      const Geo32 Gc = ld_geo(A.geo32, T);
+      float ex, ey, ez;
+      dpos32(Gc, bs, ex, ey, ez);
+      bary_q(Gc, ex, ey, ez, Qb);
+    }
+    if (moved) {
+      A.x[p] = b[0];
+      A.y[p] = b[1];
+      A.z[p] = b[2];
+    } else {   // frozen at the last crossing point
+      const double sd = (double)sacc;
+      A.x[p] = fma(sd, b[0] - a0[0], a0[0]);
+      A.y[p] = fma(sd, b[1] - a0[1], a0[1]);
+      A.z[p] = fma(sd, b[2] - a0[2], a0[2]);
+    }
+    if (reflected) {
+      vxp[p] = vn[0];
+      vyp[p] = vn[1];
+      vzp[p] = vn[2];
+    }
+    if (st != FEMPIC_P_OK) {
+      A.status[p] = st;
+      T = -2 - T;
+      nfrz++;
+    }
+    A.tet[p] = T;
+    if (A.ncross) A.ncross[p] += nc;
+    ncr += (unsigned)nc;
+  }
+  const unsigned full = 0xffffffffu;
   ncr = __reduce_add_sync(full, ncr);
   nfrz = __reduce_add_sync(full, nfrz);
   if (lane == 0) {
@@ -747,8 +876,7 @@ struct ChargeArgs {
   int64_t nt;
   int32_t mixed;
   const double* geom64;
-  const double2* x0v;
-  const float4* g32;
+  const float4* geo32;
   const int4* tn;
   double* rho;
 };
@@ -765,10 +893,8 @@ __global__ void __launch_bounds__(kThreads) k_nodal_charge(ChargeArgs A) {
   const double r[3] = {A.x[p], A.y[p], A.z[p]};
   double lam[4];
   if (A.mixed) {
-    float dx, dy, dz;
-    dpos(ld_x0(A.x0v, T), r, dx, dy, dz);
     int32_t Q[4];
-    bary_q(A.g32, T, dx, dy, dz, Q);
+    bary_q_at(A.geo32, T, r, Q);
     for (int i = 0; i < 4; i++) lam[i] = (double)Q[i] * (1.0 / (double)kQOne);
   } else {
     bary64(A.geom64 + 12 * (int64_t)T, r, lam);
@@ -913,8 +1039,7 @@ struct fempic_env {
   fempic_options opt{};
   HostMesh h;
   double* geom64 = nullptr;
-  double2* x0v = nullptr;
-  float4* g32 = nullptr;
+  float4* geo32 = nullptr;
   int4* tn = nullptr;
   int4* nb = nullptr;
   int4* te = nullptr;
@@ -929,6 +1054,10 @@ struct fempic_env {
   int32_t* gtet = nullptr;
   double qw_last[kMaxSpecies] = {0};
   int32_t ns_last = 0;
+  int32_t* queue = nullptr;         // mixed form crossing queue [queue_cap]
+  int32_t* qcount = nullptr;        // its length
+  int64_t queue_cap = 0;
+  int num_sms = 1;
   int64_t steps = 0;
   // per-kernel event timing (measurement support)
   struct Rec {
@@ -980,8 +1109,8 @@ struct LaunchTimer {
 static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
-  void* ptrs[] = {e->geom64, e->x0v, e->g32, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
-                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums};
+  void* ptrs[] = {e->geom64, e->geo32, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->queue, e->qcount};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete e;
@@ -994,19 +1123,21 @@ extern "C" void fempic_env_destroy(fempic_env* env) { free_env(env); }
 static int upload(fempic_env* e) {
   const HostMesh& m = e->h;
   const int64_t nt = m.nt;
-  std::vector<double2> x0(2 * nt);
-  std::vector<float4> g(3 * nt);
+  std::vector<float4> geo(4 * nt);
   std::vector<int4> tn(nt), nb(nt), te(2 * nt), tf(nt);
   for (int64_t t = 0; t < nt; t++) {
     const double* G = &m.geom[12 * t];
-    x0[2 * t] = make_double2(G[0], G[1]);
-    x0[2 * t + 1] = make_double2(G[2], 0.0);
-    float gf[12];
-    for (int i = 0; i < 9; i++) gf[i] = (float)G[3 + i];
-    gf[9] = gf[10] = gf[11] = 0.f;
-    g[3 * t] = make_float4(gf[0], gf[1], gf[2], gf[3]);
-    g[3 * t + 1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
-    g[3 * t + 2] = make_float4(gf[8], gf[9], gf[10], gf[11]);
+    // mixed-form record: x0 as an FP32 pair (x0 = hi + lo) and FP32 gradients
+    float xh[3], xl[3], g[9];
+    for (int a = 0; a < 3; a++) {
+      xh[a] = (float)G[a];
+      xl[a] = (float)(G[a] - (double)xh[a]);
+    }
+    for (int i = 0; i < 9; i++) g[i] = (float)G[3 + i];
+    geo[4 * t] = make_float4(xh[0], xh[1], xh[2], xl[0]);
+    geo[4 * t + 1] = make_float4(xl[1], xl[2], g[0], g[1]);
+    geo[4 * t + 2] = make_float4(g[2], g[3], g[4], g[5]);
+    geo[4 * t + 3] = make_float4(g[6], g[7], g[8], 0.f);
     tn[t] = make_int4(m.tn[4 * t], m.tn[4 * t + 1], m.tn[4 * t + 2], m.tn[4 * t + 3]);
     nb[t] = make_int4(m.nb[4 * t], m.nb[4 * t + 1], m.nb[4 * t + 2], m.nb[4 * t + 3]);
     te[2 * t] = make_int4(m.te[6 * t], m.te[6 * t + 1], m.te[6 * t + 2], m.te[6 * t + 3]);
@@ -1014,15 +1145,13 @@ static int upload(fempic_env* e) {
     tf[t] = make_int4(m.tf[4 * t], m.tf[4 * t + 1], m.tf[4 * t + 2], m.tf[4 * t + 3]);
   }
   FEMPIC_CUDA(dalloc(&e->geom64, 12 * nt));
-  FEMPIC_CUDA(dalloc(&e->x0v, 2 * nt));
-  FEMPIC_CUDA(dalloc(&e->g32, 3 * nt));
+  FEMPIC_CUDA(dalloc(&e->geo32, 4 * nt));
   FEMPIC_CUDA(dalloc(&e->tn, nt));
   FEMPIC_CUDA(dalloc(&e->nb, nt));
   FEMPIC_CUDA(dalloc(&e->te, 2 * nt));
   FEMPIC_CUDA(dalloc(&e->tf, nt));
   FEMPIC_CUDA(cudaMemcpy(e->geom64, m.geom.data(), 12 * nt * sizeof(double), cudaMemcpyHostToDevice));
-  FEMPIC_CUDA(cudaMemcpy(e->x0v, x0.data(), 2 * nt * sizeof(double2), cudaMemcpyHostToDevice));
-  FEMPIC_CUDA(cudaMemcpy(e->g32, g.data(), 3 * nt * sizeof(float4), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->geo32, geo.data(), 4 * nt * sizeof(float4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->tn, tn.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->nb, nb.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->te, te.data(), 2 * nt * sizeof(int4), cudaMemcpyHostToDevice));
@@ -1058,7 +1187,8 @@ extern "C" int fempic_env_create(const fempic_mesh_desc* mesh, const fempic_opti
   fempic_env* e = new (std::nothrow) fempic_env();
   if (!e) return fail(FEMPIC_ENOMEM, "env_create: host allocation");
   e->opt = *opts;
-  if (cudaGetDevice(&e->device) != cudaSuccess) {
+  if (cudaGetDevice(&e->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device) != cudaSuccess) {
     delete e;
     return fail(FEMPIC_ECUDA, "env_create: no CUDA device");
   }
@@ -1156,6 +1286,21 @@ extern "C" int fempic_locate(fempic_env* env, const fempic_particles* p, void* s
   return FEMPIC_OK;
 }
 
+// Crossing queue of the mixed form: one slot per particle, grown on demand.
+static int ensure_queue(fempic_env* env, int64_t n, cudaStream_t st) {
+  if (!env->qcount) FEMPIC_CUDA(dalloc(&env->qcount, 1));
+  if (env->queue_cap >= n) return FEMPIC_OK;
+  if (env->queue) {
+    FEMPIC_CUDA(cudaStreamSynchronize(st));
+    cudaFree(env->queue);
+    env->queue = nullptr;
+    env->queue_cap = 0;
+  }
+  FEMPIC_CUDA(dalloc(&env->queue, n));
+  env->queue_cap = n;
+  return FEMPIC_OK;
+}
+
 static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
   if (env->dGq && env->dGq_species >= ns) return FEMPIC_OK;
   // The integer accumulators hold one step only; a larger species count
@@ -1198,7 +1343,7 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   {
   LaunchTimer lt(env, st, FEMPIC_K_FIELD);
   if (mixed) {
-    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->g32, env->te, env->tf,
+    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geo32, env->te, env->tf,
                                                       static_cast<const float2*>(envl->e_tilde),
                                                       static_cast<const float2*>(envl->b_tilde), (float)cre,
                                                       (float)cim, static_cast<float4*>(env->field));
@@ -1234,8 +1379,7 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   A.nt = nt;
   A.ne = env->h.ne;
   A.geom64 = env->geom64;
-  A.x0v = env->x0v;
-  A.g32 = env->g32;
+  A.geo32 = env->geo32;
   A.tn = env->tn;
   A.nb = env->nb;
   A.te = env->te;
@@ -1243,12 +1387,22 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   A.dG = env->dG;
   A.dGq = env->dGq;
   A.stats = env->stats;
+  if (mixed) {
+    rc = ensure_queue(env, p->n, st);
+    if (rc) return rc;
+    A.queue = env->queue;
+    A.qcount = env->qcount;
+    FEMPIC_CUDA(cudaMemsetAsync(env->qcount, 0, sizeof(int32_t), st));
+  }
   {
     LaunchTimer lt(env, st, FEMPIC_K_PUSH);
-    if (mixed)
+    if (mixed) {
       k_push_mixed<<<blocks_for(p->n), kThreads, 0, st>>>(A);
-    else
+      const unsigned cross_blocks = (unsigned)std::min<int64_t>(blocks_for(p->n), (int64_t)env->num_sms * 8);
+      k_cross_mixed<<<cross_blocks, kThreads, 0, st>>>(A);
+    } else {
       k_push_fp64<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+    }
   }
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
@@ -1309,8 +1463,7 @@ extern "C" int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, d
   A.nt = env->h.nt;
   A.mixed = env->opt.precision == FEMPIC_MIXED;
   A.geom64 = env->geom64;
-  A.x0v = env->x0v;
-  A.g32 = env->g32;
+  A.geo32 = env->geo32;
   A.tn = env->tn;
   A.rho = rho;
   {
