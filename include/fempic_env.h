@@ -117,6 +117,16 @@ typedef struct {
   double amp;                /* host scalar: slow envelope amplitude a(t) at this step */
 } fempic_envelope;
 
+typedef struct {
+  int64_t n;                 /* number of particles (same as the particle set) */
+  double* rx;                /* device f64 [n] adjoint of the positions */
+  double* ry;
+  double* rz;
+  void* vx;                  /* device [n] adjoint of the velocities: f64 (FP64 form) or f32 (mixed) */
+  void* vy;
+  void* vz;
+} fempic_adjoint;
+
 /* Derive the mesh tables (sorted tet nodes, edges, faces, neighbours, wall
  * codes, FP64 barycentric geometry, point-location grid) on the host and
  * upload them to the current device; allocate the edge accumulators dG and
@@ -169,10 +179,39 @@ int fempic_reset_deposit(fempic_env* env, void* stream);
  * Errors: EINVAL, ECUDA. */
 int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, double* rho, void* stream);
 
-/* Host-side counters accumulated by push_step since create / the last call:
- * out3 = {face crossings, particles frozen (any non-OK status), steps}.
+/* Host-side counters accumulated by push_step since create:
+ * out4 = {face crossings, particles frozen (any non-OK status), steps,
+ * staging waits that gave up}.  The last one counts CTAs of the staged push
+ * kernel whose bounded wait (about 1 s) for a bulk copy expired; they stop
+ * early, so any non-zero value means that step's results are incomplete.
  * Synchronizes the stream.  Errors: EINVAL, ECUDA. */
-int fempic_stats(fempic_env* env, int64_t* out3, void* stream);
+int fempic_stats(fempic_env* env, int64_t* out4, void* stream);
+
+/* Reverse mode of one fempic_push_step (gradients of a loss of the particle
+ * state after some steps, with respect to the envelope DoFs and the initial
+ * phase space; the paper has no adjoint, this differentiates its particle
+ * step: gather, carrier, Boris, position update and wall mirrors, Sec. III-D).
+ * `before` is the particle state the forward step started from and `after`
+ * the state it produced (only velocities and statuses of `after` are read:
+ * a velocity component with the opposite sign marks a wall mirror, a
+ * non-OK status a freeze).  On entry adj holds the adjoint of `after`; on
+ * exit the adjoint of `before`.  The derivative is that of the piecewise
+ * smooth map for the tet sequence the forward step took.  Particles frozen
+ * during the step get a zero adjoint.  e_grad (complex128 [Ne]) and b_grad
+ * (complex128 [Nf]) accumulate dL/dRe + j dL/dIm of the DoFs (added to, in
+ * FP64).  The mixed form differentiates its FP32 push in FP32 and keeps the
+ * position adjoint and the DoF gradients in FP64.  Stream-ordered; the
+ * field pre-pass of this step is recomputed.  Errors: EINVAL, ECUDA. */
+int fempic_push_step_adjoint(fempic_env* env, const fempic_particles* before, const fempic_particles* after,
+                             const fempic_envelope* envl, double omega0, double t, double dt,
+                             const fempic_adjoint* adj, void* e_grad, void* b_grad, void* stream);
+
+/* Total kinetic energy sum_p 1/2 m w |v|^2 over particles with tet >= 0,
+ * written to *ke (device f64 scalar, overwritten).  When seed is non-NULL it
+ * also receives the adjoint of that loss: vbar = m w v, rbar = 0 (0 for
+ * particles without a tet).  Stream-ordered.  Errors: EINVAL, ECUDA. */
+int fempic_kinetic_energy(fempic_env* env, const fempic_particles* p, double* ke, const fempic_adjoint* seed,
+                          void* stream);
 
 /* Keep the particle SoA ordered for coalesced, tet-local access (the
  * particle state of Sec. III-D in a GPU layout; no counterpart in the

@@ -657,3 +657,186 @@ double or_kinetic_energy(int64_t n, const double *vx, const double *vy, const do
   }
   return ke;
 }
+
+/* ------------------------------------------------------------------ JVP */
+/* Forward-mode tangent of one step, for checking gradients.  The values
+ * follow exactly the path of or_push_step (same tets, crossings and wall
+ * events); the tangents (dr, dv) and the tangent DoFs (de, db, complex
+ * interleaved like the DoFs) are propagated through every smooth operation:
+ *   dE~ = sum_e de_e W1_e(r) + sum_e e_e (dW1_e/dr) dr,
+ *     with (dW1_ij/dr) dr = (gl_i . dr) gl_j - (gl_j . dr) gl_i;
+ *   dB~ = sum_f db_f W2_f(r) + sum_f b_f (dW2_f/dr) dr,
+ *     with (dW2_ijl/dr) dr = 2 ((gl_i . dr) c_jl + (gl_j . dr) c_li + (gl_l . dr) c_ij);
+ *   the carrier product, every Boris operation, r + dt v, and at a wall the
+ *   mirrored component.  A particle frozen at a crossing point gets the
+ *   tangent of that point (through the tangent of the exit parameter).
+ * The tet sequence is held fixed: this is the derivative of the piecewise
+ * smooth map on the piece the values lie in. */
+static void tangent_fields(const omesh *m, int32_t T, const double *r, const double *dr, const double *e_dof,
+                           const double *b_dof, const double *de, const double *dbf, double *dEt, double *dBt) {
+  double W1[18], W2[12], lam[4];
+  or_whitney1(m, T, r, W1);
+  or_whitney2(m, T, r, W2);
+  or_bary(m, T, r, lam);
+  const double *g = m->gl + 12 * (int64_t)T;
+  double gd[4];
+  for (int k = 0; k < 4; k++) gd[k] = (g[3 * k] * dr[0] + g[3 * k + 1] * dr[1]) + g[3 * k + 2] * dr[2];
+  for (int i = 0; i < 6; i++) { dEt[i] = 0.0; dBt[i] = 0.0; }
+  for (int e = 0; e < 6; e++) {
+    int64_t id = m->te[6 * (int64_t)T + e];
+    int i = LE[e][0], j = LE[e][1];
+    for (int a = 0; a < 3; a++) {
+      double dW = gd[i] * g[3 * j + a] - gd[j] * g[3 * i + a];
+      dEt[a] += de[2 * id] * W1[3 * e + a] + e_dof[2 * id] * dW;
+      dEt[3 + a] += de[2 * id + 1] * W1[3 * e + a] + e_dof[2 * id + 1] * dW;
+    }
+  }
+  for (int f = 0; f < 4; f++) {
+    int64_t id = m->tf[4 * (int64_t)T + f];
+    int i = LF[f][0], j = LF[f][1], l = LF[f][2];
+    double cjl[3], cli[3], cij[3];
+    cross3(g + 3 * j, g + 3 * l, cjl);
+    cross3(g + 3 * l, g + 3 * i, cli);
+    cross3(g + 3 * i, g + 3 * j, cij);
+    for (int a = 0; a < 3; a++) {
+      double dW = 2.0 * ((gd[i] * cjl[a] + gd[j] * cli[a]) + gd[l] * cij[a]);
+      dBt[a] += dbf[2 * id] * W2[3 * f + a] + b_dof[2 * id] * dW;
+      dBt[3 + a] += dbf[2 * id + 1] * W2[3 * f + a] + b_dof[2 * id + 1] * dW;
+    }
+  }
+}
+
+static double dot3(const double *a, const double *b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
+static void step_one_jvp(const omesh *m, oparts *P, int64_t p, double kq, double qw, double cre, double cim,
+                         const double *e_dof, const double *b_dof, double dt, int32_t max_cross, int32_t wall_mode,
+                         double *dG, double *TR, double *TV, const double *de, const double *dbf) {
+  int32_t T = P->tet[p];
+  if (T < 0) return;
+  if (T >= m->nt) { P->tet[p] = -1; P->status[p] = OR_LOST; return; }
+  double a[3] = {P->x[p], P->y[p], P->z[p]};
+  double v[3] = {P->vx[p], P->vy[p], P->vz[p]};
+  double da[3] = {TR[3 * p], TR[3 * p + 1], TR[3 * p + 2]};
+  double dv[3] = {TV[3 * p], TV[3 * p + 1], TV[3 * p + 2]};
+  double Et[6], Bt[6], E[3], B[3], dEt[6], dBt[6], dE[3], dB[3];
+  or_gather(m, T, a, e_dof, b_dof, Et, Bt);
+  tangent_fields(m, T, a, da, e_dof, b_dof, de, dbf, dEt, dBt);
+  for (int c = 0; c < 3; c++) {
+    E[c] = cre * Et[c] - cim * Et[3 + c];
+    B[c] = cre * Bt[c] - cim * Bt[3 + c];
+    dE[c] = cre * dEt[c] - cim * dEt[3 + c];
+    dB[c] = cre * dBt[c] - cim * dBt[3 + c];
+  }
+  double vm[3], tau[3], s[3], vp[3], vpl[3], vn[3], b[3], cr[3];
+  double dvm[3], dtau[3], ds[3], dvp[3], dvpl[3], dvn[3], db[3], c1[3], c2[3];
+  for (int c = 0; c < 3; c++) { vm[c] = v[c] + kq * E[c]; dvm[c] = dv[c] + kq * dE[c]; }
+  for (int c = 0; c < 3; c++) { tau[c] = kq * B[c]; dtau[c] = kq * dB[c]; }
+  double t2 = (tau[0] * tau[0] + tau[1] * tau[1]) + tau[2] * tau[2];
+  double dt2 = 2.0 * dot3(tau, dtau);
+  double f = 2.0 / (1.0 + t2);
+  double df = -0.5 * f * f * dt2;
+  for (int c = 0; c < 3; c++) { s[c] = f * tau[c]; ds[c] = df * tau[c] + f * dtau[c]; }
+  cross3(vm, tau, cr);
+  cross3(dvm, tau, c1);
+  cross3(vm, dtau, c2);
+  for (int c = 0; c < 3; c++) { vp[c] = vm[c] + cr[c]; dvp[c] = dvm[c] + c1[c] + c2[c]; }
+  cross3(vp, s, cr);
+  cross3(dvp, s, c1);
+  cross3(vp, ds, c2);
+  for (int c = 0; c < 3; c++) { vpl[c] = vm[c] + cr[c]; dvpl[c] = dvm[c] + c1[c] + c2[c]; }
+  for (int c = 0; c < 3; c++) { vn[c] = vpl[c] + kq * E[c]; dvn[c] = dvpl[c] + kq * dE[c]; }
+  for (int c = 0; c < 3; c++) { b[c] = a[c] + dt * vn[c]; db[c] = da[c] + dt * dvn[c]; }
+  if (!finite3(vn) || !finite3(b)) { P->status[p] = OR_NONFINITE; P->tet[p] = -2 - T; return; }
+  double la[4], lb[4], lp[4];
+  or_bary(m, T, a, la);
+  int entry = -1;
+  int32_t ncross = 0;
+  for (;;) {
+    or_bary(m, T, b, lb);
+    int kx = -1;
+    double smin = INFINITY;
+    for (int k = 0; k < 4; k++) {
+      if (k == entry || !(lb[k] < 0.0)) continue;
+      double sk = la[k] / (la[k] - lb[k]);
+      if (sk < 0.0) sk = 0.0;
+      if (sk < smin) { smin = sk; kx = k; }
+    }
+    if (kx < 0) {
+      deposit_segment(m, T, la, lb, qw, dG);
+      for (int c = 0; c < 3; c++) { a[c] = b[c]; da[c] = db[c]; }
+      break;
+    }
+    /* tangent of the exit parameter s = la_k / (la_k - lb_k), with the
+     * barycentric tangents of the piece ends taken from their positions */
+    const double *g = m->gl + 12 * (int64_t)T;
+    double dla = (g[3 * kx] * da[0] + g[3 * kx + 1] * da[1]) + g[3 * kx + 2] * da[2];
+    double dlb = (g[3 * kx] * db[0] + g[3 * kx + 1] * db[1]) + g[3 * kx + 2] * db[2];
+    double den = la[kx] - lb[kx];
+    double dsm = (smin > 0.0) ? (dla * den - la[kx] * (dla - dlb)) / (den * den) : 0.0;
+    double pp[3], dpp[3];
+    for (int c = 0; c < 3; c++) {
+      pp[c] = a[c] + smin * (b[c] - a[c]);
+      dpp[c] = da[c] + dsm * (b[c] - a[c]) + smin * (db[c] - da[c]);
+    }
+    for (int i = 0; i < 4; i++) lp[i] = (i == kx) ? 0.0 : la[i] + smin * (lb[i] - la[i]);
+    deposit_segment(m, T, la, lp, qw, dG);
+    ncross++;
+    for (int c = 0; c < 3; c++) { a[c] = pp[c]; da[c] = dpp[c]; }
+    if (ncross > max_cross) { P->status[p] = OR_CAP; T = -2 - T; break; }
+    int32_t nbt = m->nb[4 * (int64_t)T + kx];
+    if (nbt >= 0) {
+      const int32_t *on = m->tn + 4 * (int64_t)T;
+      const int32_t *nn = m->tn + 4 * (int64_t)nbt;
+      int ent = -1;
+      for (int i2 = 0; i2 < 4; i2++) {
+        int hit = -1;
+        for (int i = 0; i < 4; i++)
+          if (on[i] == nn[i2]) hit = i;
+        if (hit >= 0) la[i2] = lp[hit];
+        else { la[i2] = 0.0; ent = i2; }
+      }
+      T = nbt;
+      entry = ent;
+    } else if (nbt <= -1 && nbt >= -6 && wall_mode == 0) {
+      int code = -1 - nbt, ax = code / 2, side = code % 2;
+      double L = side ? m->hi[ax] : m->lo[ax];
+      b[ax] = 2.0 * L - b[ax];
+      db[ax] = -db[ax];
+      vn[ax] = -vn[ax];
+      dvn[ax] = -dvn[ax];
+      for (int i = 0; i < 4; i++) la[i] = lp[i];
+      entry = kx;
+    } else {
+      P->status[p] = OR_ABSORBED;
+      T = -2 - T;
+      break;
+    }
+  }
+  P->x[p] = a[0]; P->y[p] = a[1]; P->z[p] = a[2];
+  P->vx[p] = vn[0]; P->vy[p] = vn[1]; P->vz[p] = vn[2];
+  P->tet[p] = T;
+  if (P->n_cross) P->n_cross[p] += ncross;
+  for (int c = 0; c < 3; c++) { TR[3 * p + c] = da[c]; TV[3 * p + c] = dv[c] = dvn[c]; }
+}
+
+/* One step of values and tangents.  tr, tv: [n][3] tangents of position and
+ * velocity, updated in place; de, db: tangent DoFs (complex interleaved). */
+int or_push_step_jvp(const void *h, int64_t n, double *x, double *y, double *z, double *vx, double *vy,
+                     double *vz, int32_t *tet, uint8_t *status, int32_t *n_cross, int32_t n_species,
+                     const int64_t *species_begin, const double *q, const double *mass, const double *w,
+                     const double *e_dof, const double *b_dof, double amp, double omega0, double t,
+                     double dt, int32_t max_cross, int32_t wall_mode, double *dG, double *tr, double *tv,
+                     const double *de, const double *db) {
+  const omesh *m = (const omesh *)h;
+  oparts P = {x, y, z, vx, vy, vz, tet, status, n_cross};
+  double phi = omega0 * t;
+  double cre = amp * cos(phi), cim = amp * sin(phi);
+  for (int32_t s = 0; s < n_species; s++) {
+    double kq = ((q[s] / mass[s]) * dt) * 0.5;
+    double qw = q[s] * w[s];
+    int64_t p1 = species_begin[s + 1] < n ? species_begin[s + 1] : n;
+    for (int64_t p = species_begin[s]; p < p1; p++)
+      step_one_jvp(m, &P, p, kq, qw, cre, cim, e_dof, b_dof, dt, max_cross, wall_mode, dG, tr, tv, de, db);
+  }
+  return 0;
+}

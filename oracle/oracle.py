@@ -59,6 +59,11 @@ def _load():
                                      [_i32, _u8, C.c_void_p, C.c_int32, _i64, _d, _d, _d, _d, _d,
                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
                                       C.c_int32, _d])
+        lib.or_push_step_jvp.restype = C.c_int
+        lib.or_push_step_jvp.argtypes = ([C.c_void_p, C.c_int64] + [_d] * 6 +
+                                         [_i32, _u8, C.c_void_p, C.c_int32, _i64, _d, _d, _d, _d, _d,
+                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                          C.c_int32, _d, _d, _d, _d, _d])
         lib.or_nodal_charge.argtypes = [C.c_void_p, C.c_int64, _d, _d, _d, _i32, C.c_int32, _i64, _d,
                                         _d, _d]
         lib.or_edge_divergence.argtypes = [C.c_void_p, _d, _d]
@@ -200,6 +205,36 @@ def push_step(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, t, d
                           st.n_cross.ctypes.data_as(C.c_void_p), len(st.q), st.species_begin, st.q,
                           st.m, st.w, e, b, float(amp), float(omega0), float(t), float(dt),
                           int(max_crossings), int(wall_mode), dG)
+
+
+def push_step_jvp(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, t, dt, dG, tr, tv, de, db,
+                  max_crossings=4096, wall_mode=0):
+    """One oracle step of values and forward-mode tangents.
+
+    tr, tv: float64 [n, 3] tangents of position and velocity (updated in
+    place); de, db: complex tangent DoFs."""
+    e = _f64(np.ascontiguousarray(e_dof, np.complex128).view(np.float64))
+    b = _f64(np.ascontiguousarray(b_dof, np.complex128).view(np.float64))
+    tde = _f64(np.ascontiguousarray(de, np.complex128).view(np.float64))
+    tdb = _f64(np.ascontiguousarray(db, np.complex128).view(np.float64))
+    assert tr.dtype == np.float64 and tr.flags.c_contiguous and tr.shape == (st.n, 3)
+    assert tv.dtype == np.float64 and tv.flags.c_contiguous and tv.shape == (st.n, 3)
+    mesh.lib.or_push_step_jvp(mesh.h, st.n, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.tet, st.status,
+                              st.n_cross.ctypes.data_as(C.c_void_p), len(st.q), st.species_begin, st.q,
+                              st.m, st.w, e, b, float(amp), float(omega0), float(t), float(dt),
+                              int(max_crossings), int(wall_mode), dG, tr.reshape(-1), tv.reshape(-1),
+                              tde, tdb)
+
+
+def kinetic_energy_jvp(st: OracleState, tv):
+    """Tangent of the total kinetic energy sum 1/2 m w |v|^2 over active particles."""
+    out = 0.0
+    for s in range(len(st.q)):
+        a, b = int(st.species_begin[s]), int(st.species_begin[s + 1])
+        act = st.tet[a:b] >= 0
+        v = np.stack([st.vx[a:b], st.vy[a:b], st.vz[a:b]], 1)[act]
+        out += st.m[s] * st.w[s] * float(np.sum(v * tv[a:b][act]))
+    return out
 
 
 def envelope_frame(G, omega0, t):

@@ -27,7 +27,7 @@ FEMPIC_WALL_ABSORB = 1
 # Every function declared in include/fempic_env.h.
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step",
            "fempic_deposit", "fempic_reset_deposit", "fempic_nodal_charge", "fempic_stats",
-           "fempic_sort", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
+           "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
 FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT = range(6)
 FEMPIC_K_COUNT = 8
 FEMPIC_SORT_NOALLOC_MAX_KEYS = 1 << 21
@@ -48,6 +48,11 @@ class fempic_particles(C.Structure):
                 ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p), ("tet", C.c_void_p),
                 ("status", C.c_void_p), ("n_cross", C.c_void_p), ("n_species", C.c_int32),
                 ("species_begin", C.c_void_p), ("q", C.c_void_p), ("m", C.c_void_p), ("w", C.c_void_p)]
+
+
+class fempic_adjoint(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rx", C.c_void_p), ("ry", C.c_void_p), ("rz", C.c_void_p),
+                ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p)]
 
 
 class fempic_envelope(C.Structure):
@@ -82,6 +87,11 @@ def load(path: str = LIB_PATH):
         lib.fempic_reset_deposit.argtypes = [C.c_void_p, C.c_void_p]
         lib.fempic_nodal_charge.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p, C.c_void_p]
         lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_push_step_adjoint.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles),
+                                                 P(fempic_envelope), C.c_double, C.c_double, C.c_double,
+                                                 P(fempic_adjoint), C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_kinetic_energy.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p, C.c_void_p,
+                                              C.c_void_p]
         lib.fempic_sort.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
         lib.fempic_sort_noalloc.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
         lib.fempic_profile_enable.argtypes = [C.c_void_p, C.c_int32]
@@ -138,8 +148,20 @@ def fempic_nodal_charge(env, parts: fempic_particles, rho, stream=0):
     check(load().fempic_nodal_charge(env, C.byref(parts), rho, stream), "fempic_nodal_charge")
 
 
-def fempic_stats(env, out3, stream=0):
-    check(load().fempic_stats(env, out3, stream), "fempic_stats")
+def fempic_stats(env, out4, stream=0):
+    check(load().fempic_stats(env, out4, stream), "fempic_stats")
+
+
+def fempic_push_step_adjoint(env, before: fempic_particles, after: fempic_particles, envl: fempic_envelope,
+                             omega0, t, dt, adj: fempic_adjoint, e_grad, b_grad, stream=0):
+    check(load().fempic_push_step_adjoint(env, C.byref(before), C.byref(after), C.byref(envl), float(omega0),
+                                          float(t), float(dt), C.byref(adj), e_grad, b_grad, stream),
+          "fempic_push_step_adjoint")
+
+
+def fempic_kinetic_energy(env, parts: fempic_particles, ke, seed=None, stream=0):
+    check(load().fempic_kinetic_energy(env, C.byref(parts), ke, C.byref(seed) if seed is not None else None,
+                                       stream), "fempic_kinetic_energy")
 
 
 def fempic_sort(env, parts_in: fempic_particles, parts_out: fempic_particles, stream=0):

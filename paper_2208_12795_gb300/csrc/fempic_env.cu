@@ -3,7 +3,9 @@
 //
 // Data layout on the device (per tet, indexed by tet id):
 //   geom64  double[12]  x0, grad l1, grad l2, grad l3        (96 B, FP64 form + location)
-//   geo32   float4 x4   x0 as an FP32 pair + grad l1..l3     (64 B, mixed form)
+//   tetrec  float4 x8   mixed form, one 128 B line per tet: x0 as an FP32 pair
+//                       and grad l1..l3 (64 B), the per-step affine field
+//                       (48 B, written by k_field_f32), neighbours (16 B)
 //   tn      int4        sorted global node ids
 //   nb      int4        neighbour across local face k, or wall code
 //   te      int4 x 2    6 global edge ids, padded to 8
@@ -86,16 +88,15 @@ struct PushArgs {
   double lo[3], hi[3];
   int64_t nt, ne;
   const double* geom64;
-  const float4* geo32;
+  const float4* tetrec;
   const int4* tn;
   const int4* nb;
   const int4* te;
   const void* field;
   double* dG;                   // FP64 form accumulator [Ne]
   unsigned long long* dGq;      // mixed form accumulators [ns][Ne], units of 2^-48 (q w)
-  unsigned long long* stats;    // [0] crossings, [1] frozen
-  int32_t* queue;               // mixed form: particles leaving their tet this step
-  int32_t* qcount;              // mixed form: queue length
+  unsigned long long* stats;    // [0] crossings, [1] frozen, [2] staging wait timeouts
+  uint32_t* leave;              // mixed form: bit (p % 32) of word p / 32 = particle p leaves its tet
 };
 
 __device__ __forceinline__ int species_of(const Species& sp, int64_t p) {
@@ -252,14 +253,13 @@ __global__ void __launch_bounds__(kThreads) k_field_fp64(int64_t nt, const doubl
   for (int i = 0; i < 5; i++) o[i] = make_double2(out[2 * i], out[2 * i + 1]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, const float4* __restrict__ geo32,
+__global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, float4* __restrict__ rec,
                                                          const int4* __restrict__ te, const int4* __restrict__ tf,
                                                          const float2* __restrict__ edof,
-                                                         const float2* __restrict__ fdof, float cre, float cim,
-                                                         float4* __restrict__ field) {
+                                                         const float2* __restrict__ fdof, float cre, float cim) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
-  const float4 a = geo32[4 * t + 1], b = geo32[4 * t + 2], c = geo32[4 * t + 3];
+  const float4 a = rec[8 * t + 1], b = rec[8 * t + 2], c = rec[8 * t + 3];
   V3<float> g[4];
   g[1] = {a.z, a.w, b.x};
   g[2] = {b.y, b.z, b.w};
@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, const float4
   const int32_t fid[4] = {f.x, f.y, f.z, f.w};
   float out[10];
   field_coeffs<float, float2>(g, edof, fdof, eid, fid, cre, cim, out);
-  field[3 * t] = make_float4(out[0], out[1], out[2], out[3]);
-  field[3 * t + 1] = make_float4(out[4], out[5], out[6], out[7]);
-  field[3 * t + 2] = make_float4(out[8], out[9], 0.f, 0.f);
+  rec[8 * t + 4] = make_float4(out[0], out[1], out[2], out[3]);
+  rec[8 * t + 5] = make_float4(out[4], out[5], out[6], out[7]);
+  rec[8 * t + 6] = make_float4(out[8], out[9], 0.f, 0.f);
 }
 
 // ------------------------------------------------------------ FP64 push
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
 // from an exact split of each FP64 coordinate into a 24-bit head and the
 // rest (integer bit operations), minus the tet origin held as an FP32 pair.
 //
-// Mixed per-tet record geo32 (4 x float4 = 64 B):
+// Mixed per-tet record tetrec (8 x float4 = 128 B), first 64 B:
 //   (x0h.x, x0h.y, x0h.z, x0l.x), (x0l.y, x0l.z, g1.x, g1.y),
 //   (g1.z, g2.x, g2.y, g2.z), (g3.x, g3.y, g3.z, 0)
 // with x0 = x0h + x0l and g_k = grad lambda_k.
@@ -489,8 +489,8 @@ struct Geo32 {
   float4 a, b, c, d;
 };
 
-__device__ __forceinline__ Geo32 ld_geo(const float4* __restrict__ geo, int64_t T) {
-  return Geo32{__ldg(geo + 4 * T), __ldg(geo + 4 * T + 1), __ldg(geo + 4 * T + 2), __ldg(geo + 4 * T + 3)};
+__device__ __forceinline__ Geo32 ld_geo(const float4* __restrict__ rec, int64_t T) {
+  return Geo32{__ldg(rec + 8 * T), __ldg(rec + 8 * T + 1), __ldg(rec + 8 * T + 2), __ldg(rec + 8 * T + 3)};
 }
 
 // d = r - x0 in FP32 from the split position and the split tet origin.
@@ -547,102 +547,110 @@ __device__ __forceinline__ double advance(double a, float dt32, float v) {
   return __dadd_rn(a, (double)__fmul_rn(dt32, v));
 }
 
-// Common path: gather, carrier, Boris, position update and the barycentric
-// integers of both ends in the home tet.  A particle that stays in its tet
-// deposits its one segment (warp-reduced) and is done; a particle that leaves
-// it stores its new velocity, keeps its start point, and is queued for
-// k_cross_mixed, which tracks it densely (about 1 in 8 particles per step on
-// the thermal cavity load, but nearly every warp holds one).
-__global__ void __launch_bounds__(kThreads, 4) k_push_mixed(PushArgs A) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  unsigned nfrz = 0;
-  long long gh[6] = {0, 0, 0, 0, 0, 0};
-  int32_t key = -1 - lane;               // (home tet, species) run key; negative = no deposit
-  int32_t Thome = 0;
-  int shome = 0;
-  bool queue = false;
-  if (p < A.n) {
-    const int32_t T = A.tet[p];
-    if (T >= A.nt) {
-      A.tet[p] = -1;
-      A.status[p] = FEMPIC_P_LOST;
-      nfrz = 1;
-    } else if (T >= 0) {
-      const int s = species_of(A.sp, p);
-      const float kq = (float)A.sp.kq[s];
-      float* vxp = static_cast<float*>(A.vx);
-      float* vyp = static_cast<float*>(A.vy);
-      float* vzp = static_cast<float*>(A.vz);
-      const double a[3] = {A.x[p], A.y[p], A.z[p]};
-      const float v0 = vxp[p], v1 = vyp[p], v2 = vzp[p];
-      const Geo32 G = ld_geo(A.geo32, T);
-      const FF rs[3] = {split_f64(a[0]), split_f64(a[1]), split_f64(a[2])};
-      float dx, dy, dz;
-      dpos32(G, rs, dx, dy, dz);
-      const float4* F = static_cast<const float4*>(A.field) + 3 * (int64_t)T;
-      const float4 f0 = __ldg(F), f1 = __ldg(F + 1), f2 = __ldg(F + 2);
-      // f0 = (E0x, E0y, E0z, Wx), f1 = (Wy, Wz, B0x, B0y), f2 = (B0z, beta, -, -)
-      const float Ex = f0.x + (dy * f1.y - dz * f1.x);
-      const float Ey = f0.y + (dz * f0.w - dx * f1.y);
-      const float Ez = f0.z + (dx * f1.x - dy * f0.w);
-      const float Bx = f1.z + f2.y * dx, By = f1.w + f2.y * dy, Bz = f2.x + f2.y * dz;
-      const float vmx = v0 + kq * Ex, vmy = v1 + kq * Ey, vmz = v2 + kq * Ez;
-      const float tx = kq * Bx, ty = kq * By, tz = kq * Bz;
-      const float t2 = tx * tx + ty * ty + tz * tz;
-      const float f = 2.0f / (1.0f + t2);
-      const float sx = f * tx, sy = f * ty, sz = f * tz;
-      const float vpx = vmx + (vmy * tz - vmz * ty);
-      const float vpy = vmy + (vmz * tx - vmx * tz);
-      const float vpz = vmz + (vmx * ty - vmy * tx);
-      const float vn0 = vmx + (vpy * sz - vpz * sy) + kq * Ex;
-      const float vn1 = vmy + (vpz * sx - vpx * sz) + kq * Ey;
-      const float vn2 = vmz + (vpx * sy - vpy * sx) + kq * Ez;
-      const float dt32 = (float)A.dt;
-      const double b0 = advance(a[0], dt32, vn0), b1 = advance(a[1], dt32, vn1), b2 = advance(a[2], dt32, vn2);
-      if (!(isfinite(vn0) && isfinite(vn1) && isfinite(vn2) && finite_f64(b0) && finite_f64(b1) &&
-            finite_f64(b2))) {
-        A.status[p] = FEMPIC_P_NONFINITE;
-        A.tet[p] = -2 - T;
-        nfrz = 1;
-      } else {
-        int32_t Qa[4], Qb[4];
-        bary_q(G, dx, dy, dz, Qa);
-        const FF bs[3] = {split_f64(b0), split_f64(b1), split_f64(b2)};
-        float bx, by, bz;
-        dpos32(G, bs, bx, by, bz);
-        bary_q(G, bx, by, bz, Qb);
-        vxp[p] = vn0;
-        vyp[p] = vn1;
-        vzp[p] = vn2;
-        if ((Qb[0] | Qb[1] | Qb[2] | Qb[3]) < 0) {
-          queue = true;        // leaves its tet: start point kept, tracked by k_cross_mixed
-        } else {
-          gq(Qa, Qb, gh);
-          key = T * kMaxSpecies + s;
-          Thome = T;
-          shome = s;
-          A.x[p] = b0;
-          A.y[p] = b1;
-          A.z[p] = b2;
-        }
-      }
-    }
+// Per-lane result of the common path, consumed by the warp epilogue.
+struct LaneOut {
+  long long gh[6];     // one-segment deposit (home tet)
+  int4 e0, e1;         // edge ids of the home tet (loaded with its record)
+  int32_t key;         // (home tet, species) run key; negative = no deposit
+  int32_t Thome;
+  int shome;
+  bool queue;          // leaves its tet: marked for k_cross_mixed
+  unsigned nfrz;
+};
+
+__device__ __forceinline__ void lane_init(LaneOut& o, int lane) {
+#pragma unroll
+  for (int e = 0; e < 6; e++) o.gh[e] = 0;
+  o.key = -1 - lane;
+  o.Thome = 0;
+  o.shome = 0;
+  o.queue = false;
+  o.nfrz = 0;
+}
+
+// Common path of one particle with its state already loaded: gather, carrier,
+// Boris, position update and the barycentric integers of both ends in the
+// home tet.  A particle that stays in its tet writes its new state and keeps
+// its one-segment deposit for the warp reduction; a particle that leaves it
+// stores its new velocity, keeps its start point, and is marked in the leave
+// mask for k_cross_mixed.
+__device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int32_t T, double ax, double ay,
+                                               double az, float v0, float v1, float v2, LaneOut& o) {
+  if (T >= A.nt) {
+    A.tet[p] = -1;
+    A.status[p] = FEMPIC_P_LOST;
+    o.nfrz = 1;
+    return;
   }
+  if (T < 0) return;
+  const int s = species_of(A.sp, p);
+  const float kq = (float)A.sp.kq[s];
+  const float4* R = A.tetrec + 8 * (int64_t)T;
+  const Geo32 G = Geo32{__ldg(R), __ldg(R + 1), __ldg(R + 2), __ldg(R + 3)};
+  const float4 f0 = __ldg(R + 4), f1 = __ldg(R + 5), f2 = __ldg(R + 6);
+  o.e0 = __ldg(&A.te[2 * (int64_t)T]);
+  o.e1 = __ldg(&A.te[2 * (int64_t)T + 1]);
+  const FF rs[3] = {split_f64(ax), split_f64(ay), split_f64(az)};
+  float dx, dy, dz;
+  dpos32(G, rs, dx, dy, dz);
+  // f0 = (E0x, E0y, E0z, Wx), f1 = (Wy, Wz, B0x, B0y), f2 = (B0z, beta, -, -)
+  const float Ex = f0.x + (dy * f1.y - dz * f1.x);
+  const float Ey = f0.y + (dz * f0.w - dx * f1.y);
+  const float Ez = f0.z + (dx * f1.x - dy * f0.w);
+  const float Bx = f1.z + f2.y * dx, By = f1.w + f2.y * dy, Bz = f2.x + f2.y * dz;
+  const float vmx = v0 + kq * Ex, vmy = v1 + kq * Ey, vmz = v2 + kq * Ez;
+  const float tx = kq * Bx, ty = kq * By, tz = kq * Bz;
+  const float t2 = tx * tx + ty * ty + tz * tz;
+  const float f = 2.0f / (1.0f + t2);
+  const float sx = f * tx, sy = f * ty, sz = f * tz;
+  const float vpx = vmx + (vmy * tz - vmz * ty);
+  const float vpy = vmy + (vmz * tx - vmx * tz);
+  const float vpz = vmz + (vmx * ty - vmy * tx);
+  const float vn0 = vmx + (vpy * sz - vpz * sy) + kq * Ex;
+  const float vn1 = vmy + (vpz * sx - vpx * sz) + kq * Ey;
+  const float vn2 = vmz + (vpx * sy - vpy * sx) + kq * Ez;
+  const float dt32 = (float)A.dt;
+  const double b0 = advance(ax, dt32, vn0), b1 = advance(ay, dt32, vn1), b2 = advance(az, dt32, vn2);
+  if (!(isfinite(vn0) && isfinite(vn1) && isfinite(vn2) && finite_f64(b0) && finite_f64(b1) && finite_f64(b2))) {
+    A.status[p] = FEMPIC_P_NONFINITE;
+    A.tet[p] = -2 - T;
+    o.nfrz = 1;
+    return;
+  }
+  int32_t Qa[4], Qb[4];
+  bary_q(G, dx, dy, dz, Qa);
+  const FF bs[3] = {split_f64(b0), split_f64(b1), split_f64(b2)};
+  float bx, by, bz;
+  dpos32(G, bs, bx, by, bz);
+  bary_q(G, bx, by, bz, Qb);
+  static_cast<float*>(A.vx)[p] = vn0;
+  static_cast<float*>(A.vy)[p] = vn1;
+  static_cast<float*>(A.vz)[p] = vn2;
+  if ((Qb[0] | Qb[1] | Qb[2] | Qb[3]) < 0) {
+    o.queue = true;
+    return;
+  }
+  gq(Qa, Qb, o.gh);
+  o.key = T * kMaxSpecies + s;
+  o.Thome = T;
+  o.shome = s;
+  A.x[p] = b0;
+  A.y[p] = b1;
+  A.z[p] = b2;
+}
+
+// Warp epilogue (all 32 lanes): record which lanes leave their tet in the
+// warp's word of the leave mask (no atomics: the word index is p / 32),
+// reduce the one-segment deposits over runs of equal (tet, species)
+// keys (particles are sorted by tet, so neighbouring lanes usually share
+// one), and flush one int64 atomic per edge and run.
+__device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p, int lane, LaneOut& o) {
   const unsigned full = 0xffffffffu;
-  // warp-aggregated append to the crossing queue
-  const unsigned qmask = __ballot_sync(full, queue);
-  if (qmask) {
-    const int leader = __ffs(qmask) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(A.qcount, __popc(qmask));
-    base = __shfl_sync(full, base, leader);
-    if (queue) A.queue[base + __popc(qmask & ((1u << lane) - 1u))] = (int32_t)p;
-  }
-  // Warp segmented reduction of the one-segment deposits over runs of equal
-  // keys (particles are sorted by tet, so neighbouring lanes usually share one).
-  const int32_t prev = __shfl_up_sync(full, key, 1);
-  const bool head = lane == 0 || prev != key;
+  // every warp writes its own word of the leave mask (p is 32-aligned per warp)
+  const unsigned qmask = __ballot_sync(full, o.queue);
+  if (lane == 0 && p < A.n) A.leave[p >> 5] = qmask;
+  const int32_t prev = __shfl_up_sync(full, o.key, 1);
+  const bool head = lane == 0 || prev != o.key;
   const unsigned heads = __ballot_sync(full, head);
   const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
   const int run_end = above ? (__ffs(above) - 2) : 31;
@@ -650,31 +658,189 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_mixed(PushArgs A) {
   for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
     for (int e = 0; e < 6; e++) {
-      const long long o = __shfl_down_sync(full, gh[e], off);
-      if (lane + off <= run_end) gh[e] += o;
+      const long long v = __shfl_down_sync(full, o.gh[e], off);
+      if (lane + off <= run_end) o.gh[e] += v;
     }
   }
-  if (head && key >= 0) {
-    const int4 e0 = __ldg(&A.te[2 * (int64_t)Thome]), e1 = __ldg(&A.te[2 * (int64_t)Thome + 1]);
-    const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
-    unsigned long long* base = A.dGq + (int64_t)shome * A.ne;
+  if (head && o.key >= 0) {
+    const int32_t eid[6] = {o.e0.x, o.e0.y, o.e0.z, o.e0.w, o.e1.x, o.e1.y};
+    unsigned long long* base = A.dGq + (int64_t)o.shome * A.ne;
 #pragma unroll
     for (int e = 0; e < 6; e++)
-      if (gh[e]) atomicAdd(base + eid[e], (unsigned long long)gh[e]);
+      if (o.gh[e]) atomicAdd(base + eid[e], (unsigned long long)o.gh[e]);
   }
-  nfrz = __reduce_add_sync(full, nfrz);
-  if (lane == 0 && nfrz) atomicAdd(A.stats + 1, (unsigned long long)nfrz);
+  const unsigned nf = __reduce_add_sync(full, o.nfrz);
+  if (lane == 0 && nf) atomicAdd(A.stats + 1, (unsigned long long)nf);
 }
 
-// Crossing path, one queued particle per thread (grid-stride over the queue
-// filled by k_push_mixed in the same step): rebuild b, split the segment at
-// every face it crosses, deposit each in-tet piece, reflect or absorb at walls.
+// Common path, one particle per thread, state read straight from global
+// memory.  Used when the particle arrays are not 16-byte aligned (so bulk
+// copies cannot stage them) and for a ragged last tile.
+__global__ void __launch_bounds__(kThreads, 4) k_push_mixed(PushArgs A, int64_t p0) {
+  const int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  LaneOut o;
+  lane_init(o, lane);
+  if (p < A.n) {
+    const int32_t T = A.tet[p];
+    if (T >= 0) {
+      const float* vx = static_cast<const float*>(A.vx);
+      const float* vy = static_cast<const float*>(A.vy);
+      const float* vz = static_cast<const float*>(A.vz);
+      mixed_particle(A, p, T, A.x[p], A.y[p], A.z[p], vx[p], vy[p], vz[p], o);
+    } else {
+      mixed_particle(A, p, T, 0.0, 0.0, 0.0, 0.f, 0.f, 0.f, o);
+    }
+  }
+  mixed_warp_epilogue(A, p, lane, o);
+}
+
+// ------------------------------------------------- staged common path (TMA)
+// Persistent CTAs walk full 256-particle tiles.  Each tile's slices of the
+// seven particle arrays (x, y, z f64; vx, vy, vz f32; tet i32; 10 KB) are
+// brought into shared memory by cp.async.bulk copies completing on an
+// mbarrier, in a ring of three stages filled two tiles ahead, so HBM latency
+// overlaps the arithmetic.  A stage is refilled only after the iteration
+// that read it has finished on every thread.
+// Every wait is bounded by the global timer (about 1 s); a CTA that times
+// out records it in stats[2], drains the copies it issued, and stops.
+constexpr int kTile = kThreads;
+constexpr int kStageBytes = kTile * (3 * 8 + 3 * 4 + 4);   // 10240
+constexpr int kStages = 3;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false after about one second.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void stage_tile(const PushArgs& A, unsigned char* stage, int64_t tile, uint64_t* bar) {
+  const int64_t p0 = tile * kTile;
+  mbar_expect_tx(bar, kStageBytes);
+  bulk_g2s(stage, A.x + p0, kTile * 8, bar);
+  bulk_g2s(stage + kTile * 8, A.y + p0, kTile * 8, bar);
+  bulk_g2s(stage + kTile * 16, A.z + p0, kTile * 8, bar);
+  bulk_g2s(stage + kTile * 24, static_cast<const float*>(A.vx) + p0, kTile * 4, bar);
+  bulk_g2s(stage + kTile * 28, static_cast<const float*>(A.vy) + p0, kTile * 4, bar);
+  bulk_g2s(stage + kTile * 32, static_cast<const float*>(A.vz) + p0, kTile * 4, bar);
+  bulk_g2s(stage + kTile * 36, A.tet + p0, kTile * 4, bar);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_push_mixed_tma(PushArgs A, int64_t ntiles) {
+  __shared__ __align__(128) unsigned char smem[kStages][kStageBytes];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    for (int k = 0; k < kStages; k++) mbar_init(&bar[k], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int64_t stride = gridDim.x;
+  const int64_t t0 = blockIdx.x;
+  if (tid == 0)
+    for (int k = 0; k < kStages; k++)
+      if (t0 + k * stride < ntiles) stage_tile(A, smem[k], t0 + k * stride, &bar[k]);
+  uint32_t phase = 0u;   // bit k = parity of the next wait on stage k
+  int st = 0;
+  for (int64_t it = 0, tile = t0; tile < ntiles; tile += stride, it++) {
+    // Every thread finished iteration it-1 (which used stage st-1) before
+    // this barrier; the proxy fence orders those shared-memory reads before
+    // the bulk copy that refills that stage below.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const bool ok = mbar_wait_bounded(&bar[st], (phase >> st) & 1u);
+    if (__syncthreads_or(!ok)) {
+      // give up: record it, wait (bounded) for this CTA's copies still in
+      // flight (stages of tiles it .. it+kStages-1 not yet consumed), stop
+      if (tid == 0) {
+        atomicAdd(A.stats + 2, 1ull);
+        for (int k = 0; k < kStages; k++) {
+          const int sk = (st + k) % kStages;
+          if (tile + k * stride < ntiles) mbar_wait_bounded(&bar[sk], (phase >> sk) & 1u);
+        }
+      }
+      return;
+    }
+    phase ^= 1u << st;
+    if (tid == 0 && it > 0) {
+      const int prev = (st + kStages - 1) % kStages;
+      const int64_t next = tile + (kStages - 1) * stride;
+      if (next < ntiles) stage_tile(A, smem[prev], next, &bar[prev]);
+    }
+    const unsigned char* S = smem[st];
+    const double ax = reinterpret_cast<const double*>(S)[tid];
+    const double ay = reinterpret_cast<const double*>(S + kTile * 8)[tid];
+    const double az = reinterpret_cast<const double*>(S + kTile * 16)[tid];
+    const float v0 = reinterpret_cast<const float*>(S + kTile * 24)[tid];
+    const float v1 = reinterpret_cast<const float*>(S + kTile * 28)[tid];
+    const float v2 = reinterpret_cast<const float*>(S + kTile * 32)[tid];
+    const int32_t T = reinterpret_cast<const int32_t*>(S + kTile * 36)[tid];
+    const int64_t p = tile * kTile + tid;
+    LaneOut o;
+    lane_init(o, lane);
+    mixed_particle(A, p, T, ax, ay, az, v0, v1, v2, o);
+    mixed_warp_epilogue(A, p, lane, o);
+    st = (st + 1) % kStages;
+  }
+}
+
+// Crossing path for the particles the common path marked in the leave mask
+// this step (grid-stride over mask words, one word per thread): rebuild b,
+// split the segment at every face it crosses, deposit each in-tet piece,
+// reflect or absorb at walls.
 __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A) {
   const int lane = threadIdx.x & 31;
-  const int32_t count = *A.qcount;
   unsigned ncr = 0, nfrz = 0;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const int64_t p = A.queue[i];
+  const int64_t nwords = (A.n + 31) >> 5;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords;
+       w += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t bits = A.leave[w]; bits; bits &= bits - 1u) {
+    const int64_t p = (w << 5) + (__ffs(bits) - 1);
     int32_t T = A.tet[p];
     const int s = species_of(A.sp, p);
     float* vxp = static_cast<float*>(A.vx);
@@ -687,7 +853,7 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A) {
     int32_t Qa[4], Qb[4], Qp[4];
     FF bs[3] = {split_f64(b[0]), split_f64(b[1]), split_f64(b[2])};
     {
-      const Geo32 G = ld_geo(A.geo32, T);
+      const Geo32 G = ld_geo(A.tetrec, T);
       const FF rs[3] = {split_f64(a0[0]), split_f64(a0[1]), split_f64(a0[2])};
       float dx, dy, dz;
       dpos32(G, rs, dx, dy, dz);
@@ -790,7 +956,7 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A) {
         moved = false;
         break;
       }
-      const Geo32 Gc = ld_geo(A.geo32, T);
+      const Geo32 Gc = ld_geo(A.tetrec, T);
       float ex, ey, ez;
       dpos32(Gc, bs, ex, ey, ez);
       bary_q(Gc, ex, ey, ez, Qb);
@@ -818,6 +984,7 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A) {
     A.tet[p] = T;
     if (A.ncross) A.ncross[p] += nc;
     ncr += (unsigned)nc;
+  }
   }
   const unsigned full = 0xffffffffu;
   ncr = __reduce_add_sync(full, ncr);
@@ -876,7 +1043,7 @@ struct ChargeArgs {
   int64_t nt;
   int32_t mixed;
   const double* geom64;
-  const float4* geo32;
+  const float4* tetrec;
   const int4* tn;
   double* rho;
 };
@@ -894,7 +1061,7 @@ __global__ void __launch_bounds__(kThreads) k_nodal_charge(ChargeArgs A) {
   double lam[4];
   if (A.mixed) {
     int32_t Q[4];
-    bary_q_at(A.geo32, T, r, Q);
+    bary_q_at(A.tetrec, T, r, Q);
     for (int i = 0; i < 4; i++) lam[i] = (double)Q[i] * (1.0 / (double)kQOne);
   } else {
     bary64(A.geom64 + 12 * (int64_t)T, r, lam);
@@ -1026,6 +1193,308 @@ __global__ void __launch_bounds__(kThreads) k_sort_scatter(SortArgs A) {
   if (A.oncross) A.oncross[q] = A.ncross[p];
 }
 
+// ----------------------------------------------------------------- adjoint
+// Reverse mode of one particle step for the fixed tet sequence of the forward
+// step.  Per particle it recomputes the gather and the Boris rotation from
+// the state before the step, reads which walls mirrored the particle from
+// the sign of each velocity component after the step, and propagates the
+// adjoint (rbar, vbar) of the state after the step back to the state before
+// it.  The adjoint of the per-tet affine field (E0, W, B0, beta) is reduced
+// over runs of equal tets in each warp and added to tetgrad in FP64; the
+// transposed pre-pass k_field_adjoint maps it to the complex DoFs.  A
+// particle frozen during the step gets a zero adjoint (its later state no
+// longer depends on its earlier one through the step map).
+struct AdjArgs {
+  int64_t n;
+  const double* x;
+  const double* y;
+  const double* z;
+  const void* vx;
+  const void* vy;
+  const void* vz;
+  const int32_t* tet;
+  const void* vx1;           // velocities after the step
+  const void* vy1;
+  const void* vz1;
+  const uint8_t* status1;    // statuses after the step
+  Species sp;
+  double dt;
+  int64_t nt;
+  const double* geom64;
+  const double* field64;
+  const float4* tetrec;
+  double* rbx;
+  double* rby;
+  double* rbz;
+  void* vbx;
+  void* vby;
+  void* vbz;
+  double* tetgrad;           // [nt][10]
+};
+
+template <typename R>
+struct Vec {
+  R x, y, z;
+};
+template <typename R>
+__device__ __forceinline__ Vec<R> vx3(Vec<R> a, Vec<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ R vd3(Vec<R> a, Vec<R> b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+
+template <typename R>
+__device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, int32_t T, R out[10]) {
+  const int s = species_of(A.sp, p);
+  const R kq = (R)A.sp.kq[s];
+  const R* vx = static_cast<const R*>(A.vx);
+  const R* vy = static_cast<const R*>(A.vy);
+  const R* vz = static_cast<const R*>(A.vz);
+  const Vec<R> v = {vx[p], vy[p], vz[p]};
+  Vec<R> d, E0, W, B0;
+  R beta;
+  if (sizeof(R) == 8) {
+    const double* G = A.geom64 + 12 * (int64_t)T;
+    const double* F = A.field64 + 10 * (int64_t)T;
+    d = {(R)(A.x[p] - G[0]), (R)(A.y[p] - G[1]), (R)(A.z[p] - G[2])};
+    E0 = {(R)F[0], (R)F[1], (R)F[2]};
+    W = {(R)F[3], (R)F[4], (R)F[5]};
+    B0 = {(R)F[6], (R)F[7], (R)F[8]};
+    beta = (R)F[9];
+  } else {
+    const float4* Rr = A.tetrec + 8 * (int64_t)T;
+    const Geo32 G = Geo32{__ldg(Rr), __ldg(Rr + 1), __ldg(Rr + 2), __ldg(Rr + 3)};
+    const float4 f0 = __ldg(Rr + 4), f1 = __ldg(Rr + 5), f2 = __ldg(Rr + 6);
+    const FF rs[3] = {split_f64(A.x[p]), split_f64(A.y[p]), split_f64(A.z[p])};
+    float dx, dy, dz;
+    dpos32(G, rs, dx, dy, dz);
+    d = {(R)dx, (R)dy, (R)dz};
+    E0 = {(R)f0.x, (R)f0.y, (R)f0.z};
+    W = {(R)f0.w, (R)f1.x, (R)f1.y};
+    B0 = {(R)f1.z, (R)f1.w, (R)f2.x};
+    beta = (R)f2.y;
+  }
+  // forward recompute
+  const Vec<R> dW = vx3(d, W);
+  const Vec<R> E = {E0.x + dW.x, E0.y + dW.y, E0.z + dW.z};
+  const Vec<R> B = {B0.x + beta * d.x, B0.y + beta * d.y, B0.z + beta * d.z};
+  const Vec<R> vm = {v.x + kq * E.x, v.y + kq * E.y, v.z + kq * E.z};
+  const Vec<R> tau = {kq * B.x, kq * B.y, kq * B.z};
+  const R t2 = vd3(tau, tau);
+  const R f = R(2) / (R(1) + t2);
+  const Vec<R> sv = {f * tau.x, f * tau.y, f * tau.z};
+  const Vec<R> c1 = vx3(vm, tau);
+  const Vec<R> vp = {vm.x + c1.x, vm.y + c1.y, vm.z + c1.z};
+  const Vec<R> c2 = vx3(vp, sv);
+  const Vec<R> vn = {vm.x + c2.x + kq * E.x, vm.y + c2.y + kq * E.y, vm.z + c2.z + kq * E.z};
+  // wall mirrors: a reflected component comes out with the opposite sign
+  const R* vx1 = static_cast<const R*>(A.vx1);
+  const R* vy1 = static_cast<const R*>(A.vy1);
+  const R* vz1 = static_cast<const R*>(A.vz1);
+  const R mx = vn.x * vx1[p] < R(0) ? R(-1) : R(1);
+  const R my = vn.y * vy1[p] < R(0) ? R(-1) : R(1);
+  const R mz = vn.z * vz1[p] < R(0) ? R(-1) : R(1);
+  R* vbx = static_cast<R*>(A.vbx);
+  R* vby = static_cast<R*>(A.vby);
+  R* vbz = static_cast<R*>(A.vbz);
+  // adjoint of the output state, mirrored back
+  const double rbx = (double)mx * A.rbx[p], rby = (double)my * A.rby[p], rbz = (double)mz * A.rbz[p];
+  const R dt = (R)A.dt;
+  // b = r + dt vn
+  Vec<R> vnb = {mx * vbx[p] + dt * (R)rbx, my * vby[p] + dt * (R)rby, mz * vbz[p] + dt * (R)rbz};
+  // vn = vpl + kq E ;  vpl = vm + vp x s
+  Vec<R> Eb = {kq * vnb.x, kq * vnb.y, kq * vnb.z};
+  Vec<R> vmb = vnb;
+  const Vec<R> vpb = vx3(sv, vnb);
+  const Vec<R> sb = vx3(vnb, vp);
+  // s = f tau
+  Vec<R> taub = {f * sb.x, f * sb.y, f * sb.z};
+  const R fb = vd3(tau, sb);
+  const R t2b = R(-0.5) * f * f * fb;
+  taub.x += R(2) * t2b * tau.x;
+  taub.y += R(2) * t2b * tau.y;
+  taub.z += R(2) * t2b * tau.z;
+  // vp = vm + vm x tau
+  const Vec<R> a1 = vx3(tau, vpb), a2 = vx3(vpb, vm);
+  vmb = {vmb.x + vpb.x + a1.x, vmb.y + vpb.y + a1.y, vmb.z + vpb.z + a1.z};
+  taub = {taub.x + a2.x, taub.y + a2.y, taub.z + a2.z};
+  // tau = kq B ; vm = v + kq E
+  const Vec<R> Bb = {kq * taub.x, kq * taub.y, kq * taub.z};
+  Eb = {Eb.x + kq * vmb.x, Eb.y + kq * vmb.y, Eb.z + kq * vmb.z};
+  // E = E0 + d x W ; B = B0 + beta d
+  const Vec<R> Wb = vx3(Eb, d);
+  const Vec<R> db1 = vx3(W, Eb);
+  const R betab = vd3(Bb, d);
+  A.rbx[p] = rbx + (double)(db1.x + beta * Bb.x);
+  A.rby[p] = rby + (double)(db1.y + beta * Bb.y);
+  A.rbz[p] = rbz + (double)(db1.z + beta * Bb.z);
+  vbx[p] = vmb.x;
+  vby[p] = vmb.y;
+  vbz[p] = vmb.z;
+  out[0] = Eb.x; out[1] = Eb.y; out[2] = Eb.z;
+  out[3] = Wb.x; out[4] = Wb.y; out[5] = Wb.z;
+  out[6] = Bb.x; out[7] = Bb.y; out[8] = Bb.z;
+  out[9] = betab;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  R g[10];
+#pragma unroll
+  for (int i = 0; i < 10; i++) g[i] = R(0);
+  int32_t key = -1 - lane;
+  if (p < A.n) {
+    const int32_t T = A.tet[p];
+    if (T >= 0 && T < A.nt) {
+      if (A.status1[p] != FEMPIC_P_OK) {   // frozen during the step
+        A.rbx[p] = A.rby[p] = A.rbz[p] = 0.0;
+        static_cast<R*>(A.vbx)[p] = static_cast<R*>(A.vby)[p] = static_cast<R*>(A.vbz)[p] = R(0);
+      } else {
+        adjoint_particle<R>(A, p, T, g);
+        key = T;
+      }
+    }
+  }
+  const unsigned full = 0xffffffffu;
+  const int32_t prev = __shfl_up_sync(full, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const unsigned heads = __ballot_sync(full, head);
+  const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
+  const int run_end = above ? (__ffs(above) - 2) : 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+      const R o = __shfl_down_sync(full, g[i], off);
+      if (lane + off <= run_end) g[i] += o;
+    }
+  }
+  if (head && key >= 0) {
+    double* tg = A.tetgrad + 10 * (int64_t)key;
+#pragma unroll
+    for (int i = 0; i < 10; i++)
+      if (g[i] != R(0)) atomicAdd(tg + i, (double)g[i]);
+  }
+}
+
+// Transpose of the per-tet pre-pass for one step: from the adjoint of
+// (E0, W, B0, beta) to the adjoint of the carrier-restored DoFs eps, bet,
+// then through eps = c_re Re(e~) - c_im Im(e~) to dL/dRe + j dL/dIm of the
+// complex DoFs (FP64 atomics over the tets sharing an edge or face); tetgrad
+// is cleared for the next step.
+__global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, int32_t mixed, const double* __restrict__ geom64,
+                                                             const float4* __restrict__ rec, const int4* __restrict__ te,
+                                                             const int4* __restrict__ tf, double cre, double cim,
+                                                             double* __restrict__ tetgrad, double* __restrict__ egrad,
+                                                             double* __restrict__ bgrad) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double* tg = tetgrad + 10 * t;
+  double a[10];
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    a[i] = tg[i];
+    any = any || a[i] != 0.0;
+  }
+  if (!any) return;
+#pragma unroll
+  for (int i = 0; i < 10; i++) tg[i] = 0.0;
+  V3<double> g[4];
+  if (mixed) {
+    const float4 q = rec[8 * t + 1], r = rec[8 * t + 2], c = rec[8 * t + 3];
+    g[1] = {q.z, q.w, r.x};
+    g[2] = {r.y, r.z, r.w};
+    g[3] = {c.x, c.y, c.z};
+    // the forward pre-pass formed g_0 in FP32
+    g[0] = {(double)-((float)g[1].x + (float)g[2].x + (float)g[3].x),
+            (double)-((float)g[1].y + (float)g[2].y + (float)g[3].y),
+            (double)-((float)g[1].z + (float)g[2].z + (float)g[3].z)};
+  } else {
+    const double* G = geom64 + 12 * t;
+    g[1] = {G[3], G[4], G[5]};
+    g[2] = {G[6], G[7], G[8]};
+    g[3] = {G[9], G[10], G[11]};
+    g[0] = {-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z)};
+  }
+  const V3<double> E0b = {a[0], a[1], a[2]}, Wb = {a[3], a[4], a[5]}, B0b = {a[6], a[7], a[8]};
+  const double betab = a[9];
+  double epsb[6], betb[4];
+#pragma unroll
+  for (int e = 0; e < 6; e++) epsb[e] = vdot(Wb, vcross(g[le1(e)], g[le0(e)]));
+  epsb[0] += vdot(E0b, g[1]);
+  epsb[1] += vdot(E0b, g[2]);
+  epsb[2] += vdot(E0b, g[3]);
+  betb[0] = 0.0;
+  betb[1] = 2.0 * vdot(B0b, vcross(g[2], g[3]));
+  betb[2] = 2.0 * vdot(B0b, vcross(g[1], g[3]));
+  betb[3] = 2.0 * vdot(B0b, vcross(g[1], g[2]));
+#pragma unroll
+  for (int f = 0; f < 4; f++) betb[f] += 2.0 * betab * vdot(g[lf(f, 0)], vcross(g[lf(f, 1)], g[lf(f, 2)]));
+  const int4 e0 = te[2 * t], e1 = te[2 * t + 1], fi = tf[t];
+  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
+  const int32_t fid[4] = {fi.x, fi.y, fi.z, fi.w};
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    atomicAdd(egrad + 2 * (int64_t)eid[e], cre * epsb[e]);
+    atomicAdd(egrad + 2 * (int64_t)eid[e] + 1, -cim * epsb[e]);
+  }
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    atomicAdd(bgrad + 2 * (int64_t)fid[f], cre * betb[f]);
+    atomicAdd(bgrad + 2 * (int64_t)fid[f] + 1, -cim * betb[f]);
+  }
+}
+
+// Total kinetic energy sum_p 1/2 m w |v|^2 over particles with tet >= 0 into
+// *ke (FP64 atomics), and optionally the adjoint seed vbar = m w v, rbar = 0.
+struct KEArgs {
+  int64_t n;
+  const void* vx;
+  const void* vy;
+  const void* vz;
+  const int32_t* tet;
+  Species sp;                // species ranges
+  double mw[kMaxSpecies];    // m w per species
+  double* ke;
+  double* rbx;
+  double* rby;
+  double* rbz;
+  void* vbx;
+  void* vby;
+  void* vbz;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_kinetic_energy(KEArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = A.n;
+  const void *vx = A.vx, *vy = A.vy, *vz = A.vz;
+  void *vbx = A.vbx, *vby = A.vby, *vbz = A.vbz;
+  double *rbx = A.rbx, *rby = A.rby, *rbz = A.rbz;
+  double e = 0.0;
+  if (p < n && A.tet[p] >= 0) {
+    const double mw = A.mw[species_of(A.sp, p)];
+    const double a = static_cast<const R*>(vx)[p], b = static_cast<const R*>(vy)[p], c = static_cast<const R*>(vz)[p];
+    e = 0.5 * mw * (a * a + b * b + c * c);
+    if (vbx) {
+      static_cast<R*>(vbx)[p] = (R)(mw * a);
+      static_cast<R*>(vby)[p] = (R)(mw * b);
+      static_cast<R*>(vbz)[p] = (R)(mw * c);
+      rbx[p] = rby[p] = rbz[p] = 0.0;
+    }
+  } else if (p < n && vbx) {
+    static_cast<R*>(vbx)[p] = static_cast<R*>(vby)[p] = static_cast<R*>(vbz)[p] = R(0);
+    rbx[p] = rby[p] = rbz[p] = 0.0;
+  }
+  for (int off = 16; off > 0; off >>= 1) e += __shfl_down_sync(0xffffffffu, e, off);
+  if ((threadIdx.x & 31) == 0 && e != 0.0) atomicAdd(A.ke, e);
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
@@ -1039,7 +1508,7 @@ struct fempic_env {
   fempic_options opt{};
   HostMesh h;
   double* geom64 = nullptr;
-  float4* geo32 = nullptr;
+  float4* tetrec = nullptr;
   int4* tn = nullptr;
   int4* nb = nullptr;
   int4* te = nullptr;
@@ -1054,9 +1523,9 @@ struct fempic_env {
   int32_t* gtet = nullptr;
   double qw_last[kMaxSpecies] = {0};
   int32_t ns_last = 0;
-  int32_t* queue = nullptr;         // mixed form crossing queue [queue_cap]
-  int32_t* qcount = nullptr;        // its length
-  int64_t queue_cap = 0;
+  uint32_t* leave = nullptr;        // mixed form leave mask [leave_cap words]
+  double* tetgrad = nullptr;        // adjoint of the per-tet affine field [nt][10]
+  int64_t leave_cap = 0;
   int num_sms = 1;
   int64_t steps = 0;
   // per-kernel event timing (measurement support)
@@ -1109,8 +1578,8 @@ struct LaunchTimer {
 static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
-  void* ptrs[] = {e->geom64, e->geo32, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
-                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->queue, e->qcount};
+  void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->leave, e->tetgrad};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete e;
@@ -1123,7 +1592,7 @@ extern "C" void fempic_env_destroy(fempic_env* env) { free_env(env); }
 static int upload(fempic_env* e) {
   const HostMesh& m = e->h;
   const int64_t nt = m.nt;
-  std::vector<float4> geo(4 * nt);
+  std::vector<float4> geo(8 * nt);
   std::vector<int4> tn(nt), nb(nt), te(2 * nt), tf(nt);
   for (int64_t t = 0; t < nt; t++) {
     const double* G = &m.geom[12 * t];
@@ -1134,10 +1603,15 @@ static int upload(fempic_env* e) {
       xl[a] = (float)(G[a] - (double)xh[a]);
     }
     for (int i = 0; i < 9; i++) g[i] = (float)G[3 + i];
-    geo[4 * t] = make_float4(xh[0], xh[1], xh[2], xl[0]);
-    geo[4 * t + 1] = make_float4(xl[1], xl[2], g[0], g[1]);
-    geo[4 * t + 2] = make_float4(g[2], g[3], g[4], g[5]);
-    geo[4 * t + 3] = make_float4(g[6], g[7], g[8], 0.f);
+    geo[8 * t] = make_float4(xh[0], xh[1], xh[2], xl[0]);
+    geo[8 * t + 1] = make_float4(xl[1], xl[2], g[0], g[1]);
+    geo[8 * t + 2] = make_float4(g[2], g[3], g[4], g[5]);
+    geo[8 * t + 3] = make_float4(g[6], g[7], g[8], 0.f);
+    for (int k = 4; k < 7; k++) geo[8 * t + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int32_t nbk[4] = {m.nb[4 * t], m.nb[4 * t + 1], m.nb[4 * t + 2], m.nb[4 * t + 3]};
+    float4 nbf;
+    std::memcpy(&nbf, nbk, sizeof(nbf));
+    geo[8 * t + 7] = nbf;
     tn[t] = make_int4(m.tn[4 * t], m.tn[4 * t + 1], m.tn[4 * t + 2], m.tn[4 * t + 3]);
     nb[t] = make_int4(m.nb[4 * t], m.nb[4 * t + 1], m.nb[4 * t + 2], m.nb[4 * t + 3]);
     te[2 * t] = make_int4(m.te[6 * t], m.te[6 * t + 1], m.te[6 * t + 2], m.te[6 * t + 3]);
@@ -1145,13 +1619,13 @@ static int upload(fempic_env* e) {
     tf[t] = make_int4(m.tf[4 * t], m.tf[4 * t + 1], m.tf[4 * t + 2], m.tf[4 * t + 3]);
   }
   FEMPIC_CUDA(dalloc(&e->geom64, 12 * nt));
-  FEMPIC_CUDA(dalloc(&e->geo32, 4 * nt));
+  FEMPIC_CUDA(dalloc(&e->tetrec, 8 * nt));
   FEMPIC_CUDA(dalloc(&e->tn, nt));
   FEMPIC_CUDA(dalloc(&e->nb, nt));
   FEMPIC_CUDA(dalloc(&e->te, 2 * nt));
   FEMPIC_CUDA(dalloc(&e->tf, nt));
   FEMPIC_CUDA(cudaMemcpy(e->geom64, m.geom.data(), 12 * nt * sizeof(double), cudaMemcpyHostToDevice));
-  FEMPIC_CUDA(cudaMemcpy(e->geo32, geo.data(), 4 * nt * sizeof(float4), cudaMemcpyHostToDevice));
+  FEMPIC_CUDA(cudaMemcpy(e->tetrec, geo.data(), 8 * nt * sizeof(float4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->tn, tn.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->nb, nb.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->te, te.data(), 2 * nt * sizeof(int4), cudaMemcpyHostToDevice));
@@ -1160,8 +1634,6 @@ static int upload(fempic_env* e) {
     FEMPIC_CUDA(dalloc(reinterpret_cast<double**>(&e->field), 10 * nt));
     FEMPIC_CUDA(dalloc(&e->dG, m.ne));
     FEMPIC_CUDA(cudaMemset(e->dG, 0, m.ne * sizeof(double)));
-  } else {
-    FEMPIC_CUDA(dalloc(reinterpret_cast<float4**>(&e->field), 3 * nt));
   }
   FEMPIC_CUDA(dalloc(&e->Gcum, m.ne));
   FEMPIC_CUDA(cudaMemset(e->Gcum, 0, m.ne * sizeof(double)));
@@ -1286,18 +1758,20 @@ extern "C" int fempic_locate(fempic_env* env, const fempic_particles* p, void* s
   return FEMPIC_OK;
 }
 
-// Crossing queue of the mixed form: one slot per particle, grown on demand.
-static int ensure_queue(fempic_env* env, int64_t n, cudaStream_t st) {
-  if (!env->qcount) FEMPIC_CUDA(dalloc(&env->qcount, 1));
-  if (env->queue_cap >= n) return FEMPIC_OK;
-  if (env->queue) {
+// Leave mask of the mixed form: one bit per particle, grown on demand.  The
+// common path overwrites every word it covers each step, so it needs no
+// clearing.
+static int ensure_leave(fempic_env* env, int64_t n, cudaStream_t st) {
+  const int64_t words = (n + 31) / 32;
+  if (env->leave_cap >= words) return FEMPIC_OK;
+  if (env->leave) {
     FEMPIC_CUDA(cudaStreamSynchronize(st));
-    cudaFree(env->queue);
-    env->queue = nullptr;
-    env->queue_cap = 0;
+    cudaFree(env->leave);
+    env->leave = nullptr;
+    env->leave_cap = 0;
   }
-  FEMPIC_CUDA(dalloc(&env->queue, n));
-  env->queue_cap = n;
+  FEMPIC_CUDA(dalloc(&env->leave, words));
+  env->leave_cap = words;
   return FEMPIC_OK;
 }
 
@@ -1343,10 +1817,10 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   {
   LaunchTimer lt(env, st, FEMPIC_K_FIELD);
   if (mixed) {
-    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geo32, env->te, env->tf,
+    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf,
                                                       static_cast<const float2*>(envl->e_tilde),
                                                       static_cast<const float2*>(envl->b_tilde), (float)cre,
-                                                      (float)cim, static_cast<float4*>(env->field));
+                                                      (float)cim);
   } else {
     k_field_fp64<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf,
                                                        static_cast<const double2*>(envl->e_tilde),
@@ -1379,7 +1853,7 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   A.nt = nt;
   A.ne = env->h.ne;
   A.geom64 = env->geom64;
-  A.geo32 = env->geo32;
+  A.tetrec = env->tetrec;
   A.tn = env->tn;
   A.nb = env->nb;
   A.te = env->te;
@@ -1388,17 +1862,26 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   A.dGq = env->dGq;
   A.stats = env->stats;
   if (mixed) {
-    rc = ensure_queue(env, p->n, st);
+    rc = ensure_leave(env, p->n, st);
     if (rc) return rc;
-    A.queue = env->queue;
-    A.qcount = env->qcount;
-    FEMPIC_CUDA(cudaMemsetAsync(env->qcount, 0, sizeof(int32_t), st));
+    A.leave = env->leave;
   }
   {
     LaunchTimer lt(env, st, FEMPIC_K_PUSH);
     if (mixed) {
-      k_push_mixed<<<blocks_for(p->n), kThreads, 0, st>>>(A);
-      const unsigned cross_blocks = (unsigned)std::min<int64_t>(blocks_for(p->n), (int64_t)env->num_sms * 8);
+      // bulk copies need 16-byte aligned sources: stage full tiles when every
+      // particle array allows it; the ragged tail (or everything) goes plain
+      const uintptr_t align = (uintptr_t)p->x | (uintptr_t)p->y | (uintptr_t)p->z | (uintptr_t)p->vx |
+                              (uintptr_t)p->vy | (uintptr_t)p->vz | (uintptr_t)p->tet;
+      const int64_t ntiles = (align & 15u) ? 0 : p->n / kTile;
+      if (ntiles > 0) {
+        const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)env->num_sms * 4);
+        k_push_mixed_tma<<<grid, kThreads, 0, st>>>(A, ntiles);
+      }
+      const int64_t rest = p->n - ntiles * kTile;
+      if (rest > 0) k_push_mixed<<<blocks_for(rest), kThreads, 0, st>>>(A, ntiles * kTile);
+      const unsigned cross_blocks =
+          (unsigned)std::min<int64_t>(blocks_for((p->n + 31) / 32), (int64_t)env->num_sms * 8);
       k_cross_mixed<<<cross_blocks, kThreads, 0, st>>>(A);
     } else {
       k_push_fp64<<<blocks_for(p->n), kThreads, 0, st>>>(A);
@@ -1463,7 +1946,7 @@ extern "C" int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, d
   A.nt = env->h.nt;
   A.mixed = env->opt.precision == FEMPIC_MIXED;
   A.geom64 = env->geom64;
-  A.geo32 = env->geo32;
+  A.tetrec = env->tetrec;
   A.tn = env->tn;
   A.rho = rho;
   {
@@ -1474,15 +1957,16 @@ extern "C" int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, d
   return FEMPIC_OK;
 }
 
-extern "C" int fempic_stats(fempic_env* env, int64_t* out3, void* stream) {
-  if (!env || !out3) return fail(FEMPIC_EINVAL, "stats: NULL argument");
-  unsigned long long h[2] = {0, 0};
+extern "C" int fempic_stats(fempic_env* env, int64_t* out4, void* stream) {
+  if (!env || !out4) return fail(FEMPIC_EINVAL, "stats: NULL argument");
+  unsigned long long h[3] = {0, 0, 0};
   cudaStream_t st = (cudaStream_t)stream;
-  FEMPIC_CUDA(cudaMemcpyAsync(h, env->stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  FEMPIC_CUDA(cudaMemcpyAsync(h, env->stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   FEMPIC_CUDA(cudaStreamSynchronize(st));
-  out3[0] = (int64_t)h[0];
-  out3[1] = (int64_t)h[1];
-  out3[2] = env->steps;
+  out4[0] = (int64_t)h[0];
+  out4[1] = (int64_t)h[1];
+  out4[2] = env->steps;
+  out4[3] = (int64_t)h[2];
   return FEMPIC_OK;
 }
 
@@ -1679,6 +2163,133 @@ extern "C" int fempic_sort_noalloc(fempic_env* env, const fempic_particles* in, 
   A.offsets = offsets;
   A.cursor = counts;
   k_sort_scatter<<<blocks_for(in->n), kThreads, 0, st>>>(A);
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+// ------------------------------------------------------------------ adjoint ABI
+static int check_adjoint(const fempic_adjoint* a, int64_t n) {
+  if (!a) return fail(FEMPIC_EINVAL, "adjoint: NULL adjoint state");
+  if (a->n != n) return fail(FEMPIC_EINVAL, "adjoint: size differs from the particle set");
+  if (n > 0 && (!a->rx || !a->ry || !a->rz || !a->vx || !a->vy || !a->vz))
+    return fail(FEMPIC_EINVAL, "adjoint: NULL array");
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles* before,
+                                        const fempic_particles* after, const fempic_envelope* envl, double omega0,
+                                        double t, double dt, const fempic_adjoint* adj, void* e_grad, void* b_grad,
+                                        void* stream) {
+  if (!env || !envl || !e_grad || !b_grad) return fail(FEMPIC_EINVAL, "push_step_adjoint: NULL argument");
+  int rc = check_particles(before, true);
+  if (rc) return rc;
+  rc = check_particles(after, true);
+  if (rc) return rc;
+  if (before->n != after->n) return fail(FEMPIC_EINVAL, "push_step_adjoint: before/after sizes differ");
+  rc = check_adjoint(adj, before->n);
+  if (rc) return rc;
+  if (!envl->e_tilde || !envl->b_tilde) return fail(FEMPIC_EINVAL, "push_step_adjoint: NULL DoF arrays");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(omega0) || !std::isfinite(t) || !std::isfinite(envl->amp))
+    return fail(FEMPIC_EINVAL, "push_step_adjoint: non-finite or non-positive scalar");
+  cudaStream_t st = (cudaStream_t)stream;
+  AdjArgs A{};
+  rc = fill_species(before, dt, &A.sp);
+  if (rc) return rc;
+  const bool mixed = env->opt.precision == FEMPIC_MIXED;
+  const int64_t nt = env->h.nt;
+  if (!env->tetgrad) {
+    FEMPIC_CUDA(dalloc(&env->tetgrad, 10 * nt));
+    FEMPIC_CUDA(cudaMemsetAsync(env->tetgrad, 0, 10 * nt * sizeof(double), st));
+  }
+  // the per-tet affine field of this step (same carrier as the forward step)
+  const double phi = omega0 * t;
+  double cre = envl->amp * std::cos(phi), cim = envl->amp * std::sin(phi);
+  if (mixed) {
+    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf,
+                                                      static_cast<const float2*>(envl->e_tilde),
+                                                      static_cast<const float2*>(envl->b_tilde), (float)cre,
+                                                      (float)cim);
+    cre = (double)(float)cre;
+    cim = (double)(float)cim;
+  } else {
+    k_field_fp64<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf,
+                                                       static_cast<const double2*>(envl->e_tilde),
+                                                       static_cast<const double2*>(envl->b_tilde), cre, cim,
+                                                       static_cast<double*>(env->field));
+  }
+  FEMPIC_CUDA(cudaGetLastError());
+  if (before->n > 0) {
+    A.n = before->n;
+    A.x = before->x;
+    A.y = before->y;
+    A.z = before->z;
+    A.vx = before->vx;
+    A.vy = before->vy;
+    A.vz = before->vz;
+    A.tet = before->tet;
+    A.vx1 = after->vx;
+    A.vy1 = after->vy;
+    A.vz1 = after->vz;
+    A.status1 = after->status;
+    A.dt = dt;
+    A.nt = nt;
+    A.geom64 = env->geom64;
+    A.field64 = static_cast<const double*>(env->field);
+    A.tetrec = env->tetrec;
+    A.rbx = adj->rx;
+    A.rby = adj->ry;
+    A.rbz = adj->rz;
+    A.vbx = adj->vx;
+    A.vby = adj->vy;
+    A.vbz = adj->vz;
+    A.tetgrad = env->tetgrad;
+    if (mixed)
+      k_push_adjoint<float><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+    else
+      k_push_adjoint<double><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+    FEMPIC_CUDA(cudaGetLastError());
+  }
+  k_field_adjoint<<<blocks_for(nt), kThreads, 0, st>>>(nt, mixed ? 1 : 0, env->geom64, env->tetrec, env->te, env->tf,
+                                                        cre, cim, env->tetgrad, static_cast<double*>(e_grad),
+                                                        static_cast<double*>(b_grad));
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_kinetic_energy(fempic_env* env, const fempic_particles* p, double* ke,
+                                     const fempic_adjoint* seed, void* stream) {
+  if (!env || !ke) return fail(FEMPIC_EINVAL, "kinetic_energy: NULL argument");
+  int rc = check_particles(p, true);
+  if (rc) return rc;
+  if (seed) {
+    rc = check_adjoint(seed, p->n);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  FEMPIC_CUDA(cudaMemsetAsync(ke, 0, sizeof(double), st));
+  if (p->n == 0) return FEMPIC_OK;
+  KEArgs A{};
+  rc = fill_species(p, 1.0, &A.sp);
+  if (rc) return rc;
+  for (int s = 0; s < kMaxSpecies; s++) A.mw[s] = s < p->n_species ? p->m[s] * p->w[s] : 0.0;
+  A.n = p->n;
+  A.vx = p->vx;
+  A.vy = p->vy;
+  A.vz = p->vz;
+  A.tet = p->tet;
+  A.ke = ke;
+  if (seed) {
+    A.rbx = seed->rx;
+    A.rby = seed->ry;
+    A.rbz = seed->rz;
+    A.vbx = seed->vx;
+    A.vby = seed->vy;
+    A.vbz = seed->vz;
+  }
+  if (env->opt.precision == FEMPIC_MIXED)
+    k_kinetic_energy<float><<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  else
+    k_kinetic_energy<double><<<blocks_for(p->n), kThreads, 0, st>>>(A);
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
 }

@@ -178,9 +178,9 @@ class FempicEnv:
         st.swap(scratch)
 
     def stats(self, stream=None) -> dict:
-        out = np.zeros(3, np.int64)
+        out = np.zeros(4, np.int64)
         capi.fempic_stats(self.h, out.ctypes.data, _stream(stream))
-        return dict(crossings=int(out[0]), frozen=int(out[1]), steps=int(out[2]))
+        return dict(crossings=int(out[0]), frozen=int(out[1]), steps=int(out[2]), wait_timeouts=int(out[3]))
 
     def profile(self, enable: bool):
         """Start (clearing earlier records) or stop per-kernel event timing."""

@@ -314,3 +314,42 @@ def test_sort_by_species_and_tet(prec):
         assert np.all((perm[seg] >= sb[s]) & (perm[seg] < sb[s + 1]))   # species ranges stay put
         key = np.where(after["tet"][seg] >= 0, after["tet"][seg], env.n_tets)
         assert np.all(np.diff(key) >= 0)
+
+
+# -------------------------------------------------- staged vs plain path
+def _unaligned_copy(t):
+    """Same values in a buffer offset by one element: not 16-byte aligned."""
+    buf = torch.empty(t.numel() + 1, dtype=t.dtype, device=t.device)
+    v = buf[1:]
+    v.copy_(t)
+    return v
+
+
+def test_mixed_staged_path_equals_plain_path():
+    """The bulk-copy staged common-path kernel (16-byte aligned particle
+    arrays) and the plain kernel (unaligned arrays) give bit-identical
+    particles and, the deposit being integer, bit-identical dG."""
+    FempicEnv, ParticleState = _env_mod()
+    wl = I.te101_cavity(12, 2_000_000, 5.0, 1e4, 5, 7, dt=2e-9)   # ~13 tiles per staged CTA
+    res = []
+    for aligned in (True, False):
+        env = FempicEnv.from_mesh(wl.mesh, precision=MIXED)
+        st = ParticleState.from_host(wl.particles, MIXED)
+        if not aligned:
+            for k in ("x", "y", "z", "vx", "vy", "vz", "tet", "status", "n_cross"):
+                setattr(st, k, _unaligned_copy(getattr(st, k)))
+        env.locate(st)
+        e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+        b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+        G = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+        for n in range(wl.steps):
+            env.push_step(st, e, b, wl.amp(n * wl.dt), wl.omega0, n * wl.dt, wl.dt)
+            env.deposit(wl.omega0, (n + 1) * wl.dt, G_cum_out=G)
+        torch.cuda.synchronize()
+        res.append((st.to_numpy(), G.cpu().numpy(), env.stats()))
+        env.close()
+    (a, Ga, sa), (b_, Gb, sb) = res
+    for k in a:
+        assert np.array_equal(a[k], b_[k]), k
+    assert np.array_equal(Ga, Gb)
+    assert sa["crossings"] == sb["crossings"] > 0 and sa["wait_timeouts"] == sb["wait_timeouts"] == 0
