@@ -1,0 +1,165 @@
+"""Gradients of the kinetic energy after K particle steps (reverse mode).
+
+Every derivative is computed by the library's kernels
+(`fempic_push_step_adjoint`, `fempic_kinetic_energy`); this module only
+schedules them: a forward pass that keeps a checkpoint of the particle state
+every `every` steps, then a reverse sweep that, segment by segment from the
+last, recomputes the segment's states from its checkpoint and runs the adjoint
+steps backwards.  Memory: one state per checkpoint plus `every` + 1 states for
+the segment being reversed.
+
+The derivative is that of the piecewise smooth map for the tet sequence the
+forward run took (a particle that crosses a face keeps the crossing; a
+perturbation that would change the sequence is outside what it describes).
+Complex DoF gradients follow dL/dRe + j dL/dIm, the convention torch uses for
+real losses of complex tensors.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import capi
+from .capi import FEMPIC_FP64
+from .env import FempicEnv, ParticleState, _ptr, _stream
+
+
+class AdjointState:
+    """Adjoint of the particle state: rbar (f64) and vbar (velocity dtype)."""
+
+    def __init__(self, n: int, vdtype, device="cuda"):
+        z = lambda dt: torch.zeros(n, dtype=dt, device=device)
+        self.rx, self.ry, self.rz = z(torch.float64), z(torch.float64), z(torch.float64)
+        self.vx, self.vy, self.vz = z(vdtype), z(vdtype), z(vdtype)
+        self.n = n
+
+    def cstruct(self) -> capi.fempic_adjoint:
+        a = capi.fempic_adjoint()
+        a.n = self.n
+        a.rx, a.ry, a.rz = _ptr(self.rx), _ptr(self.ry), _ptr(self.rz)
+        a.vx, a.vy, a.vz = _ptr(self.vx), _ptr(self.vy), _ptr(self.vz)
+        return a
+
+
+def clone_state(st: ParticleState) -> ParticleState:
+    c = lambda t: None if t is None else t.clone()
+    o = ParticleState(c(st.x), c(st.y), c(st.z), c(st.vx), c(st.vy), c(st.vz), st.species_begin, st.q, st.m, st.w,
+                      tet=c(st.tet), track_crossings=st.n_cross is not None)
+    o.status = st.status.clone()
+    if st.n_cross is not None:
+        o.n_cross = st.n_cross.clone()
+    return o
+
+
+def kinetic_energy(env: FempicEnv, st: ParticleState, seed: AdjointState | None = None, stream=None):
+    """Total kinetic energy (device f64 scalar); fills `seed` with its adjoint."""
+    ke = torch.empty((), dtype=torch.float64, device=st.x.device)
+    capi.fempic_kinetic_energy(env.h, st.cstruct(), _ptr(ke), seed.cstruct() if seed is not None else None,
+                               _stream(stream))
+    return ke
+
+
+@dataclasses.dataclass
+class Schedule:
+    """Envelope and time stepping of a gradient window."""
+    amp: object            # callable t -> a(t)
+    omega0: float
+    dt: float
+    steps: int
+    every: int = 10        # checkpoint interval
+    t0: float = 0.0
+
+
+def _step(env, st, e, b, sch: Schedule, k: int):
+    t = sch.t0 + k * sch.dt
+    env.push_step(st, e, b, sch.amp(t), sch.omega0, t, sch.dt)
+    env.reset_deposit()
+
+
+def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule):
+    """Run sch.steps steps from a copy of st0; returns (final state, checkpoints)."""
+    st = clone_state(st0)
+    ckpts = []
+    for k in range(sch.steps):
+        if k % sch.every == 0:
+            ckpts.append(clone_state(st))
+        _step(env, st, e, b, sch, k)
+    return st, ckpts
+
+
+def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState):
+    """Propagate `adj` (adjoint of the final state) back to the initial state;
+    returns the complex128 gradients of the edge and face DoFs."""
+    eg = torch.zeros(env.n_edges, dtype=torch.complex128, device=e.device)
+    bg = torch.zeros(env.n_faces, dtype=torch.complex128, device=b.device)
+    stream = _stream(None)
+    for s in range(len(ckpts) - 1, -1, -1):
+        k0 = s * sch.every
+        k1 = min(sch.steps, k0 + sch.every)
+        stash = [ckpts[s]]
+        cur = clone_state(ckpts[s])
+        for k in range(k0, k1):
+            _step(env, cur, e, b, sch, k)
+            stash.append(clone_state(cur))
+        for k in range(k1 - 1, k0 - 1, -1):
+            j = k - k0
+            t = sch.t0 + k * sch.dt
+            envl = capi.fempic_envelope(_ptr(e), _ptr(b), float(sch.amp(t)))
+            capi.fempic_push_step_adjoint(env.h, stash[j].cstruct(), stash[j + 1].cstruct(), envl, sch.omega0, t,
+                                          sch.dt, adj.cstruct(), _ptr(eg), _ptr(bg), stream)
+        del stash, cur
+    return eg, bg
+
+
+def kinetic_energy_and_grad(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule):
+    """(L, dL/de, dL/db, adjoint of the initial state) for L = kinetic energy
+    after sch.steps steps from st0 (st0 is not modified)."""
+    final, ckpts = forward_checkpointed(env, st0, e, b, sch)
+    vdt = torch.float64 if env.precision == FEMPIC_FP64 else torch.float32
+    adj = AdjointState(st0.n, vdt, device=st0.x.device)
+    L = kinetic_energy(env, final, seed=adj)
+    eg, bg = reverse_sweep(env, ckpts, e, b, sch, adj)
+    return L, eg, bg, adj
+
+
+class KineticEnergyAfterSteps(torch.autograd.Function):
+    """L = total kinetic energy after `sch.steps` particle steps, as a
+    differentiable function of the envelope DoFs (e, b) and the initial
+    positions and velocities.  The forward keeps checkpoints; the backward
+    runs the reverse sweep on the device."""
+
+    @staticmethod
+    def forward(ctx, e, b, x, y, z, vx, vy, vz, env: FempicEnv, template: ParticleState, sch: Schedule):
+        st0 = ParticleState(x.detach(), y.detach(), z.detach(), vx.detach(), vy.detach(), vz.detach(),
+                            template.species_begin, template.q, template.m, template.w, tet=template.tet.clone(),
+                            track_crossings=False)
+        st0.status = template.status.clone()
+        final, ckpts = forward_checkpointed(env, st0, e.detach(), b.detach(), sch)
+        ctx.env, ctx.sch, ctx.ckpts, ctx.final = env, sch, ckpts, final
+        ctx.e, ctx.b = e.detach(), b.detach()
+        ctx.dtypes = (e.dtype, b.dtype)
+        return kinetic_energy(env, final).clone()
+
+    @staticmethod
+    def backward(ctx, gL):
+        env, sch = ctx.env, ctx.sch
+        vdt = torch.float64 if env.precision == FEMPIC_FP64 else torch.float32
+        adj = AdjointState(ctx.final.n, vdt, device=ctx.final.x.device)
+        kinetic_energy(env, ctx.final, seed=adj)
+        eg, bg = reverse_sweep(env, ctx.ckpts, ctx.e, ctx.b, sch, adj)
+        g = gL.to(torch.float64)
+        return ((eg * g).to(ctx.dtypes[0]), (bg * g).to(ctx.dtypes[1]),
+                adj.rx * g, adj.ry * g, adj.rz * g,
+                adj.vx * g.to(vdt), adj.vy * g.to(vdt), adj.vz * g.to(vdt), None, None, None)
+
+
+def grad_dot(eg, bg, adj: AdjointState, de, db, tr, tv) -> float:
+    """<gradient, direction> for a direction over (e, b, r0, v0) given as
+    numpy arrays (de, db complex; tr, tv [n, 3])."""
+    s = float(np.sum(eg.real * de.real + eg.imag * de.imag))
+    s += float(np.sum(bg.real * db.real + bg.imag * db.imag))
+    r = np.stack([adj.rx.cpu().numpy(), adj.ry.cpu().numpy(), adj.rz.cpu().numpy()], 1)
+    v = np.stack([adj.vx.cpu().numpy(), adj.vy.cpu().numpy(), adj.vz.cpu().numpy()], 1).astype(np.float64)
+    return s + float(np.sum(r * tr)) + float(np.sum(v * tv))

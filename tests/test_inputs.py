@@ -92,3 +92,12 @@ def test_seeded_loads_reproducible():
     assert np.array_equal(a.x, b.x) and np.array_equal(a.vz, b.vz)
     sig = I.thermal_sigma(1.0, I.M_ELECTRON)
     assert abs(np.std(np.r_[a.vx, a.vy, a.vz]) / sig - 1) < 0.05
+
+
+def test_complex_gradient_convention_matches_torch():
+    """For real L of complex z, torch's gradient is dL/dRe + j dL/dIm: for
+    L = |z|^2 that is 2z, the convention the adjoint returns."""
+    torch = pytest.importorskip("torch")
+    z = torch.tensor([1.5 - 2.0j, -0.25 + 0.5j], dtype=torch.complex128, requires_grad=True)
+    (z.abs() ** 2).sum().backward()
+    assert torch.allclose(z.grad, 2 * z.detach())
