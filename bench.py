@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-particles", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient-window measurement")
     return ap.parse_args()
 
 
@@ -275,12 +276,55 @@ def run_ours(args):
     mixed["h2d"], mixed["d2h"] = h2d, d2h
     env.close()
 
+    adj = None if args.no_adjoint else adjoint_window(rank)
     if rank == 0:
         cpu = None if (args.no_cpu or world > 1) else cpu_baseline(wl, args.cpu_particles, args.cpu_steps)
-        report(args, world, n_p, out, cpu)
+        report(args, world, n_p, out, cpu, adj)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def adjoint_window(rank):
+    """Gradient of the kinetic energy after K = 50 steps on the 48^3 cube with
+    4M electrons at 5 eV, checkpoints every 10 (the differentiation
+    workload): forward with checkpoints, then the reverse sweep (segment
+    recompute + adjoint steps), both forms, timed with CUDA events."""
+    import torch
+    from paper_2208_12795_gb300 import adjoint as A, inputs as I
+    from paper_2208_12795_gb300.env import FempicEnv, ParticleState
+    wl = I.workload_adjoint48()
+    res = {}
+    for form, prec in (("mixed", 1), ("fp64", 0)):
+        env = FempicEnv.from_mesh(wl.mesh, precision=prec)
+        st0 = ParticleState.from_host(wl.particles, prec, track_crossings=False)
+        env.locate(st0)
+        sc = st0.empty_like()
+        env.sort(st0, sc)
+        e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+        b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+        sch = A.Schedule(wl.amp, wl.omega0, wl.dt, wl.steps, 10)
+        A.kinetic_energy_and_grad(env, st0, e, b, A.Schedule(wl.amp, wl.omega0, wl.dt, 4, 2))   # warm-up
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        final, ckpts = A.forward_checkpointed(env, st0, e, b, sch)
+        ev[1].record()
+        vdt = torch.float64 if prec == 0 else torch.float32
+        adj = A.AdjointState(st0.n, vdt)
+        A.kinetic_energy(env, final, seed=adj)
+        A.reverse_sweep(env, ckpts, e, b, sch, adj)
+        ev[2].record()
+        torch.cuda.synchronize()
+        t_fwd, t_rev = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+        units = st0.n * sch.steps
+        res[form] = {"forward_particle_steps_per_s": units / t_fwd,
+                     "reverse_particle_steps_per_s": units / t_rev,
+                     "gradient_window_s": t_fwd + t_rev}
+        env.close()
+    return {"workload": "cube48_4M_adjoint: 48^3x6 cube, 4M electrons at 5 eV, TE101 10 kV/m, K=50, "
+                        "checkpoint every 10; loss = kinetic energy after K steps",
+            "unit": "particle-steps/s", **res}
 
 
 def cpu_baseline(wl, n_sample, steps):
@@ -301,7 +345,7 @@ def cpu_baseline(wl, n_sample, steps):
                       f"({el:.1f} s)"}
 
 
-def report(args, world, n_p, out, cpu):
+def report(args, world, n_p, out, cpu, adj=None):
     peak, peak_src = measured_peaks()
     m = out["mixed"]
     K = args.steps
@@ -363,6 +407,8 @@ def report(args, world, n_p, out, cpu):
         rec["fp64_form"] = {"value": total / (f["ms"] / 1e3), "ms_per_step": f["ms"] / K,
                             "push_avg_launch_ms": tf * 1e3, "hbm_frac": bf / tf / 1e9 / peak,
                             "clocks": f["clocks"]}
+    if adj is not None:
+        rec["adjoint"] = adj
     if cpu is not None:
         rec["cpu_baseline"] = cpu
     print(json.dumps(rec), flush=True)

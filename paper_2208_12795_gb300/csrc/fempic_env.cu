@@ -70,6 +70,16 @@ struct Species {
   double qw[kMaxSpecies];   // q w
 };
 
+// Record of a particle that leaves its home tet: written by the common path
+// into its tile's region of the crossing queue (contiguous, so the crossing
+// kernel reads it coalesced instead of re-reading the SoA sparsely).
+struct __align__(16) CrossRec {
+  double a[3];
+  float v[3];
+  int32_t T;
+  int32_t p;
+};
+
 struct PushArgs {
   int64_t n;
   double* x;
@@ -94,9 +104,11 @@ struct PushArgs {
   const int4* te;
   const void* field;
   double* dG;                   // FP64 form accumulator [Ne]
-  unsigned long long* dGq;      // mixed form accumulators [ns][Ne], units of 2^-48 (q w)
+  unsigned long long* dGq;      // mixed form: per (species, tet) slots of the 6 local edges,
+                                // [ns][nt][8] int64 in units of 2^-48 (q w)
   unsigned long long* stats;    // [0] crossings, [1] frozen, [2] staging wait timeouts
-  uint32_t* leave;              // mixed form: bit (p % 32) of word p / 32 = particle p leaves its tet
+  CrossRec* xrec;               // mixed form: crossing records, 256-slot region per tile
+  int32_t* xcount;              // mixed form: records per tile
 };
 
 __device__ __forceinline__ int species_of(const Species& sp, int64_t p) {
@@ -531,13 +543,19 @@ __device__ __forceinline__ void gq(const int32_t a[4], const int32_t b[4], long 
   }
 }
 
+// The mixed form deposits into one 64-byte slot per (species, tet): the 6
+// local edges of the tet, contiguous, so a run head touches 2 sectors instead
+// of 6 scattered edge entries; k_deposit_finalize pulls each edge's sum from
+// the slots of its incident tets.
+__device__ __forceinline__ unsigned long long* tet_slot(const PushArgs& A, int s, int32_t T) {
+  return A.dGq + ((int64_t)s * A.nt + T) * 8;
+}
+
 __device__ __forceinline__ void depositq_atomic(const PushArgs& A, int32_t T, int s, const long long g[6]) {
-  const int4 e0 = __ldg(&A.te[2 * (int64_t)T]), e1 = __ldg(&A.te[2 * (int64_t)T + 1]);
-  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
-  unsigned long long* base = A.dGq + (int64_t)s * A.ne;
+  unsigned long long* base = tet_slot(A, s, T);
 #pragma unroll
   for (int e = 0; e < 6; e++)
-    if (g[e]) atomicAdd(base + eid[e], (unsigned long long)g[e]);
+    if (g[e]) atomicAdd(base + e, (unsigned long long)g[e]);
 }
 
 // Position after the push: the one FP64 operation of the common path.  Both
@@ -550,12 +568,18 @@ __device__ __forceinline__ double advance(double a, float dt32, float v) {
 // Per-lane result of the common path, consumed by the warp epilogue.
 struct LaneOut {
   long long gh[6];     // one-segment deposit (home tet)
-  int4 e0, e1;         // edge ids of the home tet (loaded with its record)
   int32_t key;         // (home tet, species) run key; negative = no deposit
   int32_t Thome;
   int shome;
-  bool queue;          // leaves its tet: marked for k_cross_mixed
+  bool queue;          // leaves its tet: tracked in the CTA's crossing phase
   unsigned nfrz;
+  double a[3];         // start point and new velocity of a leaving particle
+  float v[3];
+  int32_t T;
+};
+
+struct CrossList {
+  int32_t total;     // records of the current tile
 };
 
 __device__ __forceinline__ void lane_init(LaneOut& o, int lane) {
@@ -572,8 +596,8 @@ __device__ __forceinline__ void lane_init(LaneOut& o, int lane) {
 // Boris, position update and the barycentric integers of both ends in the
 // home tet.  A particle that stays in its tet writes its new state and keeps
 // its one-segment deposit for the warp reduction; a particle that leaves it
-// stores its new velocity, keeps its start point, and is marked in the leave
-// mask for k_cross_mixed.
+// stores its new velocity and hands (start point, velocity, tet) to the
+// CTA's crossing list.
 __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int32_t T, double ax, double ay,
                                                double az, float v0, float v1, float v2, LaneOut& o) {
   if (T >= A.nt) {
@@ -588,8 +612,6 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   const float4* R = A.tetrec + 8 * (int64_t)T;
   const Geo32 G = Geo32{__ldg(R), __ldg(R + 1), __ldg(R + 2), __ldg(R + 3)};
   const float4 f0 = __ldg(R + 4), f1 = __ldg(R + 5), f2 = __ldg(R + 6);
-  o.e0 = __ldg(&A.te[2 * (int64_t)T]);
-  o.e1 = __ldg(&A.te[2 * (int64_t)T + 1]);
   const FF rs[3] = {split_f64(ax), split_f64(ay), split_f64(az)};
   float dx, dy, dz;
   dpos32(G, rs, dx, dy, dz);
@@ -628,6 +650,13 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   static_cast<float*>(A.vz)[p] = vn2;
   if ((Qb[0] | Qb[1] | Qb[2] | Qb[3]) < 0) {
     o.queue = true;
+    o.a[0] = ax;
+    o.a[1] = ay;
+    o.a[2] = az;
+    o.v[0] = vn0;
+    o.v[1] = vn1;
+    o.v[2] = vn2;
+    o.T = T;
     return;
   }
   gq(Qa, Qb, o.gh);
@@ -639,16 +668,31 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   A.z[p] = b2;
 }
 
-// Warp epilogue (all 32 lanes): record which lanes leave their tet in the
-// warp's word of the leave mask (no atomics: the word index is p / 32),
-// reduce the one-segment deposits over runs of equal (tet, species)
+// Warp epilogue (all 32 lanes): append the lanes that leave their tet to the
+// CTA's crossing list (one shared-memory atomic per warp), reduce the
+// one-segment deposits over runs of equal (tet, species)
 // keys (particles are sorted by tet, so neighbouring lanes usually share
 // one), and flush one int64 atomic per edge and run.
-__device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p, int lane, LaneOut& o) {
+__device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p, int lane, LaneOut& o,
+                                                    CrossList& cl) {
   const unsigned full = 0xffffffffu;
-  // every warp writes its own word of the leave mask (p is 32-aligned per warp)
   const unsigned qmask = __ballot_sync(full, o.queue);
-  if (lane == 0 && p < A.n) A.leave[p >> 5] = qmask;
+  if (qmask) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&cl.total, __popc(qmask));
+    base = __shfl_sync(full, base, 0);
+    if (o.queue) {
+      CrossRec& r = A.xrec[(p & ~(int64_t)(kThreads - 1)) + base + __popc(qmask & ((1u << lane) - 1u))];
+      r.a[0] = o.a[0];
+      r.a[1] = o.a[1];
+      r.a[2] = o.a[2];
+      r.v[0] = o.v[0];
+      r.v[1] = o.v[1];
+      r.v[2] = o.v[2];
+      r.T = o.T;
+      r.p = (int32_t)p;
+    }
+  }
   const int32_t prev = __shfl_up_sync(full, o.key, 1);
   const bool head = lane == 0 || prev != o.key;
   const unsigned heads = __ballot_sync(full, head);
@@ -663,22 +707,34 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
     }
   }
   if (head && o.key >= 0) {
-    const int32_t eid[6] = {o.e0.x, o.e0.y, o.e0.z, o.e0.w, o.e1.x, o.e1.y};
-    unsigned long long* base = A.dGq + (int64_t)o.shome * A.ne;
+    unsigned long long* base = tet_slot(A, o.shome, o.Thome);
 #pragma unroll
     for (int e = 0; e < 6; e++)
-      if (o.gh[e]) atomicAdd(base + eid[e], (unsigned long long)o.gh[e]);
+      if (o.gh[e]) atomicAdd(base + e, (unsigned long long)o.gh[e]);
   }
   const unsigned nf = __reduce_add_sync(full, o.nfrz);
   if (lane == 0 && nf) atomicAdd(A.stats + 1, (unsigned long long)nf);
 }
 
+// End of a tile (all threads, after the tile's epilogues): publish the tile's
+// record count for the crossing kernel and reset the counter.
+__device__ __forceinline__ void publish_tile(const PushArgs& A, CrossList& cl, int64_t tile) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    A.xcount[tile] = cl.total;
+    cl.total = 0;
+  }
+}
+
 // Common path, one particle per thread, state read straight from global
 // memory.  Used when the particle arrays are not 16-byte aligned (so bulk
 // copies cannot stage them) and for a ragged last tile.
-__global__ void __launch_bounds__(kThreads, 4) k_push_mixed(PushArgs A, int64_t p0) {
+__global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A, int64_t p0) {
+  __shared__ CrossList cl;
   const int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) cl.total = 0;
+  __syncthreads();
   LaneOut o;
   lane_init(o, lane);
   if (p < A.n) {
@@ -692,7 +748,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_mixed(PushArgs A, int64_t 
       mixed_particle(A, p, T, 0.0, 0.0, 0.0, 0.f, 0.f, 0.f, o);
     }
   }
-  mixed_warp_epilogue(A, p, lane, o);
+  mixed_warp_epilogue(A, p, lane, o, cl);
+  publish_tile(A, cl, (p0 >> 8) + blockIdx.x);
 }
 
 // ------------------------------------------------- staged common path (TMA)
@@ -740,6 +797,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Non-blocking check that phase `parity` of `bar` has completed.
+__device__ __forceinline__ bool mbar_peek(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -772,13 +844,24 @@ __device__ __forceinline__ void stage_tile(const PushArgs& A, unsigned char* sta
   bulk_g2s(stage + kTile * 36, A.tet + p0, kTile * 4, bar);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_push_mixed_tma(PushArgs A, int64_t ntiles) {
+#ifndef FEMPIC_USE_TMA
+#define FEMPIC_USE_TMA 1
+#endif
+#ifndef FEMPIC_PREFETCH_NEXT
+#define FEMPIC_PREFETCH_NEXT 0
+#endif
+#ifndef FEMPIC_TMA_MIN_BLOCKS
+#define FEMPIC_TMA_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_tma(PushArgs A, int64_t ntiles) {
   __shared__ __align__(128) unsigned char smem[kStages][kStageBytes];
   __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ CrossList cl;
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
     for (int k = 0; k < kStages; k++) mbar_init(&bar[k], 1);
     mbar_fence_init();
+    cl.total = 0;
   }
   __syncthreads();
   const int64_t stride = gridDim.x;
@@ -820,34 +903,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_push_mixed_tma(PushArgs A, int6
     const float v1 = reinterpret_cast<const float*>(S + kTile * 28)[tid];
     const float v2 = reinterpret_cast<const float*>(S + kTile * 32)[tid];
     const int32_t T = reinterpret_cast<const int32_t*>(S + kTile * 36)[tid];
+#if FEMPIC_PREFETCH_NEXT
+    {
+      // warm L1 with the tet records of the next tile if its stage has landed
+      const int nst = (st + 1) % kStages;
+      if (tile + stride < ntiles && mbar_peek(&bar[nst], (phase >> nst) & 1u)) {
+        const int32_t Tn = reinterpret_cast<const int32_t*>(smem[nst] + kTile * 36)[tid];
+        if (Tn >= 0 && Tn < A.nt) prefetch_l1(A.tetrec + 8 * (int64_t)Tn);
+      }
+    }
+#endif
     const int64_t p = tile * kTile + tid;
     LaneOut o;
     lane_init(o, lane);
     mixed_particle(A, p, T, ax, ay, az, v0, v1, v2, o);
-    mixed_warp_epilogue(A, p, lane, o);
+    mixed_warp_epilogue(A, p, lane, o, cl);
+    publish_tile(A, cl, tile);
     st = (st + 1) % kStages;
   }
 }
 
-// Crossing path for the particles the common path marked in the leave mask
-// this step (grid-stride over mask words, one word per thread): rebuild b,
-// split the segment at every face it crosses, deposit each in-tet piece,
-// reflect or absorb at walls.
-__global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A) {
-  const int lane = threadIdx.x & 31;
-  unsigned ncr = 0, nfrz = 0;
-  const int64_t nwords = (A.n + 31) >> 5;
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords;
-       w += (int64_t)gridDim.x * blockDim.x) {
-  for (uint32_t bits = A.leave[w]; bits; bits &= bits - 1u) {
-    const int64_t p = (w << 5) + (__ffs(bits) - 1);
-    int32_t T = A.tet[p];
+// Crossing path of one particle that leaves its home tet (from its record in
+// the crossing queue): rebuild b, split the segment at every face it
+// crosses, deposit each in-tet piece, reflect or absorb at walls, write the
+// final state.
+__device__ __forceinline__ void cross_particle(const PushArgs& A, int64_t p, int32_t T, double ax, double ay, double az,
+                                            float v0, float v1, float v2, unsigned& ncr, unsigned& nfrz) {
+  {
     const int s = species_of(A.sp, p);
     float* vxp = static_cast<float*>(A.vx);
     float* vyp = static_cast<float*>(A.vy);
     float* vzp = static_cast<float*>(A.vz);
-    double a0[3] = {A.x[p], A.y[p], A.z[p]};   // start of the current straight piece
-    float vn[3] = {vxp[p], vyp[p], vzp[p]};
+    double a0[3] = {ax, ay, az};   // start of the current straight piece
+    float vn[3] = {v0, v1, v2};
     const float dt32 = (float)A.dt;
     double b[3] = {advance(a0[0], dt32, vn[0]), advance(a0[1], dt32, vn[1]), advance(a0[2], dt32, vn[2])};
     int32_t Qa[4], Qb[4], Qp[4];
@@ -985,6 +1073,20 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A) {
     if (A.ncross) A.ncross[p] += nc;
     ncr += (unsigned)nc;
   }
+}
+
+// Crossing pass of the mixed form: one warp per 256-particle tile region of
+// the queue, lanes taking its records in turn.
+__global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t ntiles) {
+  const int lane = threadIdx.x & 31;
+  unsigned ncr = 0, nfrz = 0;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
+    const int32_t cnt = A.xcount[t];
+    for (int32_t i = lane; i < cnt; i += 32) {
+      const CrossRec r = A.xrec[t * kThreads + i];
+      cross_particle(A, r.p, r.T, r.a[0], r.a[1], r.a[2], r.v[0], r.v[1], r.v[2], ncr, nfrz);
+    }
   }
   const unsigned full = 0xffffffffu;
   ncr = __reduce_add_sync(full, ncr);
@@ -1001,6 +1103,9 @@ struct FinalizeArgs {
   int32_t mixed;
   int32_t ns;
   double qwscale[kMaxSpecies];   // q w 2^-48 per species (mixed form)
+  int64_t nt;
+  const int32_t* inc_start;      // mixed form: edge -> incident (tet, local edge) slots, CSR
+  const int32_t* inc;            //   entries T * 8 + k
   double* dG;
   unsigned long long* dGq;
   double* Gcum;
@@ -1015,11 +1120,18 @@ __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
   if (e >= A.ne) return;
   double d;
   if (A.mixed) {
+    // pull the edge's sum from its incident tet slots (each slot belongs to
+    // exactly one edge, which also clears it for the next step)
     d = 0.0;
+    const int32_t i0 = A.inc_start[e], i1 = A.inc_start[e + 1];
     for (int s = 0; s < A.ns; s++) {
-      const long long q = (long long)A.dGq[(int64_t)s * A.ne + e];
+      unsigned long long* base = A.dGq + (int64_t)s * A.nt * 8;
+      long long q = 0;
+      for (int32_t i = i0; i < i1; i++) {
+        q += (long long)base[A.inc[i]];
+        base[A.inc[i]] = 0ull;
+      }
       d += A.qwscale[s] * (double)q;
-      A.dGq[(int64_t)s * A.ne + e] = 0ull;
     }
   } else {
     d = A.dG[e];
@@ -1515,18 +1627,22 @@ struct fempic_env {
   int4* tf = nullptr;
   void* field = nullptr;
   double* dG = nullptr;
-  unsigned long long* dGq = nullptr;
+  unsigned long long* dGq = nullptr;   // mixed form [dGq_species][nt][8]
   int32_t dGq_species = 0;
+  int32_t* inc_start = nullptr;        // edge -> (tet, local edge) incidence, CSR [ne + 1]
+  int32_t* inc = nullptr;              // [6 nt] entries T * 8 + k
   double* Gcum = nullptr;
   unsigned long long* stats = nullptr;
   int64_t* gstart = nullptr;
   int32_t* gtet = nullptr;
   double qw_last[kMaxSpecies] = {0};
   int32_t ns_last = 0;
-  uint32_t* leave = nullptr;        // mixed form leave mask [leave_cap words]
   double* tetgrad = nullptr;        // adjoint of the per-tet affine field [nt][10]
-  int64_t leave_cap = 0;
+  CrossRec* xrec = nullptr;         // mixed form crossing queue [xtiles * 256]
+  int32_t* xcount = nullptr;        // [xtiles]
+  int64_t xtiles = 0;
   int num_sms = 1;
+  int tma_blocks_per_sm = 0;        // resident CTAs of the staged kernel (persistent grid)
   int64_t steps = 0;
   // per-kernel event timing (measurement support)
   struct Rec {
@@ -1579,7 +1695,8 @@ static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
-                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->leave, e->tetgrad};
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->xrec, e->xcount,
+                  e->inc_start, e->inc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete e;
@@ -1634,6 +1751,19 @@ static int upload(fempic_env* e) {
     FEMPIC_CUDA(dalloc(reinterpret_cast<double**>(&e->field), 10 * nt));
     FEMPIC_CUDA(dalloc(&e->dG, m.ne));
     FEMPIC_CUDA(cudaMemset(e->dG, 0, m.ne * sizeof(double)));
+  }
+  {
+    // edge -> (tet, local edge) incidence for the mixed form's pull finalize
+    std::vector<int32_t> start(m.ne + 1, 0), inc(6 * nt);
+    for (int64_t i = 0; i < 6 * nt; i++) start[m.te[i] + 1]++;
+    for (int64_t e2 = 0; e2 < m.ne; e2++) start[e2 + 1] += start[e2];
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    for (int64_t t = 0; t < nt; t++)
+      for (int k = 0; k < 6; k++) inc[fill[m.te[6 * t + k]]++] = (int32_t)(t * 8 + k);
+    FEMPIC_CUDA(dalloc(&e->inc_start, m.ne + 1));
+    FEMPIC_CUDA(dalloc(&e->inc, 6 * nt));
+    FEMPIC_CUDA(cudaMemcpy(e->inc_start, start.data(), (m.ne + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    FEMPIC_CUDA(cudaMemcpy(e->inc, inc.data(), 6 * nt * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   FEMPIC_CUDA(dalloc(&e->Gcum, m.ne));
   FEMPIC_CUDA(cudaMemset(e->Gcum, 0, m.ne * sizeof(double)));
@@ -1758,20 +1888,23 @@ extern "C" int fempic_locate(fempic_env* env, const fempic_particles* p, void* s
   return FEMPIC_OK;
 }
 
-// Leave mask of the mixed form: one bit per particle, grown on demand.  The
-// common path overwrites every word it covers each step, so it needs no
-// clearing.
-static int ensure_leave(fempic_env* env, int64_t n, cudaStream_t st) {
-  const int64_t words = (n + 31) / 32;
-  if (env->leave_cap >= words) return FEMPIC_OK;
-  if (env->leave) {
+// Crossing queue of the mixed form: a 256-record region per tile of 256
+// particles plus a count per tile, grown on demand (every tile count is
+// rewritten by the common path each step, so nothing needs clearing).
+static int ensure_xqueue(fempic_env* env, int64_t n, cudaStream_t st) {
+  const int64_t tiles = (n + kThreads - 1) / kThreads;
+  if (env->xtiles >= tiles) return FEMPIC_OK;
+  if (env->xrec) {
     FEMPIC_CUDA(cudaStreamSynchronize(st));
-    cudaFree(env->leave);
-    env->leave = nullptr;
-    env->leave_cap = 0;
+    cudaFree(env->xrec);
+    cudaFree(env->xcount);
+    env->xrec = nullptr;
+    env->xcount = nullptr;
+    env->xtiles = 0;
   }
-  FEMPIC_CUDA(dalloc(&env->leave, words));
-  env->leave_cap = words;
+  FEMPIC_CUDA(dalloc(&env->xrec, tiles * kThreads));
+  FEMPIC_CUDA(dalloc(&env->xcount, tiles));
+  env->xtiles = tiles;
   return FEMPIC_OK;
 }
 
@@ -1781,8 +1914,8 @@ static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
   // reallocates them, so a step must be finalized (fempic_deposit) before the
   // species table grows.
   unsigned long long* nq = nullptr;
-  FEMPIC_CUDA(dalloc(&nq, (size_t)ns * env->h.ne));
-  FEMPIC_CUDA(cudaMemsetAsync(nq, 0, (size_t)ns * env->h.ne * sizeof(unsigned long long), st));
+  FEMPIC_CUDA(dalloc(&nq, (size_t)ns * env->h.nt * 8));
+  FEMPIC_CUDA(cudaMemsetAsync(nq, 0, (size_t)ns * env->h.nt * 8 * sizeof(unsigned long long), st));
   if (env->dGq) {
     FEMPIC_CUDA(cudaStreamSynchronize(st));
     cudaFree(env->dGq);
@@ -1862,9 +1995,11 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   A.dGq = env->dGq;
   A.stats = env->stats;
   if (mixed) {
-    rc = ensure_leave(env, p->n, st);
+    rc = ensure_xqueue(env, p->n, st);
     if (rc) return rc;
-    A.leave = env->leave;
+    A.xrec = env->xrec;
+    A.xcount = env->xcount;
+
   }
   {
     LaunchTimer lt(env, st, FEMPIC_K_PUSH);
@@ -1873,16 +2008,22 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
       // particle array allows it; the ragged tail (or everything) goes plain
       const uintptr_t align = (uintptr_t)p->x | (uintptr_t)p->y | (uintptr_t)p->z | (uintptr_t)p->vx |
                               (uintptr_t)p->vy | (uintptr_t)p->vz | (uintptr_t)p->tet;
-      const int64_t ntiles = (align & 15u) ? 0 : p->n / kTile;
+      const int64_t ntiles = (FEMPIC_USE_TMA && !(align & 15u)) ? p->n / kTile : 0;
       if (ntiles > 0) {
-        const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)env->num_sms * 4);
+        if (env->tma_blocks_per_sm == 0) {
+          int nb = 0;
+          FEMPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_mixed_tma, kThreads, 0));
+          env->tma_blocks_per_sm = nb > 0 ? nb : 1;
+        }
+        const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)env->num_sms * env->tma_blocks_per_sm);
         k_push_mixed_tma<<<grid, kThreads, 0, st>>>(A, ntiles);
       }
       const int64_t rest = p->n - ntiles * kTile;
       if (rest > 0) k_push_mixed<<<blocks_for(rest), kThreads, 0, st>>>(A, ntiles * kTile);
+      const int64_t all_tiles = (p->n + kTile - 1) / kTile;
       const unsigned cross_blocks =
-          (unsigned)std::min<int64_t>(blocks_for((p->n + 31) / 32), (int64_t)env->num_sms * 8);
-      k_cross_mixed<<<cross_blocks, kThreads, 0, st>>>(A);
+          (unsigned)std::min<int64_t>((all_tiles + 7) / 8, (int64_t)env->num_sms * 8);
+      k_cross_mixed<<<cross_blocks, kThreads, 0, st>>>(A, all_tiles);
     } else {
       k_push_fp64<<<blocks_for(p->n), kThreads, 0, st>>>(A);
     }
@@ -1901,6 +2042,9 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
   A.mixed = mixed;
   A.ns = mixed ? (env->dGq ? env->ns_last : 0) : 0;
   for (int s = 0; s < kMaxSpecies; s++) A.qwscale[s] = env->qw_last[s] * 0x1p-48;
+  A.nt = env->h.nt;
+  A.inc_start = env->inc_start;
+  A.inc = env->inc;
   A.dG = env->dG;
   A.dGq = env->dGq;
   A.Gcum = env->Gcum;
@@ -1924,7 +2068,8 @@ extern "C" int fempic_reset_deposit(fempic_env* env, void* stream) {
   FEMPIC_CUDA(cudaMemsetAsync(env->Gcum, 0, env->h.ne * sizeof(double), st));
   if (env->dG) FEMPIC_CUDA(cudaMemsetAsync(env->dG, 0, env->h.ne * sizeof(double), st));
   if (env->dGq)
-    FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)env->dGq_species * env->h.ne * sizeof(unsigned long long), st));
+    FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)env->dGq_species * env->h.nt * 8 * sizeof(unsigned long long),
+                                st));
   return FEMPIC_OK;
 }
 
