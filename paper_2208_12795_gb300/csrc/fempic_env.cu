@@ -797,21 +797,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Non-blocking check that phase `parity` of `bar` has completed.
-__device__ __forceinline__ bool mbar_peek(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -846,9 +831,6 @@ __device__ __forceinline__ void stage_tile(const PushArgs& A, unsigned char* sta
 
 #ifndef FEMPIC_USE_TMA
 #define FEMPIC_USE_TMA 1
-#endif
-#ifndef FEMPIC_PREFETCH_NEXT
-#define FEMPIC_PREFETCH_NEXT 0
 #endif
 #ifndef FEMPIC_TMA_MIN_BLOCKS
 #define FEMPIC_TMA_MIN_BLOCKS 3
@@ -903,16 +885,6 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_
     const float v1 = reinterpret_cast<const float*>(S + kTile * 28)[tid];
     const float v2 = reinterpret_cast<const float*>(S + kTile * 32)[tid];
     const int32_t T = reinterpret_cast<const int32_t*>(S + kTile * 36)[tid];
-#if FEMPIC_PREFETCH_NEXT
-    {
-      // warm L1 with the tet records of the next tile if its stage has landed
-      const int nst = (st + 1) % kStages;
-      if (tile + stride < ntiles && mbar_peek(&bar[nst], (phase >> nst) & 1u)) {
-        const int32_t Tn = reinterpret_cast<const int32_t*>(smem[nst] + kTile * 36)[tid];
-        if (Tn >= 0 && Tn < A.nt) prefetch_l1(A.tetrec + 8 * (int64_t)Tn);
-      }
-    }
-#endif
     const int64_t p = tile * kTile + tid;
     LaneOut o;
     lane_init(o, lane);
@@ -1103,11 +1075,8 @@ struct FinalizeArgs {
   int32_t mixed;
   int32_t ns;
   double qwscale[kMaxSpecies];   // q w 2^-48 per species (mixed form)
-  int64_t nt;
-  const int32_t* inc_start;      // mixed form: edge -> incident (tet, local edge) slots, CSR
-  const int32_t* inc;            //   entries T * 8 + k
   double* dG;
-  unsigned long long* dGq;
+  unsigned long long* dGe;       // mixed form: per-edge int64 sums [ns][ne] (from the slot flush)
   double* Gcum;
   double* dG_out;
   double* Gcum_out;
@@ -1115,23 +1084,42 @@ struct FinalizeArgs {
   double c, s;                   // cos, sin of omega0 t_next
 };
 
+// Mixed form, first half of the finalize: each (species, tet) slot of 6 local
+// edge sums is read coalesced, cleared, and added to its edges' int64 sums
+// (integer atomics: exact and independent of order).
+__global__ void __launch_bounds__(kThreads) k_slot_flush(int64_t nslots, int64_t nt, int64_t ne,
+                                                          unsigned long long* __restrict__ slots,
+                                                          const int4* __restrict__ te,
+                                                          unsigned long long* __restrict__ dGe) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nslots) return;
+  ulonglong2* sl = reinterpret_cast<ulonglong2*>(slots + 8 * i);
+  const ulonglong2 a = sl[0], b = sl[1], c = sl[2];
+  if ((a.x | a.y | b.x | b.y | c.x | c.y) == 0ull) return;
+  sl[0] = make_ulonglong2(0ull, 0ull);
+  sl[1] = make_ulonglong2(0ull, 0ull);
+  sl[2] = make_ulonglong2(0ull, 0ull);
+  const int64_t s = i / nt, t = i - s * nt;
+  const int4 e0 = te[2 * t], e1 = te[2 * t + 1];
+  unsigned long long* base = dGe + s * ne;
+  if (a.x) atomicAdd(base + e0.x, a.x);
+  if (a.y) atomicAdd(base + e0.y, a.y);
+  if (b.x) atomicAdd(base + e0.z, b.x);
+  if (b.y) atomicAdd(base + e0.w, b.y);
+  if (c.x) atomicAdd(base + e1.x, c.x);
+  if (c.y) atomicAdd(base + e1.y, c.y);
+}
+
 __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= A.ne) return;
   double d;
   if (A.mixed) {
-    // pull the edge's sum from its incident tet slots (each slot belongs to
-    // exactly one edge, which also clears it for the next step)
     d = 0.0;
-    const int32_t i0 = A.inc_start[e], i1 = A.inc_start[e + 1];
     for (int s = 0; s < A.ns; s++) {
-      unsigned long long* base = A.dGq + (int64_t)s * A.nt * 8;
-      long long q = 0;
-      for (int32_t i = i0; i < i1; i++) {
-        q += (long long)base[A.inc[i]];
-        base[A.inc[i]] = 0ull;
-      }
+      const long long q = (long long)A.dGe[(int64_t)s * A.ne + e];
       d += A.qwscale[s] * (double)q;
+      A.dGe[(int64_t)s * A.ne + e] = 0ull;
     }
   } else {
     d = A.dG[e];
@@ -1629,8 +1617,7 @@ struct fempic_env {
   double* dG = nullptr;
   unsigned long long* dGq = nullptr;   // mixed form [dGq_species][nt][8]
   int32_t dGq_species = 0;
-  int32_t* inc_start = nullptr;        // edge -> (tet, local edge) incidence, CSR [ne + 1]
-  int32_t* inc = nullptr;              // [6 nt] entries T * 8 + k
+  unsigned long long* dGe = nullptr;   // mixed form per-edge sums [dGq_species][ne]
   double* Gcum = nullptr;
   unsigned long long* stats = nullptr;
   int64_t* gstart = nullptr;
@@ -1696,7 +1683,7 @@ static void free_env(fempic_env* e) {
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
                   e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->xrec, e->xcount,
-                  e->inc_start, e->inc};
+                  e->dGe};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete e;
@@ -1751,19 +1738,6 @@ static int upload(fempic_env* e) {
     FEMPIC_CUDA(dalloc(reinterpret_cast<double**>(&e->field), 10 * nt));
     FEMPIC_CUDA(dalloc(&e->dG, m.ne));
     FEMPIC_CUDA(cudaMemset(e->dG, 0, m.ne * sizeof(double)));
-  }
-  {
-    // edge -> (tet, local edge) incidence for the mixed form's pull finalize
-    std::vector<int32_t> start(m.ne + 1, 0), inc(6 * nt);
-    for (int64_t i = 0; i < 6 * nt; i++) start[m.te[i] + 1]++;
-    for (int64_t e2 = 0; e2 < m.ne; e2++) start[e2 + 1] += start[e2];
-    std::vector<int32_t> fill(start.begin(), start.end() - 1);
-    for (int64_t t = 0; t < nt; t++)
-      for (int k = 0; k < 6; k++) inc[fill[m.te[6 * t + k]]++] = (int32_t)(t * 8 + k);
-    FEMPIC_CUDA(dalloc(&e->inc_start, m.ne + 1));
-    FEMPIC_CUDA(dalloc(&e->inc, 6 * nt));
-    FEMPIC_CUDA(cudaMemcpy(e->inc_start, start.data(), (m.ne + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
-    FEMPIC_CUDA(cudaMemcpy(e->inc, inc.data(), 6 * nt * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   FEMPIC_CUDA(dalloc(&e->Gcum, m.ne));
   FEMPIC_CUDA(cudaMemset(e->Gcum, 0, m.ne * sizeof(double)));
@@ -1914,13 +1888,18 @@ static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
   // reallocates them, so a step must be finalized (fempic_deposit) before the
   // species table grows.
   unsigned long long* nq = nullptr;
+  unsigned long long* ne = nullptr;
   FEMPIC_CUDA(dalloc(&nq, (size_t)ns * env->h.nt * 8));
+  FEMPIC_CUDA(dalloc(&ne, (size_t)ns * env->h.ne));
   FEMPIC_CUDA(cudaMemsetAsync(nq, 0, (size_t)ns * env->h.nt * 8 * sizeof(unsigned long long), st));
+  FEMPIC_CUDA(cudaMemsetAsync(ne, 0, (size_t)ns * env->h.ne * sizeof(unsigned long long), st));
   if (env->dGq) {
     FEMPIC_CUDA(cudaStreamSynchronize(st));
     cudaFree(env->dGq);
+    cudaFree(env->dGe);
   }
   env->dGq = nq;
+  env->dGe = ne;
   env->dGq_species = ns;
   return FEMPIC_OK;
 }
@@ -2042,11 +2021,8 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
   A.mixed = mixed;
   A.ns = mixed ? (env->dGq ? env->ns_last : 0) : 0;
   for (int s = 0; s < kMaxSpecies; s++) A.qwscale[s] = env->qw_last[s] * 0x1p-48;
-  A.nt = env->h.nt;
-  A.inc_start = env->inc_start;
-  A.inc = env->inc;
   A.dG = env->dG;
-  A.dGq = env->dGq;
+  A.dGe = env->dGe;
   A.Gcum = env->Gcum;
   A.dG_out = dG_out;
   A.Gcum_out = G_cum_out;
@@ -2056,6 +2032,12 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
   A.s = std::sin(phi);
   {
     LaunchTimer lt(env, (cudaStream_t)stream, FEMPIC_K_FINALIZE);
+    if (mixed && env->dGq) {
+      const int64_t nslots = (int64_t)A.ns * env->h.nt;
+      if (nslots > 0)
+        k_slot_flush<<<blocks_for(nslots), kThreads, 0, (cudaStream_t)stream>>>(nslots, env->h.nt, env->h.ne, env->dGq,
+                                                                                env->te, env->dGe);
+    }
     k_deposit_finalize<<<blocks_for(A.ne), kThreads, 0, (cudaStream_t)stream>>>(A);
   }
   FEMPIC_CUDA(cudaGetLastError());
@@ -2067,9 +2049,11 @@ extern "C" int fempic_reset_deposit(fempic_env* env, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   FEMPIC_CUDA(cudaMemsetAsync(env->Gcum, 0, env->h.ne * sizeof(double), st));
   if (env->dG) FEMPIC_CUDA(cudaMemsetAsync(env->dG, 0, env->h.ne * sizeof(double), st));
-  if (env->dGq)
+  if (env->dGq) {
     FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)env->dGq_species * env->h.nt * 8 * sizeof(unsigned long long),
                                 st));
+    FEMPIC_CUDA(cudaMemsetAsync(env->dGe, 0, (size_t)env->dGq_species * env->h.ne * sizeof(unsigned long long), st));
+  }
   return FEMPIC_OK;
 }
 
