@@ -32,6 +32,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (gather+push+track+deposit), FP32-mixed vs FP64, % HBM peak"
+DATA_DESC = {
+    "cube48": "synthetic (seeded): Kuhn cube mesh, TE101 envelope DoFs, uniform Maxwellian electrons",
+    "jittered64": "synthetic (seeded): jittered Kuhn cube mesh, random windowed complex DoFs, beam + plasma electrons",
+    "large96": "synthetic (seeded, generated in chunks): Kuhn cube mesh, random windowed complex DoFs, "
+               "Maxwellian electrons and ions",
+}
+WORKLOAD_DESC = {
+    "cube48": "cube48_10M_te101: 48^3x6 Kuhn cube (663,552 tets), 10M electrons at 5 eV, TE101 10 kV/m, dt 0.5 ns",
+    "jittered64": "jittered64_50M: 64^3x6 cube with interior nodes jittered +-20% (1,572,864 tets), 5M 10 keV "
+                  "electron beam along z + 45M 5 eV plasma with 1+0.5cos(2 pi x) density, random windowed DoFs, "
+                  "dt 0.5 ns",
+    "large96": "large96_400M: 96^3x6 Kuhn cube (5,308,416 tets), 200M electrons + 200M ions (1836 m_e) at 2 eV, "
+               "random windowed DoFs, dt 0.5 ns",
+}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "push_mixed_cube48_10M.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2208_12795_gb300", "csrc", f)
@@ -51,6 +65,9 @@ def parse():
     ap.add_argument("--cpu-particles", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient-window measurement")
+    ap.add_argument("--workload", choices=("cube48", "jittered64", "large96"), default="cube48",
+                    help="cube48: 48^3x6 cube, 10M e- (headline); jittered64: 64^3x6 jittered cube, 50M "
+                         "(10 keV beam + cosine plasma), random DoFs; large96: 96^3x6 cube, 400M e- + ions")
     return ap.parse_args()
 
 
@@ -175,14 +192,42 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     n_p = args.particles
-    wl = I.te101_cavity(48, n_p, 5.0, 1e4, 100, 2 + 100 * rank, name="cube48_10M_te101")
+    big_host = None
+    if args.workload == "cube48":
+        wl = I.te101_cavity(48, n_p, 5.0, 1e4, 100, 2 + 100 * rank, name="cube48_10M_te101")
+    elif args.workload == "jittered64":
+        n_p = args.particles if args.particles != 10_000_000 else 50_000_000
+        wl = I.workload_jittered64(n_p)
+        args.no_fp64 = True
+    else:
+        n_p = args.particles if args.particles != 10_000_000 else 400_000_000
+        big_host = I.large96_species(n_p)
+        wl = I.workload_large96(n_particles=2)          # mesh, DoFs, dt; particles streamed below
+        args.no_fp64 = True
+        args.no_cpu = True
     mesh = wl.mesh
     stream = torch.cuda.current_stream()
+
+    def particle_state(prec):
+        if big_host is None:
+            return ParticleState.from_host(wl.particles, prec, track_crossings=False)
+        sb, q, m, w, temp = big_host
+        vdt = torch.float64 if prec == 0 else torch.float32
+        arrs = [torch.empty(n_p, dtype=torch.float64, device="cuda") for _ in range(3)] + \
+               [torch.empty(n_p, dtype=vdt, device="cuda") for _ in range(3)]
+        chunk = 20_000_000
+        for s in range(len(q)):
+            for c0 in range(int(sb[s]), int(sb[s + 1]), chunk):
+                c1 = min(int(sb[s + 1]), c0 + chunk)
+                cols = I.maxwellian_chunk(I.SEED_BASE + 5 + 1000 * s, c0 // chunk, c1 - c0, temp, m[s])
+                for a, col in zip(arrs, cols):
+                    a[c0:c1].copy_(torch.from_numpy(np.ascontiguousarray(col)))
+        return ParticleState(*arrs, sb, q, m, w, track_crossings=False)
 
     def timed_form(form):
         prec = 1 if form == "mixed" else 0
         env = FempicEnv.from_mesh(mesh, precision=prec)
-        st = ParticleState.from_host(wl.particles, prec, track_crossings=False)
+        st = particle_state(prec)
         env.locate(st)
         scratch = st.empty_like()
         env.sort(st, scratch)                 # initial tet-sorted layout (untimed)
@@ -276,7 +321,7 @@ def run_ours(args):
     mixed["h2d"], mixed["d2h"] = h2d, d2h
     env.close()
 
-    adj = None if args.no_adjoint else adjoint_window(rank)
+    adj = None if (args.no_adjoint or args.workload != "cube48") else adjoint_window(rank)
     if rank == 0:
         cpu = None if (args.no_cpu or world > 1) else cpu_baseline(wl, args.cpu_particles, args.cpu_steps)
         report(args, world, n_p, out, cpu, adj)
@@ -369,15 +414,14 @@ def report(args, world, n_p, out, cpu, adj=None):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32+f64 mixed (FP32 gather/carrier/Boris; FP64 positions; int64 exact deposit)",
-        "data": "synthetic (seeded): Kuhn cube mesh, TE101 envelope DoFs, uniform Maxwellian electrons",
+        "data": DATA_DESC[args.workload],
         "config": {
-            "workload": "cube48_10M_te101: 48^3x6 Kuhn cube (663,552 tets), 10M electrons at 5 eV, "
-                        "TE101 10 kV/m, dt 0.5 ns",
+            "workload": WORKLOAD_DESC[args.workload],
             "form": "mixed",
             "particles_per_gpu": n_p,
             "n_tets": m["counts"][3],
             "sort_every": args.sort_every,
-            "l2": "inputs larger than L2 (particle SoA 400 MB per GPU per step)",
+            "l2": f"inputs larger than L2 (particle SoA {n_p * 41 / 1e6:.0f} MB per GPU per step)",
             "parallelism": f"particle replicas x{world}, dG summed over ranks" if world > 1 else "1 GPU",
         },
         "roofline": {

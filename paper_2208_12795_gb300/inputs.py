@@ -200,7 +200,8 @@ def te101_dofs(nodes: np.ndarray, edges: np.ndarray, faces: np.ndarray, e0: floa
 
 def random_windowed_dofs(nodes, edges, faces, rng, center=(0.5, 0.5, 0.5), width=0.25,
                          e_scale=1.0, b_scale=1.0):
-    """Unit-variance complex normal DoFs times exp(-|x_mid - c|^2 / (2 w^2))."""
+    """Unit-variance complex normal DoFs times exp(-|x_mid - c|^2 / (2 w^2)),
+    times e_scale (edges) or b_scale (faces)."""
     c = np.asarray(center, dtype=np.float64)
 
     def draw(n):
@@ -380,12 +381,19 @@ def workload_cavity48(n_particles: int = 10_000_000) -> Workload:
     return te101_cavity(48, n_particles, 5.0, 1e4, 100, 2, name="cube48_10M_te101")
 
 
+def RANDOM_DOF_UNITS(h: float) -> dict:
+    """Units of the random envelope DoFs: unit variance in 10 kV/m x h per edge
+    circulation and 10 mT x h^2 per face flux, i.e. fields of order 10 kV/m
+    and 10 mT (a literal unit-variance flux on h = 1/64 would be ~4000 T)."""
+    return dict(e_scale=1e4 * h, b_scale=1e-2 * h * h)
+
+
 def workload_jittered64(n_particles: int = 50_000_000) -> Workload:
     """64^3 x 6 jittered cube, 10% 10 keV beam + 90% cosine plasma, random DoFs, 50 steps."""
     rng = np.random.default_rng(SEED_BASE + 3)
     mesh = kuhn_cube_mesh(64, jitter=0.2, rng=rng)
     _, edges, faces, _, _ = mesh_topology(mesh.tets)
-    e_t, b_t = random_windowed_dofs(mesh.nodes, edges, faces, rng)
+    e_t, b_t = random_windowed_dofs(mesh.nodes, edges, faces, rng, **RANDOM_DOF_UNITS(mesh.h))
     nb = n_particles // 10
     parts = concat_species([electron_beam(nb, 1e4, 0.005, 0.1, rng),
                             cosine_plasma(n_particles - nb, 5.0, 0.5, rng)])
@@ -397,12 +405,30 @@ def workload_adjoint48(n_particles: int = 4_000_000) -> Workload:
     return te101_cavity(48, n_particles, 5.0, 1e4, 50, 4, name="cube48_4M_adjoint")
 
 
+def maxwellian_chunk(seed: int, chunk: int, n: int, temp_ev: float, mass: float):
+    """Chunk `chunk` (n particles) of a uniform Maxwellian load, reproducible
+    from (seed, chunk) alone so a very large load can be generated chunk by
+    chunk: returns x, y, z, vx, vy, vz (float64)."""
+    rng = np.random.default_rng([seed, chunk])
+    pos = rng.random((n, 3))
+    vel = rng.standard_normal((n, 3)) * thermal_sigma(temp_ev, mass)
+    return pos[:, 0], pos[:, 1], pos[:, 2], vel[:, 0], vel[:, 1], vel[:, 2]
+
+
+def large96_species(n_particles: int = 400_000_000):
+    """Species table of the 96^3 two-species load: electrons then ions
+    (m = 1836 m_e, q = +e), both at 2 eV, weight 1e3, half each."""
+    half = n_particles // 2
+    return (np.array([0, half, n_particles], np.int64), np.array([-E_CHARGE, E_CHARGE]),
+            np.array([M_ELECTRON, 1836.0 * M_ELECTRON]), np.array([1e3, 1e3]), 2.0)
+
+
 def workload_large96(n_particles: int = 400_000_000) -> Workload:
     """96^3 x 6 cube, electrons + heavy ions (m = 1836 m_e) at 2 eV, random DoFs, 20 steps."""
     rng = np.random.default_rng(SEED_BASE + 5)
     mesh = kuhn_cube_mesh(96)
     _, edges, faces, _, _ = mesh_topology(mesh.tets)
-    e_t, b_t = random_windowed_dofs(mesh.nodes, edges, faces, rng)
+    e_t, b_t = random_windowed_dofs(mesh.nodes, edges, faces, rng, **RANDOM_DOF_UNITS(mesh.h))
     half = n_particles // 2
     el = uniform_maxwellian(half, 2.0, rng)
     ion = uniform_maxwellian(n_particles - half, 2.0, rng, q=E_CHARGE, m=1836.0 * M_ELECTRON)

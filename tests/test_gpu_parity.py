@@ -353,3 +353,72 @@ def test_mixed_staged_path_equals_plain_path():
         assert np.array_equal(a[k], b_[k]), k
     assert np.array_equal(Ga, Gb)
     assert sa["crossings"] == sb["crossings"] > 0 and sa["wait_timeouts"] == sb["wait_timeouts"] == 0
+
+
+# ------------------------------------------- other workload shapes, sampled
+def _sampled_parity(wl, prec, n_sample, seed):
+    """One step of every particle on the GPU; n_sample particles checked one
+    by one against the oracle; conservation checked over all particles."""
+    env, st, G, rho0, rho1, tet0 = gpu_run(wl, prec, 1)
+    assert (tet0 >= 0).all()
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(wl.particles.n, n_sample, replace=False))
+    P = wl.particles
+    # keep each sampled particle's species: rebuild species ranges over the sample
+    sp = np.searchsorted(P.species_begin[1:], idx, side="right")
+    order = np.argsort(sp, kind="stable")
+    idx = idx[order]
+    sp = sp[order]
+    begins = np.searchsorted(sp, np.arange(len(P.q) + 1))
+    sub = I.Particles(P.x[idx], P.y[idx], P.z[idx], P.vx[idx], P.vy[idx], P.vz[idx],
+                      begins.astype(np.int64), P.q, P.m, P.w)
+    om = OracleMesh(wl.mesh.nodes, wl.mesh.tets, wl.mesh.lo, wl.mesh.hi)
+    ost = OracleState(sub, tet0[idx])
+    oG = np.zeros(om.n_edges)
+    oracle_push(om, ost, wl.e_tilde, wl.b_tilde, wl.amp(0.0), wl.omega0, 0.0, wl.dt, oG)
+    g = {k: v[idx] for k, v in st.to_numpy().items() if v is not None}
+    er = rel_vec_err((g["x"], g["y"], g["z"]), (ost.x, ost.y, ost.z), 1.0)
+    ev = rel_vec_err((g["vx"], g["vy"], g["vz"]), (ost.vx, ost.vy, ost.vz), 1e-30)
+    same = (g["tet"] == ost.tet).mean()
+    res = conservation_residual(env, G, rho0, rho1)
+    return same, er, ev, res, g, ost
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_full_size_jittered64_beam_plasma_sampled(prec):
+    """64^3 x 6 jittered cube, 5M 10 keV beam electrons (several face crossings
+    per step) + 45M cosine-profile plasma electrons, random windowed DoFs."""
+    wl = I.workload_jittered64()
+    same, er, ev, res, g, ost = _sampled_parity(wl, prec, 20000, 321)
+    print(f"\n[jittered64 prec={prec}] tet agree {same:.6f} r err {er.max():.2e} v err {ev.max():.2e} "
+          f"conservation {res:.2e} crossings/particle {ost.n_cross.mean():.3f}")
+    assert ost.n_cross.mean() > 0.1
+    if prec == FP64:
+        assert same == 1.0 and er.max() <= 1e-12 and ev.max() <= 1e-12
+        assert np.array_equal(g["n_cross"], ost.n_cross)
+    else:
+        assert same >= 0.999 and np.median(er) <= 1e-7 and np.median(ev) <= 1e-5
+    assert res <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_large96_two_species_slice_sampled(prec):
+    """96^3 x 6 cube (5.3M tets) with the two-species load (electrons and
+    1836 m_e ions at 2 eV) and random windowed DoFs, on a 4M-particle slice."""
+    base = I.workload_large96(n_particles=2)
+    sb, q, m, w, temp = I.large96_species(4_000_000)
+    cols = []
+    for s in range(2):
+        n = int(sb[s + 1] - sb[s])
+        cols.append(I.maxwellian_chunk(I.SEED_BASE + 5 + 1000 * s, 0, n, temp, m[s]))
+    arr = [np.concatenate([c[k] for c in cols]) for k in range(6)]
+    parts = I.Particles(*arr, sb, q, m, w)
+    wl = I.Workload("large96_slice", base.mesh, parts, base.e_tilde, base.b_tilde, base.omega0, base.dt, 1, 0.0)
+    same, er, ev, res, g, ost = _sampled_parity(wl, prec, 20000, 654)
+    print(f"\n[large96 slice prec={prec}] tet agree {same:.6f} r err {er.max():.2e} v err {ev.max():.2e} "
+          f"conservation {res:.2e}")
+    if prec == FP64:
+        assert same == 1.0 and er.max() <= 1e-12 and ev.max() <= 1e-12
+    else:
+        assert same >= 0.999 and np.median(er) <= 1e-7 and np.median(ev) <= 1e-5
+    assert res <= 1e-13
