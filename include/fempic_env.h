@@ -257,6 +257,7 @@ int fempic_sort_noalloc(fempic_env* env, const fempic_particles* in, const fempi
 #define FEMPIC_K_FINALIZE 3   /* deposit finalize */
 #define FEMPIC_K_CHARGE 4     /* nodal charge */
 #define FEMPIC_K_SORT 5       /* particle sort by tet */
+#define FEMPIC_K_CROSS 6      /* mixed form crossing pass; its bracket lies inside FEMPIC_K_PUSH's */
 #define FEMPIC_K_COUNT 8
 
 /* Measurement support (no counterpart in the paper): while enabled, every
@@ -265,10 +266,13 @@ int fempic_sort_noalloc(fempic_env* env, const fempic_particles* in, const fempi
  * 0 stops.  At most 65536 launches are recorded per enable.  Errors: EINVAL. */
 int fempic_profile_enable(fempic_env* env, int32_t enable);
 
-/* Per kernel id: summed event durations (ms_out[FEMPIC_K_COUNT]) and launch
- * counts (launches_out[FEMPIC_K_COUNT]) since the last enable; synchronizes
- * on the recorded events.  Errors: EINVAL, ECUDA. */
-int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* launches_out);
+/* Per kernel id, since the last enable: summed bracket durations in ms
+ * (ms_out[FEMPIC_K_COUNT]), the number of brackets, one per library call
+ * (calls_out[FEMPIC_K_COUNT]), and the number of kernels launched inside
+ * them (kernels_out[FEMPIC_K_COUNT]; a nested bracket's kernels count under
+ * its own id only, so the sum over ids is the number of kernel launches).
+ * Synchronizes on the recorded events.  Errors: EINVAL, ECUDA. */
+int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* calls_out, int64_t* kernels_out);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* fempic_last_error(void);

@@ -28,7 +28,7 @@ FEMPIC_WALL_ABSORB = 1
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step",
            "fempic_deposit", "fempic_reset_deposit", "fempic_nodal_charge", "fempic_stats",
            "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
-FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT = range(6)
+FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS = range(7)
 FEMPIC_K_COUNT = 8
 FEMPIC_SORT_NOALLOC_MAX_KEYS = 1 << 21
 
@@ -95,7 +95,7 @@ def load(path: str = LIB_PATH):
         lib.fempic_sort.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
         lib.fempic_sort_noalloc.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
         lib.fempic_profile_enable.argtypes = [C.c_void_p, C.c_int32]
-        lib.fempic_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_last_error.restype = C.c_char_p
         lib.fempic_last_error.argtypes = []
         lib.fempic_env_destroy.argtypes = [C.c_void_p]
@@ -177,8 +177,8 @@ def fempic_profile_enable(env, enable: bool):
     check(load().fempic_profile_enable(env, 1 if enable else 0), "fempic_profile_enable")
 
 
-def fempic_profile_read(env, ms_out, launches_out):
-    check(load().fempic_profile_read(env, ms_out, launches_out), "fempic_profile_read")
+def fempic_profile_read(env, ms_out, calls_out, kernels_out):
+    check(load().fempic_profile_read(env, ms_out, calls_out, kernels_out), "fempic_profile_read")
 
 
 def fempic_last_error() -> str:

@@ -478,6 +478,21 @@ struct FF {
   float hi, lo;
 };
 
+// Exact widening of a float to double with integer operations (rebias the
+// exponent, shift the significand): GB300 runs the hardware conversion at
+// the FP64 rate, 1/64 of the FP32 rate.  Zero keeps its sign; subnormal,
+// infinite and NaN inputs take the hardware conversion, so the result is the
+// double the conversion gives for every float.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu, sign = u & 0x80000000u;
+  if (e - 1u >= 0xfeu) {
+    if ((u << 1) == 0u) return __hiloint2double((int)sign, 0);
+    return (double)f;
+  }
+  return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
 // r = hi + lo: hi keeps the leading 24 bits of the FP64 significand
 // (truncated, so exactly a float), lo the remaining 29 bits rounded to FP32.
 // |r| outside [2^-126, 2^128) maps to 0 (positions are never that small or
@@ -558,11 +573,52 @@ __device__ __forceinline__ void depositq_atomic(const PushArgs& A, int32_t T, in
     if (g[e]) atomicAdd(base + e, (unsigned long long)g[e]);
 }
 
+// Exit face of the straight piece with end barycentrics Qa -> Qb in one tet,
+// the entry face excluded: among faces with Qb_k < 0, the one whose crossing
+// parameter s_k = Qa_k / (Qa_k - Qb_k) (clamped at 0) is smallest, the lowest
+// k on ties; -1 when the piece stays inside.
+__device__ __forceinline__ int exit_face(const int32_t Qa[4], const int32_t Qb[4], int entry, float& smin) {
+  int kx = -1;
+  smin = INFINITY;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (k == entry || Qb[k] >= 0) continue;
+    const int32_t den = Qa[k] - Qb[k];
+    float sk = den > 0 ? (float)Qa[k] / (float)den : 0.0f;
+    if (sk < 0.0f) sk = 0.0f;
+    if (sk < smin) {
+      smin = sk;
+      kx = k;
+    }
+  }
+  return kx;
+}
+
+// Barycentric integers of the crossing point Qa + s (Qb - Qa) on exit face
+// kx: exactly zero on that face, the sum kept at 2^24 on the last other node.
+__device__ __forceinline__ void crossing_q(const int32_t Qa[4], const int32_t Qb[4], int kx, float smin,
+                                           int32_t Qp[4]) {
+  const int last = kx == 3 ? 2 : 3;
+  int32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    if (j == kx) {
+      Qp[j] = 0;
+    } else {
+      Qp[j] = Qa[j] + __float2int_rn(smin * (float)(Qb[j] - Qa[j]));
+      acc += Qp[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; j++)
+    if (j == last) Qp[j] += kQOne - acc;
+}
+
 // Position after the push: the one FP64 operation of the common path.  Both
 // mixed kernels form it with this exact sequence, so the crossing kernel can
 // rebuild b from the stored start point and velocity bit for bit.
 __device__ __forceinline__ double advance(double a, float dt32, float v) {
-  return __dadd_rn(a, (double)__fmul_rn(dt32, v));
+  return __dadd_rn(a, f32_to_f64(__fmul_rn(dt32, v)));
 }
 
 // Per-lane result of the common path, consumed by the warp epilogue.
@@ -645,10 +701,19 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   float bx, by, bz;
   dpos32(G, bs, bx, by, bz);
   bary_q(G, bx, by, bz, Qb);
+  // Every lane stores its full new state, a leaving particle included (its b
+  // is final unless it reflects or freezes), so the warp's stores cover whole
+  // sectors and the crossing kernel rarely rewrites positions.
   static_cast<float*>(A.vx)[p] = vn0;
   static_cast<float*>(A.vy)[p] = vn1;
   static_cast<float*>(A.vz)[p] = vn2;
+  A.x[p] = b0;
+  A.y[p] = b1;
+  A.z[p] = b2;
   if ((Qb[0] | Qb[1] | Qb[2] | Qb[3]) < 0) {
+    // leaves its tet: the crossing pass deposits all its pieces (doing the
+    // home piece here instead measured slower: the divergent exit search
+    // costs the common path more than the crossing pass saves)
     o.queue = true;
     o.a[0] = ax;
     o.a[1] = ay;
@@ -663,9 +728,6 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   o.key = T * kMaxSpecies + s;
   o.Thome = T;
   o.shome = s;
-  A.x[p] = b0;
-  A.y[p] = b1;
-  A.z[p] = b2;
 }
 
 // Warp epilogue (all 32 lanes): append the lanes that leave their tet to the
@@ -864,6 +926,7 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_
       // flight (stages of tiles it .. it+kStages-1 not yet consumed), stop
       if (tid == 0) {
         atomicAdd(A.stats + 2, 1ull);
+        for (int64_t t = tile; t < ntiles; t += stride) A.xcount[t] = 0;   // no stale records
         for (int k = 0; k < kStages; k++) {
           const int sk = (st + k) % kStages;
           if (tile + k * stride < ntiles) mbar_wait_bounded(&bar[sk], (phase >> sk) & 1u);
@@ -928,40 +991,15 @@ __device__ __forceinline__ void cross_particle(const PushArgs& A, int64_t p, int
     bool moved = true;         // false once frozen at a crossing point
     bool reflected = false;
     for (;;) {
-      int kx = -1;
-      float smin = INFINITY;
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        if (k == entry || Qb[k] >= 0) continue;
-        const int32_t den = Qa[k] - Qb[k];
-        float sk = den > 0 ? (float)Qa[k] / (float)den : 0.0f;
-        if (sk < 0.0f) sk = 0.0f;
-        if (sk < smin) {
-          smin = sk;
-          kx = k;
-        }
-      }
+      float smin;
+      const int kx = exit_face(Qa, Qb, entry, smin);
       long long g[6];
       if (kx < 0) {
         gq(Qa, Qb, g);
         depositq_atomic(A, T, s, g);
         break;
       }
-      // crossing point barycentrics: exact zero on the exit face, sum kept at 2^24
-      const int last = kx == 3 ? 2 : 3;
-      int32_t acc = 0;
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        if (j == kx) {
-          Qp[j] = 0;
-        } else {
-          Qp[j] = Qa[j] + __float2int_rn(smin * (float)(Qb[j] - Qa[j]));
-          acc += Qp[j];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j++)
-        if (j == last) Qp[j] += kQOne - acc;
+      crossing_q(Qa, Qb, kx, smin, Qp);
       gq(Qa, Qp, g);
       depositq_atomic(A, T, s, g);
       nc++;
@@ -1022,9 +1060,11 @@ __device__ __forceinline__ void cross_particle(const PushArgs& A, int64_t p, int
       bary_q(Gc, ex, ey, ez, Qb);
     }
     if (moved) {
-      A.x[p] = b[0];
-      A.y[p] = b[1];
-      A.z[p] = b[2];
+      if (reflected) {   // otherwise b is what the common path already stored
+        A.x[p] = b[0];
+        A.y[p] = b[1];
+        A.z[p] = b[2];
+      }
     } else {   // frozen at the last crossing point
       const double sd = (double)sacc;
       A.x[p] = fma(sd, b[0] - a0[0], a0[0]);
@@ -1048,7 +1088,12 @@ __device__ __forceinline__ void cross_particle(const PushArgs& A, int64_t p, int
 }
 
 // Crossing pass of the mixed form: one warp per 256-particle tile region of
-// the queue, lanes taking its records in turn.
+// the record queue, lanes taking its records in turn.  Records of one tile
+// come from neighbouring tets, so a warp's tet records and deposit slots
+// stay in cache.  (Spreading the records of several tiles over a whole CTA,
+// one per thread, measured slower.)
+constexpr int kCrossWarpsPerSm = 64;
+
 __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t ntiles) {
   const int lane = threadIdx.x & 31;
   unsigned ncr = 0, nfrz = 0;
@@ -1634,6 +1679,7 @@ struct fempic_env {
   // per-kernel event timing (measurement support)
   struct Rec {
     int kid;
+    int kernels;   // kernels launched inside the bracket
     cudaEvent_t a, b;
   };
   int32_t* sort_counts = nullptr;   // [sort_cap] per-key counters, then cursors
@@ -1654,6 +1700,7 @@ struct LaunchTimer {
   fempic_env* e;
   cudaStream_t st;
   int kid;
+  int kernels = 0;   // kernels launched inside this bracket (not counting nested brackets)
   cudaEvent_t a = nullptr, b = nullptr;
   cudaEvent_t take() {
     if (e->pool_used == e->pool.size()) {
@@ -1672,7 +1719,7 @@ struct LaunchTimer {
   ~LaunchTimer() {
     if (a && b) {
       cudaEventRecord(b, st);
-      e->recs.push_back({kid, a, b});
+      e->recs.push_back({kid, kernels, a, b});
     }
   }
 };
@@ -1857,6 +1904,7 @@ extern "C" int fempic_locate(fempic_env* env, const fempic_particles* p, void* s
   {
     LaunchTimer lt(env, (cudaStream_t)stream, FEMPIC_K_LOCATE);
     k_locate<<<blocks_for(p->n), kThreads, 0, (cudaStream_t)stream>>>(A);
+    lt.kernels = 1;
   }
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
@@ -1928,6 +1976,7 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
   const int64_t nt = env->h.nt;
   {
   LaunchTimer lt(env, st, FEMPIC_K_FIELD);
+  lt.kernels = 1;
   if (mixed) {
     k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf,
                                                       static_cast<const float2*>(envl->e_tilde),
@@ -1996,15 +2045,22 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
         }
         const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)env->num_sms * env->tma_blocks_per_sm);
         k_push_mixed_tma<<<grid, kThreads, 0, st>>>(A, ntiles);
+        lt.kernels++;
       }
       const int64_t rest = p->n - ntiles * kTile;
-      if (rest > 0) k_push_mixed<<<blocks_for(rest), kThreads, 0, st>>>(A, ntiles * kTile);
+      if (rest > 0) {
+        k_push_mixed<<<blocks_for(rest), kThreads, 0, st>>>(A, ntiles * kTile);
+        lt.kernels++;
+      }
       const int64_t all_tiles = (p->n + kTile - 1) / kTile;
-      const unsigned cross_blocks =
-          (unsigned)std::min<int64_t>((all_tiles + 7) / 8, (int64_t)env->num_sms * 8);
+      const unsigned cross_blocks = (unsigned)std::min<int64_t>(
+          (all_tiles + 7) / 8, (int64_t)env->num_sms * kCrossWarpsPerSm / (kThreads / 32));
+      LaunchTimer lc(env, st, FEMPIC_K_CROSS);   // nested: also inside the push bracket
       k_cross_mixed<<<cross_blocks, kThreads, 0, st>>>(A, all_tiles);
+      lc.kernels = 1;
     } else {
       k_push_fp64<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+      lt.kernels = 1;
     }
   }
   FEMPIC_CUDA(cudaGetLastError());
@@ -2035,10 +2091,14 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
     if (mixed && env->dGq) {
       const int64_t nslots = (int64_t)A.ns * env->h.nt;
       if (nslots > 0)
+      {
         k_slot_flush<<<blocks_for(nslots), kThreads, 0, (cudaStream_t)stream>>>(nslots, env->h.nt, env->h.ne, env->dGq,
                                                                                 env->te, env->dGe);
+        lt.kernels++;
+      }
     }
     k_deposit_finalize<<<blocks_for(A.ne), kThreads, 0, (cudaStream_t)stream>>>(A);
+    lt.kernels++;
   }
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
@@ -2081,6 +2141,7 @@ extern "C" int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, d
   {
     LaunchTimer lt(env, st, FEMPIC_K_CHARGE);
     k_nodal_charge<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+    lt.kernels = 1;
   }
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
@@ -2109,11 +2170,12 @@ extern "C" int fempic_profile_enable(fempic_env* env, int32_t enable) {
   return FEMPIC_OK;
 }
 
-extern "C" int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* launches_out) {
-  if (!env || !ms_out || !launches_out) return fail(FEMPIC_EINVAL, "profile_read: NULL argument");
+extern "C" int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* calls_out, int64_t* kernels_out) {
+  if (!env || !ms_out || !calls_out || !kernels_out) return fail(FEMPIC_EINVAL, "profile_read: NULL argument");
   for (int k = 0; k < FEMPIC_K_COUNT; k++) {
     ms_out[k] = 0.0;
-    launches_out[k] = 0;
+    calls_out[k] = 0;
+    kernels_out[k] = 0;
   }
   for (const auto& r : env->recs) {
     FEMPIC_CUDA(cudaEventSynchronize(r.b));
@@ -2121,7 +2183,8 @@ extern "C" int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* lau
     FEMPIC_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
     if (r.kid >= 0 && r.kid < FEMPIC_K_COUNT) {
       ms_out[r.kid] += ms;
-      launches_out[r.kid]++;
+      calls_out[r.kid]++;
+      kernels_out[r.kid] += r.kernels;
     }
   }
   return FEMPIC_OK;
@@ -2163,6 +2226,7 @@ extern "C" int fempic_sort(fempic_env* env, const fempic_particles* in, const fe
   }
   const int64_t tiles = (k + 2 * kScan - 1) / (2 * kScan);
   LaunchTimer lt(env, st, FEMPIC_K_SORT);
+  lt.kernels = 5;   // histogram, three scan passes, scatter
   FEMPIC_CUDA(cudaMemsetAsync(env->sort_counts, 0, k * sizeof(int32_t), st));
   k_sort_hist<<<blocks_for(in->n), kThreads, 0, st>>>(in->n, in->tet, A.sp, nt, env->sort_counts);
   k_scan_tiles<<<(unsigned)tiles, kScan, 0, st>>>(k, env->sort_counts, env->sort_offsets, env->sort_sums);

@@ -187,9 +187,12 @@ class FempicEnv:
         capi.fempic_profile_enable(self.h, enable)
 
     def profile_read(self) -> dict:
-        """Summed event time (ms) and launch count per kernel since profile(True)."""
+        """Per kernel id since profile(True): summed event time (ms), number of
+        library calls timed (`launches`) and kernels launched (`kernels`).
+        The crossing pass ("cross") is timed inside the push bracket too."""
         ms = np.zeros(capi.FEMPIC_K_COUNT, np.float64)
-        cnt = np.zeros(capi.FEMPIC_K_COUNT, np.int64)
-        capi.fempic_profile_read(self.h, ms.ctypes.data, cnt.ctypes.data)
-        names = ("locate", "field", "push", "finalize", "charge", "sort")
-        return {nm: dict(ms=float(ms[i]), launches=int(cnt[i])) for i, nm in enumerate(names)}
+        calls = np.zeros(capi.FEMPIC_K_COUNT, np.int64)
+        kern = np.zeros(capi.FEMPIC_K_COUNT, np.int64)
+        capi.fempic_profile_read(self.h, ms.ctypes.data, calls.ctypes.data, kern.ctypes.data)
+        names = ("locate", "field", "push", "finalize", "charge", "sort", "cross")
+        return {nm: dict(ms=float(ms[i]), launches=int(calls[i]), kernels=int(kern[i])) for i, nm in enumerate(names)}
