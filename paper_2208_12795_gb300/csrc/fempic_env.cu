@@ -288,14 +288,29 @@ __global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, float4* __re
 }
 
 // ------------------------------------------------------------ FP64 push
-__device__ __forceinline__ void bary64(const double* __restrict__ g, const double r[3], double lam[4]) {
-  const double dx = r[0] - g[0], dy = r[1] - g[1], dz = r[2] - g[2];
+__device__ __forceinline__ void bary64_d(const double* __restrict__ g, double dx, double dy, double dz,
+                                         double lam[4]) {
 #pragma unroll
   for (int k = 1; k < 4; k++) {
     const double* gk = g + 3 * k;
     lam[k] = fma(gk[2], dz, fma(gk[1], dy, gk[0] * dx));
   }
   lam[0] = __dsub_rn(__dsub_rn(__dsub_rn(1.0, lam[1]), lam[2]), lam[3]);
+}
+
+__device__ __forceinline__ void bary64(const double* __restrict__ g, const double r[3], double lam[4]) {
+  bary64_d(g, r[0] - g[0], r[1] - g[1], r[2] - g[2], lam);
+}
+
+// Sign and finiteness tests of doubles on their bit patterns: integer
+// instructions instead of FP64 compares, which GB300 issues at the FP64 rate.
+__device__ __forceinline__ bool finite_bits(double r) {
+  return (((unsigned)__double2hiint(r) >> 20) & 0x7ffu) != 0x7ffu;
+}
+
+__device__ __forceinline__ bool negative_bits(double r) {   // r < 0 for finite r (-0 is not negative)
+  const int hi = __double2hiint(r);
+  return hi < 0 && (((unsigned)hi & 0x7fffffffu) | (unsigned)__double2loint(r)) != 0u;
 }
 
 __device__ __forceinline__ void deposit64(const PushArgs& A, int32_t T, const double la[4], const double lb[4],
@@ -352,15 +367,15 @@ __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
       double vn[3] = {vmx + (vpy * sz - vpz * sy) + kq * Ex, vmy + (vpz * sx - vpx * sz) + kq * Ey,
                       vmz + (vpx * sy - vpy * sx) + kq * Ez};
       double b[3] = {a[0] + A.dt * vn[0], a[1] + A.dt * vn[1], a[2] + A.dt * vn[2]};
-      if (!(isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]) && isfinite(b[0]) && isfinite(b[1]) &&
-            isfinite(b[2]))) {
+      if (!(finite_bits(vn[0]) && finite_bits(vn[1]) && finite_bits(vn[2]) && finite_bits(b[0]) &&
+            finite_bits(b[1]) && finite_bits(b[2]))) {
         A.status[p] = FEMPIC_P_NONFINITE;
         A.tet[p] = -2 - T;
         nfrz = 1;
       } else {
         // (e) track + (f) deposit
         double la[4], lb[4], lp[4];
-        bary64(G, a, la);
+        bary64_d(G, dx, dy, dz, la);
         int entry = -1;
         int32_t nc = 0;
         uint8_t st = FEMPIC_P_OK;
@@ -370,7 +385,7 @@ __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
           double smin = INFINITY;
 #pragma unroll
           for (int k = 0; k < 4; k++) {
-            if (k == entry || !(lb[k] < 0.0)) continue;
+            if (k == entry || !negative_bits(lb[k])) continue;
             double sk = la[k] / (la[k] - lb[k]);
             if (sk < 0.0) sk = 0.0;
             if (sk < smin) {
@@ -508,9 +523,6 @@ __device__ __forceinline__ FF split_f64(double r) {
   return FF{fhi, sign ? -flo : flo};
 }
 
-__device__ __forceinline__ bool finite_f64(double r) {
-  return (((unsigned)__double2hiint(r) >> 20) & 0x7ffu) != 0x7ffu;
-}
 
 struct Geo32 {
   float4 a, b, c, d;
@@ -689,7 +701,7 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   const float vn2 = vmz + (vpx * sy - vpy * sx) + kq * Ez;
   const float dt32 = (float)A.dt;
   const double b0 = advance(ax, dt32, vn0), b1 = advance(ay, dt32, vn1), b2 = advance(az, dt32, vn2);
-  if (!(isfinite(vn0) && isfinite(vn1) && isfinite(vn2) && finite_f64(b0) && finite_f64(b1) && finite_f64(b2))) {
+  if (!(isfinite(vn0) && isfinite(vn1) && isfinite(vn2) && finite_bits(b0) && finite_bits(b1) && finite_bits(b2))) {
     A.status[p] = FEMPIC_P_NONFINITE;
     A.tet[p] = -2 - T;
     o.nfrz = 1;
@@ -958,154 +970,193 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_
   }
 }
 
-// Crossing path of one particle that leaves its home tet (from its record in
-// the crossing queue): rebuild b, split the segment at every face it
-// crosses, deposit each in-tet piece, reflect or absorb at walls, write the
-// final state.
-__device__ __forceinline__ void cross_particle(const PushArgs& A, int64_t p, int32_t T, double ax, double ay, double az,
-                                            float v0, float v1, float v2, unsigned& ncr, unsigned& nfrz) {
-  {
-    const int s = species_of(A.sp, p);
-    float* vxp = static_cast<float*>(A.vx);
-    float* vyp = static_cast<float*>(A.vy);
-    float* vzp = static_cast<float*>(A.vz);
-    double a0[3] = {ax, ay, az};   // start of the current straight piece
-    float vn[3] = {v0, v1, v2};
-    const float dt32 = (float)A.dt;
-    double b[3] = {advance(a0[0], dt32, vn[0]), advance(a0[1], dt32, vn[1]), advance(a0[2], dt32, vn[2])};
-    int32_t Qa[4], Qb[4], Qp[4];
-    FF bs[3] = {split_f64(b[0]), split_f64(b[1]), split_f64(b[2])};
-    {
-      const Geo32 G = ld_geo(A.tetrec, T);
-      const FF rs[3] = {split_f64(a0[0]), split_f64(a0[1]), split_f64(a0[2])};
-      float dx, dy, dz;
-      dpos32(G, rs, dx, dy, dz);
-      bary_q(G, dx, dy, dz, Qa);
-      dpos32(G, bs, dx, dy, dz);
-      bary_q(G, dx, dy, dz, Qb);
-    }
-    int entry = -1;
-    int32_t nc = 0;
-    uint8_t st = FEMPIC_P_OK;
-    float sacc = 0.f;          // current piece start = a0 + sacc (b - a0)
-    bool moved = true;         // false once frozen at a crossing point
-    bool reflected = false;
-    for (;;) {
-      float smin;
-      const int kx = exit_face(Qa, Qb, entry, smin);
-      long long g[6];
-      if (kx < 0) {
-        gq(Qa, Qb, g);
-        depositq_atomic(A, T, s, g);
-        break;
-      }
-      crossing_q(Qa, Qb, kx, smin, Qp);
-      gq(Qa, Qp, g);
-      depositq_atomic(A, T, s, g);
-      nc++;
-      sacc = __fmaf_rn(smin, 1.0f - sacc, sacc);
-      if (nc > A.max_cross) {
-        st = FEMPIC_P_CAP;
-        moved = false;
-        break;
-      }
-      const int4 nbv = __ldg(&A.nb[T]);
-      const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
-      if (nbt >= 0) {
-        const int4 o4 = __ldg(&A.tn[T]), n4 = __ldg(&A.tn[nbt]);
-        const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nnd[4] = {n4.x, n4.y, n4.z, n4.w};
-        int ent = 0;
+// Crossing path of a particle that leaves its home tet, one face at a time.
+// State of the walk: the current straight piece runs from a0 + sacc (b - a0)
+// to b inside tet T, with end barycentrics Qa -> Qb; `entry` is the face it
+// came in through.
+struct CrossState {
+  double a0[3], b[3];
+  FF bs[3];
+  float vn[3];
+  int32_t Qa[4], Qb[4];
+  int32_t T, p;
+  int entry, nc, s;
+  float sacc;
+  uint8_t st;
+  bool moved, reflected;
+};
+
+// Start from the record: rebuild b bit for bit (the common path's sequence)
+// and the integer barycentrics of both ends in the home tet.
+__device__ __forceinline__ void cross_begin(const PushArgs& A, const CrossRec& r, CrossState& c) {
+  c.p = r.p;
+  c.T = r.T;
+  c.s = species_of(A.sp, r.p);
+  const float dt32 = (float)A.dt;
 #pragma unroll
-        for (int i2 = 0; i2 < 4; i2++) {
-          int32_t val = 0;
-          bool hit = false;
-#pragma unroll
-          for (int j = 0; j < 4; j++)
-            if (on[j] == nnd[i2]) {
-              val = Qp[j];
-              hit = true;
-            }
-          Qa[i2] = val;
-          if (!hit) ent = i2;
-        }
-        T = nbt;
-        entry = ent;
-      } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
-        // materialize the wall point in FP64, mirror the rest of the step
-        const double sd = (double)sacc;
-#pragma unroll
-        for (int c = 0; c < 3; c++) a0[c] = fma(sd, b[c] - a0[c], a0[c]);
-        sacc = 0.f;
-        const int code = -1 - nbt, ax = code >> 1, side = code & 1;
-#pragma unroll
-        for (int c = 0; c < 3; c++)
-          if (c == ax) {
-            const double L = side ? A.hi[c] : A.lo[c];
-            b[c] = 2.0 * L - b[c];
-            vn[c] = -vn[c];
-            bs[c] = split_f64(b[c]);
-          }
-        reflected = true;
-#pragma unroll
-        for (int j = 0; j < 4; j++) Qa[j] = Qp[j];
-        entry = kx;
-      } else {
-        st = FEMPIC_P_ABSORBED;
-        moved = false;
-        break;
-      }
-      const Geo32 Gc = ld_geo(A.tetrec, T);
-      float ex, ey, ez;
-      dpos32(Gc, bs, ex, ey, ez);
-      bary_q(Gc, ex, ey, ez, Qb);
-    }
-    if (moved) {
-      if (reflected) {   // otherwise b is what the common path already stored
-        A.x[p] = b[0];
-        A.y[p] = b[1];
-        A.z[p] = b[2];
-      }
-    } else {   // frozen at the last crossing point
-      const double sd = (double)sacc;
-      A.x[p] = fma(sd, b[0] - a0[0], a0[0]);
-      A.y[p] = fma(sd, b[1] - a0[1], a0[1]);
-      A.z[p] = fma(sd, b[2] - a0[2], a0[2]);
-    }
-    if (reflected) {
-      vxp[p] = vn[0];
-      vyp[p] = vn[1];
-      vzp[p] = vn[2];
-    }
-    if (st != FEMPIC_P_OK) {
-      A.status[p] = st;
-      T = -2 - T;
-      nfrz++;
-    }
-    A.tet[p] = T;
-    if (A.ncross) A.ncross[p] += nc;
-    ncr += (unsigned)nc;
+  for (int k = 0; k < 3; k++) {
+    c.a0[k] = r.a[k];
+    c.vn[k] = r.v[k];
+    c.b[k] = advance(r.a[k], dt32, r.v[k]);
+    c.bs[k] = split_f64(c.b[k]);
   }
+  const Geo32 G = ld_geo(A.tetrec, c.T);
+  const FF rs[3] = {split_f64(c.a0[0]), split_f64(c.a0[1]), split_f64(c.a0[2])};
+  float dx, dy, dz;
+  dpos32(G, rs, dx, dy, dz);
+  bary_q(G, dx, dy, dz, c.Qa);
+  dpos32(G, c.bs, dx, dy, dz);
+  bary_q(G, dx, dy, dz, c.Qb);
+  c.entry = -1;
+  c.nc = 0;
+  c.sacc = 0.f;
+  c.st = FEMPIC_P_OK;
+  c.moved = true;
+  c.reflected = false;
+}
+
+// Deposit the current piece up to its exit face (or to b) and move on: into
+// the neighbour, back from a reflecting wall, or stop (absorbed, capped).
+// Returns true when the particle's step is complete.
+__device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c) {
+  float smin;
+  const int kx = exit_face(c.Qa, c.Qb, c.entry, smin);
+  long long g[6];
+  if (kx < 0) {
+    gq(c.Qa, c.Qb, g);
+    depositq_atomic(A, c.T, c.s, g);
+    return true;
+  }
+  int32_t Qp[4];
+  crossing_q(c.Qa, c.Qb, kx, smin, Qp);
+  gq(c.Qa, Qp, g);
+  depositq_atomic(A, c.T, c.s, g);
+  c.nc++;
+  c.sacc = __fmaf_rn(smin, 1.0f - c.sacc, c.sacc);
+  if (c.nc > A.max_cross) {
+    c.st = FEMPIC_P_CAP;
+    c.moved = false;
+    return true;
+  }
+  const int4 nbv = __ldg(&A.nb[c.T]);
+  const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+  if (nbt >= 0) {
+    const int4 o4 = __ldg(&A.tn[c.T]), n4 = __ldg(&A.tn[nbt]);
+    const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nnd[4] = {n4.x, n4.y, n4.z, n4.w};
+    int ent = 0;
+#pragma unroll
+    for (int i2 = 0; i2 < 4; i2++) {
+      int32_t val = 0;
+      bool hit = false;
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (on[j] == nnd[i2]) {
+          val = Qp[j];
+          hit = true;
+        }
+      c.Qa[i2] = val;
+      if (!hit) ent = i2;
+    }
+    c.T = nbt;
+    c.entry = ent;
+  } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
+    // materialize the wall point in FP64, mirror the rest of the step
+    const double sd = (double)c.sacc;
+#pragma unroll
+    for (int k = 0; k < 3; k++) c.a0[k] = fma(sd, c.b[k] - c.a0[k], c.a0[k]);
+    c.sacc = 0.f;
+    const int code = -1 - nbt, ax = code >> 1, side = code & 1;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      if (k == ax) {
+        const double L = side ? A.hi[k] : A.lo[k];
+        c.b[k] = 2.0 * L - c.b[k];
+        c.vn[k] = -c.vn[k];
+        c.bs[k] = split_f64(c.b[k]);
+      }
+    c.reflected = true;
+#pragma unroll
+    for (int j = 0; j < 4; j++) c.Qa[j] = Qp[j];
+    c.entry = kx;
+  } else {
+    c.st = FEMPIC_P_ABSORBED;
+    c.moved = false;
+    return true;
+  }
+  const Geo32 Gc = ld_geo(A.tetrec, c.T);
+  float ex, ey, ez;
+  dpos32(Gc, c.bs, ex, ey, ez);
+  bary_q(Gc, ex, ey, ez, c.Qb);
+  return false;
+}
+
+// Final state of a finished walk.
+__device__ __forceinline__ void cross_finish(const PushArgs& A, const CrossState& c, unsigned& ncr, unsigned& nfrz) {
+  const int64_t p = c.p;
+  if (c.moved) {
+    if (c.reflected) {   // otherwise b is what the common path already stored
+      A.x[p] = c.b[0];
+      A.y[p] = c.b[1];
+      A.z[p] = c.b[2];
+    }
+  } else {   // frozen at the last crossing point
+    const double sd = (double)c.sacc;
+    A.x[p] = fma(sd, c.b[0] - c.a0[0], c.a0[0]);
+    A.y[p] = fma(sd, c.b[1] - c.a0[1], c.a0[1]);
+    A.z[p] = fma(sd, c.b[2] - c.a0[2], c.a0[2]);
+  }
+  if (c.reflected) {
+    static_cast<float*>(A.vx)[p] = c.vn[0];
+    static_cast<float*>(A.vy)[p] = c.vn[1];
+    static_cast<float*>(A.vz)[p] = c.vn[2];
+  }
+  int32_t T = c.T;
+  if (c.st != FEMPIC_P_OK) {
+    A.status[p] = c.st;
+    T = -2 - T;
+    nfrz++;
+  }
+  A.tet[p] = T;
+  if (A.ncross) A.ncross[p] += c.nc;
+  ncr += (unsigned)c.nc;
 }
 
 // Crossing pass of the mixed form: one warp per 256-particle tile region of
-// the record queue, lanes taking its records in turn.  Records of one tile
-// come from neighbouring tets, so a warp's tet records and deposit slots
-// stay in cache.  (Spreading the records of several tiles over a whole CTA,
-// one per thread, measured slower.)
+// the record queue.  Each loop iteration advances every busy lane by one
+// face; a lane whose particle is done takes the tile's next record, so a
+// particle that crosses many faces (a fast beam particle) does not hold 31
+// idle lanes.  Records of one tile come from neighbouring tets, so the
+// warp's tet records and deposit slots stay in cache.
 constexpr int kCrossWarpsPerSm = 64;
 
 __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t ntiles) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   unsigned ncr = 0, nfrz = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
     const int32_t cnt = A.xcount[t];
-    for (int32_t i = lane; i < cnt; i += 32) {
-      const CrossRec r = A.xrec[t * kThreads + i];
-      cross_particle(A, r.p, r.T, r.a[0], r.a[1], r.a[2], r.v[0], r.v[1], r.v[2], ncr, nfrz);
+    int32_t next = 0;
+    bool have = false;
+    CrossState c;
+    for (;;) {
+      const unsigned idle = __ballot_sync(full, !have);
+      if (next < cnt && idle) {
+        const int32_t idx = next + __popc(idle & lt);
+        if (!have && idx < cnt) {
+          cross_begin(A, A.xrec[t * kThreads + idx], c);
+          have = true;
+        }
+        next += __popc(idle);
+      }
+      if (!__any_sync(full, have)) break;
+      if (have && cross_advance(A, c)) {
+        cross_finish(A, c, ncr, nfrz);
+        have = false;
+      }
     }
   }
-  const unsigned full = 0xffffffffu;
   ncr = __reduce_add_sync(full, ncr);
   nfrz = __reduce_add_sync(full, nfrz);
   if (lane == 0) {
