@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--cpu-particles", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient-window measurement")
+    ap.add_argument("--no-levels3", action="store_true", help="skip the three-level envelope measurement")
     ap.add_argument("--workload", choices=("cube48", "jittered64", "large96"), default="cube48",
                     help="cube48: 48^3x6 cube, 10M e- (headline); jittered64: 64^3x6 jittered cube, 50M "
                          "(10 keV beam + cosine plasma), random DoFs; large96: 96^3x6 cube, 400M e- + ions")
@@ -319,6 +320,55 @@ def run_ours(args):
         e2e_s = float(t.item())
     mixed["e2e_s"] = e2e_s
     mixed["h2d"], mixed["d2h"] = h2d, d2h
+
+    # The same step with the envelope interpolated in time from three DoF
+    # levels (t_{n-1}, t_n, t_{n+1}, a field step of 21 fine steps), device
+    # resident: only the per-tet field construction reads the extra levels.
+    lv3 = None
+    if not args.no_levels3:
+        from paper_2208_12795_gb300 import capi
+        e0 = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+        b0 = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+        e_lv = [e0 * s for s in (0.98, 1.0, 1.02)]
+        b_lv = [b0 * s for s in (0.98, 1.0, 1.02)]
+        k1 = k0 + args.steps
+        mid = (k1 + args.steps // 2) * wl.dt
+        tau = (mid - 21 * wl.dt, mid, mid + 21 * wl.dt)
+
+        def step3(n):
+            t = n * wl.dt
+            env.push_step3(st, e_lv, b_lv, capi.fempic_lagrange3(tau, t), wl.amp(t), wl.omega0, t, wl.dt)
+            env.deposit(wl.omega0, t + wl.dt, dG_out=dG_dev if world > 1 else None)
+            if world > 1:
+                dist.all_reduce(dG_dev)
+            if args.sort_every > 0 and (n + 1) % args.sort_every == 0:
+                env.sort(st, mixed["scratch"])
+
+        for n in range(k1, k1 + 3):
+            step3(n)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        env.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for n in range(k1 + 3, k1 + 3 + args.steps):
+            step3(n)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        env.profile(False)
+        ms3 = ev0.elapsed_time(ev1)
+        if world > 1:
+            tt = torch.tensor([ms3], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms3 = float(tt.item())
+        pr3 = env.profile_read()
+        lv3 = {"value": n_p * world * args.steps / (ms3 / 1e3), "unit": "particle-steps/s",
+               "ms_per_step": ms3 / args.steps, "field_ms_per_step": pr3["field"]["ms"] / args.steps,
+               "field_ms_per_step_one_level": mixed["prof"]["field"]["ms"] / args.steps,
+               "what": "fempic_push_step3: envelope interpolated from 3 DoF levels with second-order "
+                       "Lagrange weights at each fine step (field step = 21 fine steps)"}
+    mixed["levels3"] = lv3
     env.close()
 
     adj = None if (args.no_adjoint or args.workload != "cube48") else adjoint_window(rank)
@@ -453,6 +503,8 @@ def report(args, world, n_p, out, cpu, adj=None):
         rec["fp64_form"] = {"value": total / (f["ms"] / 1e3), "ms_per_step": f["ms"] / K,
                             "push_avg_launch_ms": tf * 1e3, "hbm_frac": bf / tf / 1e9 / peak,
                             "clocks": f["clocks"]}
+    if m.get("levels3") is not None:
+        rec["levels3"] = m["levels3"]
     if adj is not None:
         rec["adjoint"] = adj
     if cpu is not None:

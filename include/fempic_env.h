@@ -117,6 +117,22 @@ typedef struct {
   double amp;                /* host scalar: slow envelope amplitude a(t) at this step */
 } fempic_envelope;
 
+/* Envelope interpolated in time from three DoF levels (Sec. III-D, the
+ * simpler scheme that interpolates the downshifted fields to the fine step;
+ * Sec. III-A, second-order Lagrange representation of the field
+ * coefficients in time over [t_{n-1}, t_{n+1}]).  The envelope at t is
+ * sum_k weight[k] level_k and the field is Re{amp e^{j omega0 t} (that sum)},
+ * the carrier taken at t.  Level k is the envelope at tau_k = t_{n-1+k}, and
+ * weight[k] is the second-order Lagrange basis function of tau_k evaluated
+ * at t (fempic_lagrange3 computes it). */
+typedef struct {
+  const void* e_tilde[3];    /* device complex [Ne] edge DoFs of levels n-1, n, n+1, dtype as in
+                                fempic_envelope */
+  const void* b_tilde[3];    /* device complex [Nf] face DoFs of the same levels */
+  double weight[3];          /* host: N_k(t) of each level */
+  double amp;                /* host scalar: a(t) */
+} fempic_envelope3;
+
 typedef struct {
   int64_t n;                 /* number of particles (same as the particle set) */
   double* rx;                /* device f64 [n] adjoint of the positions */
@@ -159,6 +175,19 @@ int fempic_locate(fempic_env* env, const fempic_particles* p, void* stream);
  * species ranges), ECUDA. */
 int fempic_push_step(fempic_env* env, const fempic_particles* p, const fempic_envelope* envl,
                      double omega0, double t, double dt, void* stream);
+
+/* The step of fempic_push_step with the envelope interpolated from three
+ * levels (fempic_envelope3): only the per-tet field construction reads the
+ * extra levels; the particle work is the same.  Errors: as fempic_push_step,
+ * and EINVAL for a NULL level or a non-finite weight. */
+int fempic_push_step3(fempic_env* env, const fempic_particles* p, const fempic_envelope3* envl,
+                      double omega0, double t, double dt, void* stream);
+
+/* Second-order Lagrange weights (Sec. III-A): w_out[k] = prod_{j != k}
+ * (t - tau[j]) / (tau[k] - tau[j]) for three distinct level times tau[3];
+ * host only, no GPU work.  Errors: EINVAL (NULL, non-finite or repeated
+ * times). */
+int fempic_lagrange3(const double* tau, double t, double* w_out);
 
 /* Finalize the deposit of one step (Sec. III-D, eq. G_integral; forcing term
  * e^{-j omega0 t} G of Sec. III-A): G_cum += dG; then, when non-NULL,

@@ -259,3 +259,39 @@ def run(mesh: OracleMesh, wl, st: OracleState, steps: int, max_crossings=4096, s
         push_step(mesh, st, wl.e_tilde, wl.b_tilde, wl.amp(t), wl.omega0, t, wl.dt, G,
                   max_crossings=max_crossings, wall_mode=wl.wall_mode)
     return st, G
+
+
+# ------------------------------------------------ three-level envelope
+# Sec. III-A represents the field coefficients over [t_{n-1}, t_{n+1}] by
+# second-order Lagrange polynomials in time; Sec. III-D's simpler particle
+# scheme samples that representation at each fine step.  Reading taken: the
+# basis function multiplying level k is the one equal to 1 at that level's
+# own time tau_k = t_{n-1+k}, and the carrier is applied at the fine-step time
+# t (E = Re{a(t) e^{j omega0 t} sum_k N_k(t) e^k}).
+
+def lagrange3_weights(tau, t):
+    """N_k(t) = prod over j != k of (t - tau_j) / (tau_k - tau_j), k = 0, 1, 2."""
+    w = []
+    for k in range(3):
+        num, den = 1.0, 1.0
+        for j in range(3):
+            if j != k:
+                num *= t - tau[j]
+                den *= tau[k] - tau[j]
+        w.append(num / den)
+    return w
+
+
+def envelope3(levels, weights):
+    """The envelope at t: sum_k N_k(t) level_k (complex128 arrays)."""
+    out = np.zeros_like(np.asarray(levels[0], dtype=np.complex128))
+    for lv, wk in zip(levels, weights):
+        out = out + wk * np.asarray(lv, dtype=np.complex128)
+    return out
+
+
+def push_step3(mesh: OracleMesh, st: OracleState, e_levels, b_levels, weights, amp, omega0, t, dt, dG,
+               max_crossings=4096, wall_mode=0):
+    """One oracle step with the envelope interpolated from three levels."""
+    push_step(mesh, st, envelope3(e_levels, weights), envelope3(b_levels, weights), amp, omega0, t, dt, dG,
+              max_crossings=max_crossings, wall_mode=wall_mode)

@@ -25,7 +25,8 @@ FEMPIC_WALL_REFLECT = 0
 FEMPIC_WALL_ABSORB = 1
 
 # Every function declared in include/fempic_env.h.
-EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step",
+EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step", "fempic_push_step3",
+           "fempic_lagrange3",
            "fempic_deposit", "fempic_reset_deposit", "fempic_nodal_charge", "fempic_stats",
            "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
 FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS = range(7)
@@ -59,6 +60,11 @@ class fempic_envelope(C.Structure):
     _fields_ = [("e_tilde", C.c_void_p), ("b_tilde", C.c_void_p), ("amp", C.c_double)]
 
 
+class fempic_envelope3(C.Structure):
+    _fields_ = [("e_tilde", C.c_void_p * 3), ("b_tilde", C.c_void_p * 3), ("weight", C.c_double * 3),
+                ("amp", C.c_double)]
+
+
 class FempicError(RuntimeError):
     pass
 
@@ -80,6 +86,9 @@ def load(path: str = LIB_PATH):
         lib.fempic_env_create.argtypes = [P(fempic_mesh_desc), P(fempic_options), P(C.c_void_p)]
         lib.fempic_env_query.argtypes = [C.c_void_p] + [C.c_void_p] * 7
         lib.fempic_locate.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p]
+        lib.fempic_push_step3.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_envelope3), C.c_double,
+                                          C.c_double, C.c_double, C.c_void_p]
+        lib.fempic_lagrange3.argtypes = [C.c_void_p, C.c_double, C.c_void_p]
         lib.fempic_push_step.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_envelope), C.c_double,
                                          C.c_double, C.c_double, C.c_void_p]
         lib.fempic_deposit.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
@@ -133,6 +142,19 @@ def fempic_locate(env, parts: fempic_particles, stream=0):
 def fempic_push_step(env, parts: fempic_particles, envl: fempic_envelope, omega0, t, dt, stream=0):
     check(load().fempic_push_step(env, C.byref(parts), C.byref(envl), float(omega0), float(t), float(dt),
                                   stream), "fempic_push_step")
+
+
+def fempic_push_step3(env, parts: fempic_particles, envl: fempic_envelope3, omega0, t, dt, stream=0):
+    check(load().fempic_push_step3(env, C.byref(parts), C.byref(envl), float(omega0), float(t), float(dt),
+                                   stream), "fempic_push_step3")
+
+
+def fempic_lagrange3(tau, t) -> tuple:
+    """Second-order Lagrange weights of the three level times tau at t."""
+    tau_c = (C.c_double * 3)(*[float(x) for x in tau])
+    w = (C.c_double * 3)()
+    check(load().fempic_lagrange3(tau_c, float(t), w), "fempic_lagrange3")
+    return tuple(w)
 
 
 def fempic_deposit(env, omega0, t_next, dG_out=0, G_cum_out=0, G_env_out=0, stream=0):

@@ -199,20 +199,41 @@ __device__ __forceinline__ R vdot(V3<R> a, V3<R> b) {
   return a.x * b.x + a.y * b.y + a.z * b.z;
 }
 
-template <typename R, typename C2>
-__device__ __forceinline__ void field_coeffs(const V3<R> g[4], const C2* __restrict__ edof,
-                                             const C2* __restrict__ fdof, const int32_t* eid,
-                                             const int32_t* fid, R cre, R cim, R out[10]) {
+// Envelope DoF levels of one step and the carrier coefficient of each:
+// level k enters as Re{c_k e^k} with c_k = a(t) e^{j omega0 t} N_k(t) (one
+// level: N_0 = 1).
+template <typename C2, typename R>
+struct Levels {
+  const C2* e[3];
+  const C2* b[3];
+  R cre[3], cim[3];
+};
+
+template <typename R, typename C2, int NL>
+__device__ __forceinline__ void field_coeffs(const V3<R> g[4], const Levels<C2, R>& L, const int32_t* eid,
+                                             const int32_t* fid, R out[10]) {
   R eps[6], bet[4];
 #pragma unroll
   for (int e = 0; e < 6; e++) {
-    const C2 d = edof[eid[e]];
-    eps[e] = cre * d.x - cim * d.y;
+    const C2 d = L.e[0][eid[e]];
+    R acc = L.cre[0] * d.x - L.cim[0] * d.y;
+#pragma unroll
+    for (int k = 1; k < NL; k++) {
+      const C2 dk = L.e[k][eid[e]];
+      acc += L.cre[k] * dk.x - L.cim[k] * dk.y;
+    }
+    eps[e] = acc;
   }
 #pragma unroll
   for (int f = 0; f < 4; f++) {
-    const C2 d = fdof[fid[f]];
-    bet[f] = cre * d.x - cim * d.y;
+    const C2 d = L.b[0][fid[f]];
+    R acc = L.cre[0] * d.x - L.cim[0] * d.y;
+#pragma unroll
+    for (int k = 1; k < NL; k++) {
+      const C2 dk = L.b[k][fid[f]];
+      acc += L.cre[k] * dk.x - L.cim[k] * dk.y;
+    }
+    bet[f] = acc;
   }
   V3<R> E0 = {eps[0] * g[1].x + eps[1] * g[2].x + eps[2] * g[3].x,
               eps[0] * g[1].y + eps[1] * g[2].y + eps[2] * g[3].y,
@@ -242,11 +263,10 @@ __device__ __forceinline__ void field_coeffs(const V3<R> g[4], const C2* __restr
   out[9] = beta;
 }
 
+template <int NL>
 __global__ void __launch_bounds__(kThreads) k_field_fp64(int64_t nt, const double* __restrict__ geom64,
                                                           const int4* __restrict__ te, const int4* __restrict__ tf,
-                                                          const double2* __restrict__ edof,
-                                                          const double2* __restrict__ fdof, double cre, double cim,
-                                                          double* __restrict__ field) {
+                                                          Levels<double2, double> L, double* __restrict__ field) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const double* G = geom64 + 12 * t;
@@ -259,16 +279,16 @@ __global__ void __launch_bounds__(kThreads) k_field_fp64(int64_t nt, const doubl
   const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
   const int32_t fid[4] = {f.x, f.y, f.z, f.w};
   double out[10];
-  field_coeffs<double, double2>(g, edof, fdof, eid, fid, cre, cim, out);
+  field_coeffs<double, double2, NL>(g, L, eid, fid, out);
   double2* o = reinterpret_cast<double2*>(field + 10 * t);
 #pragma unroll
   for (int i = 0; i < 5; i++) o[i] = make_double2(out[2 * i], out[2 * i + 1]);
 }
 
+template <int NL>
 __global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, float4* __restrict__ rec,
                                                          const int4* __restrict__ te, const int4* __restrict__ tf,
-                                                         const float2* __restrict__ edof,
-                                                         const float2* __restrict__ fdof, float cre, float cim) {
+                                                         Levels<float2, float> L) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const float4 a = rec[8 * t + 1], b = rec[8 * t + 2], c = rec[8 * t + 3];
@@ -281,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, float4* __re
   const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
   const int32_t fid[4] = {f.x, f.y, f.z, f.w};
   float out[10];
-  field_coeffs<float, float2>(g, edof, fdof, eid, fid, cre, cim, out);
+  field_coeffs<float, float2, NL>(g, L, eid, fid, out);
   rec[8 * t + 4] = make_float4(out[0], out[1], out[2], out[3]);
   rec[8 * t + 5] = make_float4(out[4], out[5], out[6], out[7]);
   rec[8 * t + 6] = make_float4(out[8], out[9], 0.f, 0.f);
@@ -2003,15 +2023,25 @@ static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
   return FEMPIC_OK;
 }
 
-extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, const fempic_envelope* envl,
-                                double omega0, double t, double dt, void* stream) {
-  if (!env || !envl) return fail(FEMPIC_EINVAL, "push_step: NULL env/envelope");
+// Host view of the envelope of one step: nl DoF levels with weights N_k(t).
+struct HostLevels {
+  int nl;
+  const void* e[3];
+  const void* b[3];
+  double w[3];
+  double amp;
+};
+
+static int push_step_impl(fempic_env* env, const fempic_particles* p, const HostLevels& H, double omega0,
+                          double t, double dt, void* stream) {
   int rc = check_particles(p, true);
   if (rc) return rc;
-  if (!envl->e_tilde || !envl->b_tilde) return fail(FEMPIC_EINVAL, "push_step: NULL DoF arrays");
-  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(omega0) || !std::isfinite(t) ||
-      !std::isfinite(envl->amp))
+  for (int k = 0; k < H.nl; k++)
+    if (!H.e[k] || !H.b[k]) return fail(FEMPIC_EINVAL, "push_step: NULL DoF arrays");
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(omega0) || !std::isfinite(t) || !std::isfinite(H.amp))
     return fail(FEMPIC_EINVAL, "push_step: non-finite or non-positive scalar");
+  for (int k = 0; k < H.nl; k++)
+    if (!std::isfinite(H.w[k])) return fail(FEMPIC_EINVAL, "push_step: non-finite level weight");
   cudaStream_t st = (cudaStream_t)stream;
   PushArgs A{};
   rc = fill_species(p, dt, &A.sp);
@@ -2021,23 +2051,39 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
     rc = ensure_mixed_accumulators(env, p->n_species, st);
     if (rc) return rc;
   }
-  // (c) carrier: phase and c in FP64 on the host
+  // (c) carrier: phase and c in FP64 on the host; level k enters with c N_k(t)
   const double phi = omega0 * t;
-  const double cre = envl->amp * std::cos(phi), cim = envl->amp * std::sin(phi);
+  const double cre = H.amp * std::cos(phi), cim = H.amp * std::sin(phi);
   const int64_t nt = env->h.nt;
   {
   LaunchTimer lt(env, st, FEMPIC_K_FIELD);
   lt.kernels = 1;
   if (mixed) {
-    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf,
-                                                      static_cast<const float2*>(envl->e_tilde),
-                                                      static_cast<const float2*>(envl->b_tilde), (float)cre,
-                                                      (float)cim);
+    Levels<float2, float> L{};
+    for (int k = 0; k < H.nl; k++) {
+      L.e[k] = static_cast<const float2*>(H.e[k]);
+      L.b[k] = static_cast<const float2*>(H.b[k]);
+      L.cre[k] = (float)(cre * H.w[k]);
+      L.cim[k] = (float)(cim * H.w[k]);
+    }
+    if (H.nl == 1)
+      k_field_f32<1><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf, L);
+    else
+      k_field_f32<3><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf, L);
   } else {
-    k_field_fp64<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf,
-                                                       static_cast<const double2*>(envl->e_tilde),
-                                                       static_cast<const double2*>(envl->b_tilde), cre, cim,
-                                                       static_cast<double*>(env->field));
+    Levels<double2, double> L{};
+    for (int k = 0; k < H.nl; k++) {
+      L.e[k] = static_cast<const double2*>(H.e[k]);
+      L.b[k] = static_cast<const double2*>(H.b[k]);
+      L.cre[k] = cre * H.w[k];
+      L.cim[k] = cim * H.w[k];
+    }
+    if (H.nl == 1)
+      k_field_fp64<1><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf, L,
+                                                            static_cast<double*>(env->field));
+    else
+      k_field_fp64<3><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf, L,
+                                                            static_cast<double*>(env->field));
   }
   }
   FEMPIC_CUDA(cudaGetLastError());
@@ -2115,6 +2161,46 @@ extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, cons
     }
   }
   FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_push_step(fempic_env* env, const fempic_particles* p, const fempic_envelope* envl,
+                                double omega0, double t, double dt, void* stream) {
+  if (!env || !envl) return fail(FEMPIC_EINVAL, "push_step: NULL env/envelope");
+  HostLevels H{};
+  H.nl = 1;
+  H.e[0] = envl->e_tilde;
+  H.b[0] = envl->b_tilde;
+  H.w[0] = 1.0;
+  H.amp = envl->amp;
+  return push_step_impl(env, p, H, omega0, t, dt, stream);
+}
+
+extern "C" int fempic_push_step3(fempic_env* env, const fempic_particles* p, const fempic_envelope3* envl,
+                                 double omega0, double t, double dt, void* stream) {
+  if (!env || !envl) return fail(FEMPIC_EINVAL, "push_step3: NULL env/envelope");
+  HostLevels H{};
+  H.nl = 3;
+  for (int k = 0; k < 3; k++) {
+    H.e[k] = envl->e_tilde[k];
+    H.b[k] = envl->b_tilde[k];
+    H.w[k] = envl->weight[k];
+  }
+  H.amp = envl->amp;
+  return push_step_impl(env, p, H, omega0, t, dt, stream);
+}
+
+extern "C" int fempic_lagrange3(const double* tau, double t, double* w_out) {
+  if (!tau || !w_out) return fail(FEMPIC_EINVAL, "lagrange3: NULL argument");
+  if (!std::isfinite(t) || !std::isfinite(tau[0]) || !std::isfinite(tau[1]) || !std::isfinite(tau[2]) ||
+      tau[0] == tau[1] || tau[1] == tau[2] || tau[0] == tau[2])
+    return fail(FEMPIC_EINVAL, "lagrange3: level times must be finite and distinct");
+  for (int k = 0; k < 3; k++) {
+    double w = 1.0;
+    for (int j = 0; j < 3; j++)
+      if (j != k) w *= (t - tau[j]) / (tau[k] - tau[j]);
+    w_out[k] = w;
+  }
   return FEMPIC_OK;
 }
 
@@ -2449,17 +2535,22 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
   const double phi = omega0 * t;
   double cre = envl->amp * std::cos(phi), cim = envl->amp * std::sin(phi);
   if (mixed) {
-    k_field_f32<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf,
-                                                      static_cast<const float2*>(envl->e_tilde),
-                                                      static_cast<const float2*>(envl->b_tilde), (float)cre,
-                                                      (float)cim);
+    Levels<float2, float> L{};
+    L.e[0] = static_cast<const float2*>(envl->e_tilde);
+    L.b[0] = static_cast<const float2*>(envl->b_tilde);
+    L.cre[0] = (float)cre;
+    L.cim[0] = (float)cim;
+    k_field_f32<1><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf, L);
     cre = (double)(float)cre;
     cim = (double)(float)cim;
   } else {
-    k_field_fp64<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf,
-                                                       static_cast<const double2*>(envl->e_tilde),
-                                                       static_cast<const double2*>(envl->b_tilde), cre, cim,
-                                                       static_cast<double*>(env->field));
+    Levels<double2, double> L{};
+    L.e[0] = static_cast<const double2*>(envl->e_tilde);
+    L.b[0] = static_cast<const double2*>(envl->b_tilde);
+    L.cre[0] = cre;
+    L.cim[0] = cim;
+    k_field_fp64<1><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, env->tf, L,
+                                                          static_cast<double*>(env->field));
   }
   FEMPIC_CUDA(cudaGetLastError());
   if (before->n > 0) {

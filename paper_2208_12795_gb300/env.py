@@ -159,6 +159,28 @@ class FempicEnv:
         envl = capi.fempic_envelope(_ptr(e_dof), _ptr(b_dof), float(amp))
         capi.fempic_push_step(self.h, st.cstruct(), envl, omega0, t, dt, _stream(stream))
 
+    def push_step3(self, st: ParticleState, e_levels, b_levels, weights, amp: float, omega0: float, t: float,
+                   dt: float, stream=None):
+        """One step with the envelope interpolated from three DoF levels
+        (levels n-1, n, n+1 with their Lagrange weights at t)."""
+        if len(e_levels) != 3 or len(b_levels) != 3 or len(weights) != 3:
+            raise capi.FempicError("three levels and three weights are required")
+        for e_dof, b_dof in zip(e_levels, b_levels):
+            if e_dof.dtype != self.dof_dtype or b_dof.dtype != self.dof_dtype:
+                raise capi.FempicError(f"DoFs must be {self.dof_dtype} for this precision form")
+            if e_dof.numel() != self.n_edges or b_dof.numel() != self.n_faces or not e_dof.is_cuda:
+                raise capi.FempicError("DoF arrays must be device tensors of length n_edges / n_faces")
+        vdt = torch.float64 if self.precision == FEMPIC_FP64 else torch.float32
+        if st.vx.dtype != vdt:
+            raise capi.FempicError(f"velocities must be {vdt} for this precision form")
+        envl = capi.fempic_envelope3()
+        for k in range(3):
+            envl.e_tilde[k] = _ptr(e_levels[k])
+            envl.b_tilde[k] = _ptr(b_levels[k])
+            envl.weight[k] = float(weights[k])
+        envl.amp = float(amp)
+        capi.fempic_push_step3(self.h, st.cstruct(), envl, omega0, t, dt, _stream(stream))
+
     def deposit(self, omega0: float, t_next: float, dG_out=None, G_cum_out=None, G_env_out=None, stream=None):
         capi.fempic_deposit(self.h, omega0, t_next, _ptr(dG_out), _ptr(G_cum_out), _ptr(G_env_out),
                             _stream(stream))
