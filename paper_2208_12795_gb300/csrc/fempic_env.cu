@@ -80,6 +80,15 @@ struct __align__(16) CrossRec {
   int32_t p;
 };
 
+// FP64-form record of a leaving particle: start point and new velocity in
+// FP64.
+struct __align__(16) CrossRec64 {
+  double a[3];
+  double v[3];
+  int32_t T;
+  int32_t p;
+};
+
 struct PushArgs {
   int64_t n;
   double* x;
@@ -108,6 +117,7 @@ struct PushArgs {
                                 // [ns][nt][8] int64 in units of 2^-48 (q w)
   unsigned long long* stats;    // [0] crossings, [1] frozen, [2] staging wait timeouts
   CrossRec* xrec;               // mixed form: crossing records, 256-slot region per tile
+  CrossRec64* xrec64;           // FP64 form: the same, FP64 records
   int32_t* xcount;              // mixed form: records per tile
 };
 
@@ -347,11 +357,24 @@ __device__ __forceinline__ void deposit64(const PushArgs& A, int32_t T, const do
 
 __device__ __forceinline__ int4 ldg_int4(const int4* p) { return __ldg(p); }
 
+// FP64 form, common path: one particle per thread (a block is one 256-particle
+// tile).  Gather, Boris, position update and the barycentrics of both ends
+// in the home tet; a particle that stays deposits its segment and is done; a
+// particle that leaves stores its new state provisionally and a record for
+// the crossing pass, so the face walk does not run here with most lanes idle.
 __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
+  __shared__ int32_t total;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  unsigned ncr = 0, nfrz = 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  if (threadIdx.x == 0) total = 0;
+  __syncthreads();
+  unsigned nfrz = 0;
+  bool leave = false;
+  double a[3] = {0.0, 0.0, 0.0}, vn[3] = {0.0, 0.0, 0.0};
+  int32_t T = -1;
   if (p < A.n) {
-    int32_t T = A.tet[p];
+    T = A.tet[p];
     if (T >= A.nt) {
       A.tet[p] = -1;
       A.status[p] = FEMPIC_P_LOST;
@@ -362,7 +385,9 @@ __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
       double* vxp = static_cast<double*>(A.vx);
       double* vyp = static_cast<double*>(A.vy);
       double* vzp = static_cast<double*>(A.vz);
-      double a[3] = {A.x[p], A.y[p], A.z[p]};
+      a[0] = A.x[p];
+      a[1] = A.y[p];
+      a[2] = A.z[p];
       const double v[3] = {vxp[p], vyp[p], vzp[p]};
       const double* G = A.geom64 + 12 * (int64_t)T;
       const double2* F = reinterpret_cast<const double2*>(static_cast<const double*>(A.field) + 10 * (int64_t)T);
@@ -384,110 +409,216 @@ __global__ void __launch_bounds__(kThreads) k_push_fp64(PushArgs A) {
       const double vpx = vmx + (vmy * tz - vmz * ty);
       const double vpy = vmy + (vmz * tx - vmx * tz);
       const double vpz = vmz + (vmx * ty - vmy * tx);
-      double vn[3] = {vmx + (vpy * sz - vpz * sy) + kq * Ex, vmy + (vpz * sx - vpx * sz) + kq * Ey,
-                      vmz + (vpx * sy - vpy * sx) + kq * Ez};
-      double b[3] = {a[0] + A.dt * vn[0], a[1] + A.dt * vn[1], a[2] + A.dt * vn[2]};
+      vn[0] = vmx + (vpy * sz - vpz * sy) + kq * Ex;
+      vn[1] = vmy + (vpz * sx - vpx * sz) + kq * Ey;
+      vn[2] = vmz + (vpx * sy - vpy * sx) + kq * Ez;
+      const double b[3] = {fma(A.dt, vn[0], a[0]), fma(A.dt, vn[1], a[1]), fma(A.dt, vn[2], a[2])};
       if (!(finite_bits(vn[0]) && finite_bits(vn[1]) && finite_bits(vn[2]) && finite_bits(b[0]) &&
             finite_bits(b[1]) && finite_bits(b[2]))) {
         A.status[p] = FEMPIC_P_NONFINITE;
         A.tet[p] = -2 - T;
         nfrz = 1;
       } else {
-        // (e) track + (f) deposit
-        double la[4], lb[4], lp[4];
+        double la[4], lb[4];
         bary64_d(G, dx, dy, dz, la);
-        int entry = -1;
-        int32_t nc = 0;
-        uint8_t st = FEMPIC_P_OK;
-        for (;;) {
-          bary64(A.geom64 + 12 * (int64_t)T, b, lb);
-          int kx = -1;
-          double smin = INFINITY;
-#pragma unroll
-          for (int k = 0; k < 4; k++) {
-            if (k == entry || !negative_bits(lb[k])) continue;
-            double sk = la[k] / (la[k] - lb[k]);
-            if (sk < 0.0) sk = 0.0;
-            if (sk < smin) {
-              smin = sk;
-              kx = k;
-            }
-          }
-          if (kx < 0) {
-            deposit64(A, T, la, lb, qw);
-            a[0] = b[0];
-            a[1] = b[1];
-            a[2] = b[2];
-            break;
-          }
-#pragma unroll
-          for (int i = 0; i < 4; i++) lp[i] = (i == kx) ? 0.0 : fma(smin, lb[i] - la[i], la[i]);
-          deposit64(A, T, la, lp, qw);
-          nc++;
-#pragma unroll
-          for (int c = 0; c < 3; c++) a[c] = fma(smin, b[c] - a[c], a[c]);
-          if (nc > A.max_cross) {
-            st = FEMPIC_P_CAP;
-            break;
-          }
-          const int4 nbv = ldg_int4(&A.nb[T]);
-          const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
-          if (nbt >= 0) {
-            const int4 o4 = ldg_int4(&A.tn[T]), n4 = ldg_int4(&A.tn[nbt]);
-            const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nn[4] = {n4.x, n4.y, n4.z, n4.w};
-            int ent = 0;
-#pragma unroll
-            for (int i2 = 0; i2 < 4; i2++) {
-              int hit = -1;
-#pragma unroll
-              for (int i = 0; i < 4; i++)
-                if (on[i] == nn[i2]) hit = i;
-              double val = 0.0;
-#pragma unroll
-              for (int i = 0; i < 4; i++)
-                if (i == hit) val = lp[i];
-              la[i2] = val;
-              if (hit < 0) ent = i2;
-            }
-            T = nbt;
-            entry = ent;
-          } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
-            const int code = -1 - nbt, ax = code >> 1, side = code & 1;
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-              if (c == ax) {
-                const double L = side ? A.hi[c] : A.lo[c];
-                b[c] = 2.0 * L - b[c];
-                vn[c] = -vn[c];
-              }
-#pragma unroll
-            for (int i = 0; i < 4; i++) la[i] = lp[i];
-            entry = kx;
-          } else {
-            st = FEMPIC_P_ABSORBED;
-            break;
-          }
-        }
-        A.x[p] = a[0];
-        A.y[p] = a[1];
-        A.z[p] = a[2];
+        bary64(G, b, lb);
+        A.x[p] = b[0];
+        A.y[p] = b[1];
+        A.z[p] = b[2];
         vxp[p] = vn[0];
         vyp[p] = vn[1];
         vzp[p] = vn[2];
-        if (st != FEMPIC_P_OK) {
-          A.status[p] = st;
-          T = -2 - T;
-          nfrz = 1;
-        }
-        A.tet[p] = T;
-        if (A.ncross) A.ncross[p] += nc;
-        ncr = (unsigned)nc;
+        leave = negative_bits(lb[0]) || negative_bits(lb[1]) || negative_bits(lb[2]) || negative_bits(lb[3]);
+        if (!leave) deposit64(A, T, la, lb, qw);   // (f) the whole segment is in the home tet
       }
     }
   }
-  ncr = __reduce_add_sync(0xffffffffu, ncr);
-  nfrz = __reduce_add_sync(0xffffffffu, nfrz);
-  if ((threadIdx.x & 31) == 0) {
+  // (e) leaving particles: records for the crossing pass, in the block's region
+  const unsigned qmask = __ballot_sync(full, leave);
+  if (qmask) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&total, __popc(qmask));
+    base = __shfl_sync(full, base, 0);
+    if (leave) {
+      CrossRec64& r = A.xrec64[blockIdx.x * (int64_t)kThreads + base + __popc(qmask & ((1u << lane) - 1u))];
+      r.a[0] = a[0];
+      r.a[1] = a[1];
+      r.a[2] = a[2];
+      r.v[0] = vn[0];
+      r.v[1] = vn[1];
+      r.v[2] = vn[2];
+      r.T = T;
+      r.p = (int32_t)p;
+    }
+  }
+  nfrz = __reduce_add_sync(full, nfrz);
+  if (lane == 0 && nfrz) atomicAdd(A.stats + 1, (unsigned long long)nfrz);
+  __syncthreads();
+  if (threadIdx.x == 0) A.xcount[blockIdx.x] = total;
+}
+
+// FP64 form, crossing pass: the walk of one leaving particle, one face per
+// call, in FP64 (the paper's exit parameter s_k = la_k / (la_k - lb_k), the
+// crossing point a + s (b - a), barycentrics carried exactly onto the
+// neighbour's shared nodes).
+struct CrossState64 {
+  double a[3], b[3], vn[3];
+  double la[4], lb[4];
+  int32_t T, p;
+  int entry, nc, s;
+  uint8_t st;
+  bool reflected;
+};
+
+__device__ __forceinline__ void cross64_begin(const PushArgs& A, const CrossRec64& r, CrossState64& c) {
+  c.p = r.p;
+  c.T = r.T;
+  c.s = species_of(A.sp, r.p);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    c.a[k] = r.a[k];
+    c.vn[k] = r.v[k];
+    c.b[k] = fma(A.dt, r.v[k], r.a[k]);
+  }
+  const double* G = A.geom64 + 12 * (int64_t)c.T;
+  bary64(G, c.a, c.la);
+  bary64(G, c.b, c.lb);
+  c.entry = -1;
+  c.nc = 0;
+  c.st = FEMPIC_P_OK;
+  c.reflected = false;
+}
+
+__device__ __forceinline__ bool cross64_advance(const PushArgs& A, CrossState64& c) {
+  const double qw = A.sp.qw[c.s];
+  int kx = -1;
+  double smin = INFINITY;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (k == c.entry || !negative_bits(c.lb[k])) continue;
+    double sk = c.la[k] / (c.la[k] - c.lb[k]);
+    if (sk < 0.0) sk = 0.0;
+    if (sk < smin) {
+      smin = sk;
+      kx = k;
+    }
+  }
+  if (kx < 0) {
+    deposit64(A, c.T, c.la, c.lb, qw);
+#pragma unroll
+    for (int k = 0; k < 3; k++) c.a[k] = c.b[k];
+    return true;
+  }
+  double lp[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) lp[i] = (i == kx) ? 0.0 : fma(smin, c.lb[i] - c.la[i], c.la[i]);
+  deposit64(A, c.T, c.la, lp, qw);
+  c.nc++;
+#pragma unroll
+  for (int k = 0; k < 3; k++) c.a[k] = fma(smin, c.b[k] - c.a[k], c.a[k]);
+  if (c.nc > A.max_cross) {
+    c.st = FEMPIC_P_CAP;
+    return true;
+  }
+  const int4 nbv = ldg_int4(&A.nb[c.T]);
+  const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+  if (nbt >= 0) {
+    const int4 o4 = ldg_int4(&A.tn[c.T]), n4 = ldg_int4(&A.tn[nbt]);
+    const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nn[4] = {n4.x, n4.y, n4.z, n4.w};
+    int ent = 0;
+#pragma unroll
+    for (int i2 = 0; i2 < 4; i2++) {
+      int hit = -1;
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (on[i] == nn[i2]) hit = i;
+      double val = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (i == hit) val = lp[i];
+      c.la[i2] = val;
+      if (hit < 0) ent = i2;
+    }
+    c.T = nbt;
+    c.entry = ent;
+  } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
+    const int code = -1 - nbt, ax = code >> 1, side = code & 1;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      if (k == ax) {
+        const double L = side ? A.hi[k] : A.lo[k];
+        c.b[k] = 2.0 * L - c.b[k];
+        c.vn[k] = -c.vn[k];
+      }
+    c.reflected = true;
+#pragma unroll
+    for (int i = 0; i < 4; i++) c.la[i] = lp[i];
+    c.entry = kx;
+  } else {
+    c.st = FEMPIC_P_ABSORBED;
+    return true;
+  }
+  bary64(A.geom64 + 12 * (int64_t)c.T, c.b, c.lb);
+  return false;
+}
+
+__device__ __forceinline__ void cross64_finish(const PushArgs& A, const CrossState64& c, unsigned& ncr,
+                                               unsigned& nfrz) {
+  const int64_t p = c.p;
+  if (c.st != FEMPIC_P_OK || c.reflected) {   // otherwise a = b, already stored
+    A.x[p] = c.a[0];
+    A.y[p] = c.a[1];
+    A.z[p] = c.a[2];
+  }
+  if (c.reflected) {
+    static_cast<double*>(A.vx)[p] = c.vn[0];
+    static_cast<double*>(A.vy)[p] = c.vn[1];
+    static_cast<double*>(A.vz)[p] = c.vn[2];
+  }
+  int32_t T = c.T;
+  if (c.st != FEMPIC_P_OK) {
+    A.status[p] = c.st;
+    T = -2 - T;
+    nfrz++;
+  }
+  A.tet[p] = T;
+  if (A.ncross) A.ncross[p] += c.nc;
+  ncr += (unsigned)c.nc;
+}
+
+// One warp per 256-particle tile region; lanes take the next record when
+// their particle is done (as in the mixed form's crossing pass).
+__global__ void __launch_bounds__(kThreads) k_cross_fp64(PushArgs A, int64_t ntiles) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned ncr = 0, nfrz = 0;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
+    const int32_t cnt = A.xcount[t];
+    int32_t next = 0;
+    bool have = false;
+    CrossState64 c;
+    for (;;) {
+      const unsigned idle = __ballot_sync(full, !have);
+      if (next < cnt && idle) {
+        const int32_t idx = next + __popc(idle & lt);
+        if (!have && idx < cnt) {
+          cross64_begin(A, A.xrec64[t * kThreads + idx], c);
+          have = true;
+        }
+        next += __popc(idle);
+      }
+      if (!__any_sync(full, have)) break;
+      if (have && cross64_advance(A, c)) {
+        cross64_finish(A, c, ncr, nfrz);
+        have = false;
+      }
+    }
+  }
+  ncr = __reduce_add_sync(full, ncr);
+  nfrz = __reduce_add_sync(full, nfrz);
+  if (lane == 0) {
     if (ncr) atomicAdd(A.stats, (unsigned long long)ncr);
     if (nfrz) atomicAdd(A.stats + 1, (unsigned long long)nfrz);
   }
@@ -1742,6 +1873,7 @@ struct fempic_env {
   int32_t ns_last = 0;
   double* tetgrad = nullptr;        // adjoint of the per-tet affine field [nt][10]
   CrossRec* xrec = nullptr;         // mixed form crossing queue [xtiles * 256]
+  CrossRec64* xrec64 = nullptr;     // FP64 form crossing queue [xtiles * 256]
   int32_t* xcount = nullptr;        // [xtiles]
   int64_t xtiles = 0;
   int num_sms = 1;
@@ -1800,7 +1932,7 @@ static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
-                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->xrec, e->xcount,
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->xrec, e->xrec64, e->xcount,
                   e->dGe};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -1987,15 +2119,20 @@ extern "C" int fempic_locate(fempic_env* env, const fempic_particles* p, void* s
 static int ensure_xqueue(fempic_env* env, int64_t n, cudaStream_t st) {
   const int64_t tiles = (n + kThreads - 1) / kThreads;
   if (env->xtiles >= tiles) return FEMPIC_OK;
-  if (env->xrec) {
+  if (env->xcount) {
     FEMPIC_CUDA(cudaStreamSynchronize(st));
     cudaFree(env->xrec);
+    cudaFree(env->xrec64);
     cudaFree(env->xcount);
     env->xrec = nullptr;
+    env->xrec64 = nullptr;
     env->xcount = nullptr;
     env->xtiles = 0;
   }
-  FEMPIC_CUDA(dalloc(&env->xrec, tiles * kThreads));
+  if (env->opt.precision == FEMPIC_MIXED)
+    FEMPIC_CUDA(dalloc(&env->xrec, tiles * kThreads));
+  else
+    FEMPIC_CUDA(dalloc(&env->xrec64, tiles * kThreads));
   FEMPIC_CUDA(dalloc(&env->xcount, tiles));
   env->xtiles = tiles;
   return FEMPIC_OK;
@@ -2119,13 +2256,11 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
   A.dG = env->dG;
   A.dGq = env->dGq;
   A.stats = env->stats;
-  if (mixed) {
-    rc = ensure_xqueue(env, p->n, st);
-    if (rc) return rc;
-    A.xrec = env->xrec;
-    A.xcount = env->xcount;
-
-  }
+  rc = ensure_xqueue(env, p->n, st);
+  if (rc) return rc;
+  A.xrec = env->xrec;
+  A.xrec64 = env->xrec64;
+  A.xcount = env->xcount;
   {
     LaunchTimer lt(env, st, FEMPIC_K_PUSH);
     if (mixed) {
@@ -2158,6 +2293,12 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
     } else {
       k_push_fp64<<<blocks_for(p->n), kThreads, 0, st>>>(A);
       lt.kernels = 1;
+      const int64_t all_tiles = (p->n + kThreads - 1) / kThreads;
+      const unsigned cross_blocks = (unsigned)std::min<int64_t>(
+          (all_tiles + 7) / 8, (int64_t)env->num_sms * kCrossWarpsPerSm / (kThreads / 32));
+      LaunchTimer lc(env, st, FEMPIC_K_CROSS);   // nested: also inside the push bracket
+      k_cross_fp64<<<cross_blocks, kThreads, 0, st>>>(A, all_tiles);
+      lc.kernels = 1;
     }
   }
   FEMPIC_CUDA(cudaGetLastError());
