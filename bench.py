@@ -401,6 +401,7 @@ def adjoint_window(rank):
         sch = A.Schedule(wl.amp, wl.omega0, wl.dt, wl.steps, 10)
         A.kinetic_energy_and_grad(env, st0, e, b, A.Schedule(wl.amp, wl.omega0, wl.dt, 4, 2))   # warm-up
         torch.cuda.synchronize()
+        env.profile(True)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record()
         final, ckpts = A.forward_checkpointed(env, st0, e, b, sch)
@@ -412,10 +413,13 @@ def adjoint_window(rank):
         ev[2].record()
         torch.cuda.synchronize()
         t_fwd, t_rev = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+        prof = env.profile_read()
+        env.profile(False)
         units = st0.n * sch.steps
         res[form] = {"forward_particle_steps_per_s": units / t_fwd,
                      "reverse_particle_steps_per_s": units / t_rev,
-                     "gradient_window_s": t_fwd + t_rev}
+                     "gradient_window_s": t_fwd + t_rev,
+                     "kernel_ms": {k: v["ms"] for k, v in prof.items() if v["launches"]}}
         env.close()
     return {"workload": "cube48_4M_adjoint: 48^3x6 cube, 4M electrons at 5 eV, TE101 10 kV/m, K=50, "
                         "checkpoint every 10; loss = kinetic energy after K steps",

@@ -254,6 +254,22 @@ int fempic_kinetic_energy(fempic_env* env, const fempic_particles* p, double* ke
  * Errors: EINVAL (mismatch), ENOMEM, ECUDA. */
 int fempic_sort(fempic_env* env, const fempic_particles* in, const fempic_particles* out, void* stream);
 
+/* fempic_sort that also writes perm[q] = the index in `in` of the particle
+ * placed at position q of `out` (device int32 [n], caller owned), so that
+ * per-particle data kept elsewhere (an adjoint state) can follow the sort.
+ * Errors: as fempic_sort, and EINVAL for a NULL perm. */
+int fempic_sort_perm(fempic_env* env, const fempic_particles* in, const fempic_particles* out, int32_t* perm,
+                     void* stream);
+
+/* Carry an adjoint state back across a sort (the transpose of the
+ * permutation fempic_sort_perm applied to the particles): out[perm[q]] =
+ * in[q] for rbar (f64) and vbar (the env's velocity dtype).  in and out are
+ * caller-owned device arrays of the same n that must not overlap; perm must
+ * be a permutation of 0..n-1 (entries outside that range are skipped).
+ * Stream-ordered.  Errors: EINVAL, ECUDA. */
+int fempic_adjoint_unpermute(fempic_env* env, const fempic_adjoint* in, const fempic_adjoint* out,
+                             const int32_t* perm, void* stream);
+
 /* Same sort as fempic_sort, for callers that must not allocate device
  * memory once they are running (the paper has no counterpart; this is an
  * integration entry point).  Examples: an application whose device memory is
@@ -286,7 +302,8 @@ int fempic_sort_noalloc(fempic_env* env, const fempic_particles* in, const fempi
 #define FEMPIC_K_FINALIZE 3   /* deposit finalize */
 #define FEMPIC_K_CHARGE 4     /* nodal charge */
 #define FEMPIC_K_SORT 5       /* particle sort by tet */
-#define FEMPIC_K_CROSS 6      /* mixed form crossing pass; its bracket lies inside FEMPIC_K_PUSH's */
+#define FEMPIC_K_CROSS 6      /* crossing pass; its bracket lies inside FEMPIC_K_PUSH's */
+#define FEMPIC_K_ADJOINT 7    /* adjoint step: field rebuild, particle adjoint, field adjoint */
 #define FEMPIC_K_COUNT 8
 
 /* Measurement support (no counterpart in the paper): while enabled, every

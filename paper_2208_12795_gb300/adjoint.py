@@ -8,6 +8,12 @@ last, recomputes the segment's states from its checkpoint and runs the adjoint
 steps backwards.  Memory: one state per checkpoint plus `every` + 1 states for
 the segment being reversed.
 
+Each checkpoint is taken after sorting the state by (species, tet)
+(`fempic_sort_perm`), so the steps of every segment run on tet-ordered
+particles; the reverse sweep carries the adjoint back across each of those
+sorts with `fempic_adjoint_unpermute`.  The gradient is returned in the
+particle order of the initial state.
+
 The derivative is that of the piecewise smooth map for the tet sequence the
 forward run took (a particle that crosses a face keeps the crossing; a
 perturbation that would change the sequence is outside what it describes).
@@ -34,6 +40,12 @@ class AdjointState:
         self.rx, self.ry, self.rz = z(torch.float64), z(torch.float64), z(torch.float64)
         self.vx, self.vy, self.vz = z(vdtype), z(vdtype), z(vdtype)
         self.n = n
+
+    def swap(self, other: "AdjointState"):
+        for k in ("rx", "ry", "rz", "vx", "vy", "vz"):
+            a, b = getattr(self, k), getattr(other, k)
+            setattr(self, k, b)
+            setattr(other, k, a)
 
     def cstruct(self) -> capi.fempic_adjoint:
         a = capi.fempic_adjoint()
@@ -78,13 +90,30 @@ def _step(env, st, e, b, sch: Schedule, k: int):
     env.reset_deposit()
 
 
-def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule):
-    """Run sch.steps steps from a copy of st0; returns (final state, checkpoints)."""
-    st = clone_state(st0)
+class Checkpoint:
+    """A checkpointed state and the sort that produced its order from the
+    state before it (perm[q] = previous index of particle q; None: unsorted)."""
+
+    def __init__(self, st: ParticleState, perm):
+        self.st, self.perm = st, perm
+
+
+def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule, sort: bool = True):
+    """Run sch.steps steps from a copy of st0; returns (final state,
+    checkpoints).  With `sort`, the state is sorted by tet at every
+    checkpoint (the final state is in the last checkpoint's order)."""
+    st = st0 if (sort and sch.steps > 0) else clone_state(st0)
     ckpts = []
     for k in range(sch.steps):
         if k % sch.every == 0:
-            ckpts.append(clone_state(st))
+            if sort:
+                srt = st.empty_like()
+                perm = torch.empty(st.n, dtype=torch.int32, device=st.x.device)
+                env.sort_perm(st, srt, perm)
+                ckpts.append(Checkpoint(srt, perm))
+                st = clone_state(srt)
+            else:
+                ckpts.append(Checkpoint(clone_state(st), None))
         _step(env, st, e, b, sch, k)
     return st, ckpts
 
@@ -95,11 +124,12 @@ def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState)
     eg = torch.zeros(env.n_edges, dtype=torch.complex128, device=e.device)
     bg = torch.zeros(env.n_faces, dtype=torch.complex128, device=b.device)
     stream = _stream(None)
+    spare = None
     for s in range(len(ckpts) - 1, -1, -1):
         k0 = s * sch.every
         k1 = min(sch.steps, k0 + sch.every)
-        stash = [ckpts[s]]
-        cur = clone_state(ckpts[s])
+        stash = [ckpts[s].st]
+        cur = clone_state(ckpts[s].st)
         for k in range(k0, k1):
             _step(env, cur, e, b, sch, k)
             stash.append(clone_state(cur))
@@ -110,6 +140,11 @@ def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState)
             capi.fempic_push_step_adjoint(env.h, stash[j].cstruct(), stash[j + 1].cstruct(), envl, sch.omega0, t,
                                           sch.dt, adj.cstruct(), _ptr(eg), _ptr(bg), stream)
         del stash, cur
+        if ckpts[s].perm is not None:   # back to the order before this checkpoint's sort
+            if spare is None:
+                spare = AdjointState(adj.n, adj.vx.dtype, device=adj.rx.device)
+            capi.fempic_adjoint_unpermute(env.h, adj.cstruct(), spare.cstruct(), _ptr(ckpts[s].perm), stream)
+            adj.swap(spare)
     return eg, bg
 
 

@@ -28,8 +28,10 @@ FEMPIC_WALL_ABSORB = 1
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step", "fempic_push_step3",
            "fempic_lagrange3",
            "fempic_deposit", "fempic_reset_deposit", "fempic_nodal_charge", "fempic_stats",
-           "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
-FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS = range(7)
+           "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
+           "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
+FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS, \
+    FEMPIC_K_ADJOINT = range(8)
 FEMPIC_K_COUNT = 8
 FEMPIC_SORT_NOALLOC_MAX_KEYS = 1 << 21
 
@@ -103,6 +105,10 @@ def load(path: str = LIB_PATH):
                                               C.c_void_p]
         lib.fempic_sort.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
         lib.fempic_sort_noalloc.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p]
+        lib.fempic_sort_perm.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles), C.c_void_p,
+                                         C.c_void_p]
+        lib.fempic_adjoint_unpermute.argtypes = [C.c_void_p, P(fempic_adjoint), P(fempic_adjoint), C.c_void_p,
+                                                 C.c_void_p]
         lib.fempic_profile_enable.argtypes = [C.c_void_p, C.c_int32]
         lib.fempic_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_last_error.restype = C.c_char_p
@@ -188,6 +194,15 @@ def fempic_kinetic_energy(env, parts: fempic_particles, ke, seed=None, stream=0)
 
 def fempic_sort(env, parts_in: fempic_particles, parts_out: fempic_particles, stream=0):
     check(load().fempic_sort(env, C.byref(parts_in), C.byref(parts_out), stream), "fempic_sort")
+
+
+def fempic_sort_perm(env, parts_in: fempic_particles, parts_out: fempic_particles, perm, stream=0):
+    check(load().fempic_sort_perm(env, C.byref(parts_in), C.byref(parts_out), perm, stream), "fempic_sort_perm")
+
+
+def fempic_adjoint_unpermute(env, adj_in: fempic_adjoint, adj_out: fempic_adjoint, perm, stream=0):
+    check(load().fempic_adjoint_unpermute(env, C.byref(adj_in), C.byref(adj_out), perm, stream),
+          "fempic_adjoint_unpermute")
 
 
 def fempic_sort_noalloc(env, parts_in: fempic_particles, parts_out: fempic_particles, stream=0):

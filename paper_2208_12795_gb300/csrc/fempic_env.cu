@@ -1508,6 +1508,7 @@ struct SortArgs {
   int32_t* oncross;
   const int32_t* offsets;
   int32_t* cursor;
+  int32_t* operm;               // optional: source index of each output position
 };
 
 __global__ void __launch_bounds__(kThreads) k_sort_scatter(SortArgs A) {
@@ -1538,6 +1539,37 @@ __global__ void __launch_bounds__(kThreads) k_sort_scatter(SortArgs A) {
   A.otet[q] = T;
   A.ostatus[q] = A.status[p];
   if (A.oncross) A.oncross[q] = A.ncross[p];
+  if (A.operm) A.operm[q] = (int32_t)p;
+}
+
+// Adjoint state carried back across a sort: out[perm[q]] = in[q].
+struct AdjPermArgs {
+  int64_t n;
+  int32_t vbytes;
+  const int32_t* perm;
+  const double *rx, *ry, *rz;
+  const void *vx, *vy, *vz;
+  double *ox, *oy, *oz;
+  void *ovx, *ovy, *ovz;
+};
+
+__global__ void __launch_bounds__(kThreads) k_adjoint_unpermute(AdjPermArgs A) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= A.n) return;
+  const int64_t p = A.perm[q];
+  if (p < 0 || p >= A.n) return;   // not a permutation of 0..n-1: leave the slot (checked on the host side too)
+  A.ox[p] = A.rx[q];
+  A.oy[p] = A.ry[q];
+  A.oz[p] = A.rz[q];
+  if (A.vbytes == 8) {
+    static_cast<double*>(A.ovx)[p] = static_cast<const double*>(A.vx)[q];
+    static_cast<double*>(A.ovy)[p] = static_cast<const double*>(A.vy)[q];
+    static_cast<double*>(A.ovz)[p] = static_cast<const double*>(A.vz)[q];
+  } else {
+    static_cast<float*>(A.ovx)[p] = static_cast<const float*>(A.vx)[q];
+    static_cast<float*>(A.ovy)[p] = static_cast<const float*>(A.vy)[q];
+    static_cast<float*>(A.ovz)[p] = static_cast<const float*>(A.vz)[q];
+  }
 }
 
 // ----------------------------------------------------------------- adjoint
@@ -1547,8 +1579,12 @@ __global__ void __launch_bounds__(kThreads) k_sort_scatter(SortArgs A) {
 // the sign of each velocity component after the step, and propagates the
 // adjoint (rbar, vbar) of the state after the step back to the state before
 // it.  The adjoint of the per-tet affine field (E0, W, B0, beta) is reduced
-// over runs of equal tets in each warp and added to tetgrad in FP64; the
-// transposed pre-pass k_field_adjoint maps it to the complex DoFs.  A
+// over runs of equal tets in each warp and added to tetgrad in FP64; in the
+// mixed form a warp whose particles fall into more than 4 runs (the state
+// drifts out of tet order between sorts, and the gradient window does not
+// sort) adds each lane's 10 values straight into an FP32 row per tet with
+// vector atomics instead.  The transposed pre-pass k_field_adjoint maps both
+// to the complex DoFs.  A
 // particle frozen during the step gets a zero adjoint (its later state no
 // longer depends on its earlier one through the step map).
 struct AdjArgs {
@@ -1577,6 +1613,7 @@ struct AdjArgs {
   void* vby;
   void* vbz;
   double* tetgrad;           // [nt][10]
+  float* tetgrad32;          // mixed form: [nt][12] (10 used), per-lane vector atomics
 };
 
 template <typename R>
@@ -1591,6 +1628,12 @@ template <typename R>
 __device__ __forceinline__ R vd3(Vec<R> a, Vec<R> b) {
   return a.x * b.x + a.y * b.y + a.z * b.z;
 }
+
+__device__ __forceinline__ double flip_sign(double x, bool neg) {
+  return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
+}
+__device__ __forceinline__ double widen(float x) { return f32_to_f64(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
 
 template <typename R>
 __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, int32_t T, R out[10]) {
@@ -1646,8 +1689,9 @@ __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, in
   R* vbx = static_cast<R*>(A.vbx);
   R* vby = static_cast<R*>(A.vby);
   R* vbz = static_cast<R*>(A.vbz);
-  // adjoint of the output state, mirrored back
-  const double rbx = (double)mx * A.rbx[p], rby = (double)my * A.rby[p], rbz = (double)mz * A.rbz[p];
+  // adjoint of the output state, mirrored back (sign flips on the bit pattern)
+  const double rbx = flip_sign(A.rbx[p], mx < R(0)), rby = flip_sign(A.rby[p], my < R(0)),
+               rbz = flip_sign(A.rbz[p], mz < R(0));
   const R dt = (R)A.dt;
   // b = r + dt vn
   Vec<R> vnb = {mx * vbx[p] + dt * (R)rbx, my * vby[p] + dt * (R)rby, mz * vbz[p] + dt * (R)rbz};
@@ -1674,9 +1718,9 @@ __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, in
   const Vec<R> Wb = vx3(Eb, d);
   const Vec<R> db1 = vx3(W, Eb);
   const R betab = vd3(Bb, d);
-  A.rbx[p] = rbx + (double)(db1.x + beta * Bb.x);
-  A.rby[p] = rby + (double)(db1.y + beta * Bb.y);
-  A.rbz[p] = rbz + (double)(db1.z + beta * Bb.z);
+  A.rbx[p] = rbx + widen(db1.x + beta * Bb.x);
+  A.rby[p] = rby + widen(db1.y + beta * Bb.y);
+  A.rbz[p] = rbz + widen(db1.z + beta * Bb.z);
   vbx[p] = vmb.x;
   vby[p] = vmb.y;
   vbz[p] = vmb.z;
@@ -1710,6 +1754,15 @@ __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
   const int32_t prev = __shfl_up_sync(full, key, 1);
   const bool head = lane == 0 || prev != key;
   const unsigned heads = __ballot_sync(full, head);
+  if (sizeof(R) == 4 && __popc(heads) > 4) {   // short runs: per-lane vector atomics
+    if (key >= 0) {
+      float* row = A.tetgrad32 + 12 * (int64_t)key;
+      atomicAdd(reinterpret_cast<float4*>(row), make_float4((float)g[0], (float)g[1], (float)g[2], (float)g[3]));
+      atomicAdd(reinterpret_cast<float4*>(row + 4), make_float4((float)g[4], (float)g[5], (float)g[6], (float)g[7]));
+      atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2((float)g[8], (float)g[9]));
+    }
+    return;
+  }
   const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
   const int run_end = above ? (__ffs(above) - 2) : 31;
 #pragma unroll
@@ -1731,13 +1784,13 @@ __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
 // Transpose of the per-tet pre-pass for one step: from the adjoint of
 // (E0, W, B0, beta) to the adjoint of the carrier-restored DoFs eps, bet,
 // then through eps = c_re Re(e~) - c_im Im(e~) to dL/dRe + j dL/dIm of the
-// complex DoFs (FP64 atomics over the tets sharing an edge or face); tetgrad
-// is cleared for the next step.
+// complex DoFs (FP64 atomics over the tets sharing an edge or face); the
+// per-tet accumulators are cleared for the next step.
 __global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, int32_t mixed, const double* __restrict__ geom64,
                                                              const float4* __restrict__ rec, const int4* __restrict__ te,
                                                              const int4* __restrict__ tf, double cre, double cim,
-                                                             double* __restrict__ tetgrad, double* __restrict__ egrad,
-                                                             double* __restrict__ bgrad) {
+                                                             double* __restrict__ tetgrad, float* __restrict__ tetgrad32,
+                                                             double* __restrict__ egrad, double* __restrict__ bgrad) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double* tg = tetgrad + 10 * t;
@@ -1748,9 +1801,28 @@ __global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, int32_t 
     a[i] = tg[i];
     any = any || a[i] != 0.0;
   }
-  if (!any) return;
+  bool any32 = false;
+  if (mixed) {
+    float4* r4 = reinterpret_cast<float4*>(tetgrad32 + 12 * t);
+    const float4 u = r4[0], v = r4[1], w = r4[2];
+    const float f[10] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, w.x, w.y};
 #pragma unroll
-  for (int i = 0; i < 10; i++) tg[i] = 0.0;
+    for (int i = 0; i < 10; i++) {
+      a[i] += (double)f[i];
+      any32 = any32 || f[i] != 0.0f;
+    }
+    if (any32) {
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      r4[0] = z;
+      r4[1] = z;
+      r4[2] = z;
+    }
+  }
+  if (!any && !any32) return;
+  if (any) {
+#pragma unroll
+    for (int i = 0; i < 10; i++) tg[i] = 0.0;
+  }
   V3<double> g[4];
   if (mixed) {
     const float4 q = rec[8 * t + 1], r = rec[8 * t + 2], c = rec[8 * t + 3];
@@ -1872,6 +1944,7 @@ struct fempic_env {
   double qw_last[kMaxSpecies] = {0};
   int32_t ns_last = 0;
   double* tetgrad = nullptr;        // adjoint of the per-tet affine field [nt][10]
+  float* tetgrad32 = nullptr;       // mixed form: the same from per-lane atomics, [nt][12]
   CrossRec* xrec = nullptr;         // mixed form crossing queue [xtiles * 256]
   CrossRec64* xrec64 = nullptr;     // FP64 form crossing queue [xtiles * 256]
   int32_t* xcount = nullptr;        // [xtiles]
@@ -1932,7 +2005,7 @@ static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
-                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->xrec, e->xrec64, e->xcount,
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->xrec, e->xrec64, e->xcount,
                   e->dGe};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -2468,7 +2541,8 @@ extern "C" int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* cal
   return FEMPIC_OK;
 }
 
-extern "C" int fempic_sort(fempic_env* env, const fempic_particles* in, const fempic_particles* out, void* stream) {
+static int sort_impl(fempic_env* env, const fempic_particles* in, const fempic_particles* out, int32_t* perm,
+                     void* stream) {
   if (!env || !in || !out) return fail(FEMPIC_EINVAL, "sort: NULL argument");
   int rc = check_particles(in, true);
   if (rc) return rc;
@@ -2534,7 +2608,49 @@ extern "C" int fempic_sort(fempic_env* env, const fempic_particles* in, const fe
   A.oncross = out->n_cross;
   A.offsets = env->sort_offsets;
   A.cursor = env->sort_counts;
+  A.operm = perm;
   k_sort_scatter<<<blocks_for(in->n), kThreads, 0, st>>>(A);
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_sort(fempic_env* env, const fempic_particles* in, const fempic_particles* out, void* stream) {
+  return sort_impl(env, in, out, nullptr, stream);
+}
+
+extern "C" int fempic_sort_perm(fempic_env* env, const fempic_particles* in, const fempic_particles* out,
+                                int32_t* perm, void* stream) {
+  if (!perm) return fail(FEMPIC_EINVAL, "sort_perm: NULL permutation");
+  return sort_impl(env, in, out, perm, stream);
+}
+
+extern "C" int fempic_adjoint_unpermute(fempic_env* env, const fempic_adjoint* in, const fempic_adjoint* out,
+                                        const int32_t* perm, void* stream) {
+  if (!env || !in || !out || !perm) return fail(FEMPIC_EINVAL, "adjoint_unpermute: NULL argument");
+  if (in->n != out->n || in->n < 0) return fail(FEMPIC_EINVAL, "adjoint_unpermute: sizes differ");
+  if (in->n == 0) return FEMPIC_OK;
+  if (!in->rx || !in->ry || !in->rz || !in->vx || !in->vy || !in->vz || !out->rx || !out->ry || !out->rz ||
+      !out->vx || !out->vy || !out->vz)
+    return fail(FEMPIC_EINVAL, "adjoint_unpermute: NULL array");
+  if (in->rx == out->rx || in->vx == out->vx) return fail(FEMPIC_EINVAL, "adjoint_unpermute: in and out overlap");
+  if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "adjoint_unpermute: more than 2^31 particles");
+  AdjPermArgs A{};
+  A.n = in->n;
+  A.vbytes = env->opt.precision == FEMPIC_FP64 ? 8 : 4;
+  A.perm = perm;
+  A.rx = in->rx;
+  A.ry = in->ry;
+  A.rz = in->rz;
+  A.vx = in->vx;
+  A.vy = in->vy;
+  A.vz = in->vz;
+  A.ox = out->rx;
+  A.oy = out->ry;
+  A.oz = out->rz;
+  A.ovx = out->vx;
+  A.ovy = out->vy;
+  A.ovz = out->vz;
+  k_adjoint_unpermute<<<blocks_for(A.n), kThreads, 0, (cudaStream_t)stream>>>(A);
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
 }
@@ -2672,6 +2788,12 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
     FEMPIC_CUDA(dalloc(&env->tetgrad, 10 * nt));
     FEMPIC_CUDA(cudaMemsetAsync(env->tetgrad, 0, 10 * nt * sizeof(double), st));
   }
+  if (mixed && !env->tetgrad32) {
+    FEMPIC_CUDA(dalloc(&env->tetgrad32, 12 * nt));
+    FEMPIC_CUDA(cudaMemsetAsync(env->tetgrad32, 0, 12 * nt * sizeof(float), st));
+  }
+  LaunchTimer lt(env, st, FEMPIC_K_ADJOINT);
+  lt.kernels = 2;   // field, field adjoint (+ the particle adjoint below)
   // the per-tet affine field of this step (same carrier as the forward step)
   const double phi = omega0 * t;
   double cre = envl->amp * std::cos(phi), cim = envl->amp * std::sin(phi);
@@ -2719,14 +2841,17 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
     A.vby = adj->vy;
     A.vbz = adj->vz;
     A.tetgrad = env->tetgrad;
+    A.tetgrad32 = env->tetgrad32;
     if (mixed)
       k_push_adjoint<float><<<blocks_for(A.n), kThreads, 0, st>>>(A);
     else
       k_push_adjoint<double><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+    lt.kernels++;
     FEMPIC_CUDA(cudaGetLastError());
   }
   k_field_adjoint<<<blocks_for(nt), kThreads, 0, st>>>(nt, mixed ? 1 : 0, env->geom64, env->tetrec, env->te, env->tf,
-                                                        cre, cim, env->tetgrad, static_cast<double*>(e_grad),
+                                                        cre, cim, env->tetgrad, env->tetgrad32,
+                                                        static_cast<double*>(e_grad),
                                                         static_cast<double*>(b_grad));
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;

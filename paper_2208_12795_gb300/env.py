@@ -199,6 +199,12 @@ class FempicEnv:
         capi.fempic_sort(self.h, st.cstruct(), scratch.cstruct(), _stream(stream))
         st.swap(scratch)
 
+    def sort_perm(self, st: ParticleState, out: ParticleState, perm: torch.Tensor, stream=None):
+        """Sorted copy of `st` in `out`; perm[q] = index in `st` of out's particle q."""
+        if perm.dtype != torch.int32 or perm.numel() != st.n or not perm.is_cuda:
+            raise capi.FempicError("perm must be a device int32 tensor of length n")
+        capi.fempic_sort_perm(self.h, st.cstruct(), out.cstruct(), _ptr(perm), _stream(stream))
+
     def stats(self, stream=None) -> dict:
         out = np.zeros(4, np.int64)
         capi.fempic_stats(self.h, out.ctypes.data, _stream(stream))
@@ -216,5 +222,5 @@ class FempicEnv:
         calls = np.zeros(capi.FEMPIC_K_COUNT, np.int64)
         kern = np.zeros(capi.FEMPIC_K_COUNT, np.int64)
         capi.fempic_profile_read(self.h, ms.ctypes.data, calls.ctypes.data, kern.ctypes.data)
-        names = ("locate", "field", "push", "finalize", "charge", "sort", "cross")
+        names = ("locate", "field", "push", "finalize", "charge", "sort", "cross", "adjoint")
         return {nm: dict(ms=float(ms[i]), launches=int(calls[i]), kernels=int(kern[i])) for i, nm in enumerate(names)}
