@@ -1781,34 +1781,41 @@ __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
   }
 }
 
-// Transpose of the per-tet pre-pass for one step: from the adjoint of
-// (E0, W, B0, beta) to the adjoint of the carrier-restored DoFs eps, bet,
-// then through eps = c_re Re(e~) - c_im Im(e~) to dL/dRe + j dL/dIm of the
-// complex DoFs (FP64 atomics over the tets sharing an edge or face); the
-// per-tet accumulators are cleared for the next step.
-__global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, int32_t mixed, const double* __restrict__ geom64,
-                                                             const float4* __restrict__ rec, const int4* __restrict__ te,
-                                                             const int4* __restrict__ tf, double cre, double cim,
+// Transpose of the per-tet pre-pass for one step, first half: from the
+// adjoint of (E0, W, B0, beta) to the adjoint of the carrier-restored DoFs
+// eps (6 edges) and bet (4 faces) of each tet, written to tadj [nt][10]
+// (zeros for a tet without particles).  The mixed form does it in FP32 from
+// the FP32 tet record, the FP64 form in FP64.  The per-tet accumulators are
+// cleared for the next step.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, const double* __restrict__ geom64,
+                                                             const float4* __restrict__ rec,
                                                              double* __restrict__ tetgrad, float* __restrict__ tetgrad32,
-                                                             double* __restrict__ egrad, double* __restrict__ bgrad) {
+                                                             double* __restrict__ tadj) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
+  const bool mixed = sizeof(R) == 4;
   double* tg = tetgrad + 10 * t;
-  double a[10];
+  R a[10];
   bool any = false;
 #pragma unroll
   for (int i = 0; i < 10; i++) {
-    a[i] = tg[i];
-    any = any || a[i] != 0.0;
+    const double v = tg[i];
+    a[i] = (R)v;
+    any = any || v != 0.0;
   }
-  bool any32 = false;
+  if (any) {
+#pragma unroll
+    for (int i = 0; i < 10; i++) tg[i] = 0.0;
+  }
   if (mixed) {
     float4* r4 = reinterpret_cast<float4*>(tetgrad32 + 12 * t);
     const float4 u = r4[0], v = r4[1], w = r4[2];
     const float f[10] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, w.x, w.y};
+    bool any32 = false;
 #pragma unroll
     for (int i = 0; i < 10; i++) {
-      a[i] += (double)f[i];
+      a[i] += (R)f[i];
       any32 = any32 || f[i] != 0.0f;
     }
     if (any32) {
@@ -1817,55 +1824,80 @@ __global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, int32_t 
       r4[1] = z;
       r4[2] = z;
     }
+    any = any || any32;
   }
-  if (!any && !any32) return;
-  if (any) {
+  double* o = tadj + 10 * t;
+  if (!any) {
 #pragma unroll
-    for (int i = 0; i < 10; i++) tg[i] = 0.0;
+    for (int i = 0; i < 10; i++) o[i] = 0.0;
+    return;
   }
-  V3<double> g[4];
+  V3<R> g[4];
   if (mixed) {
     const float4 q = rec[8 * t + 1], r = rec[8 * t + 2], c = rec[8 * t + 3];
-    g[1] = {q.z, q.w, r.x};
-    g[2] = {r.y, r.z, r.w};
-    g[3] = {c.x, c.y, c.z};
-    // the forward pre-pass formed g_0 in FP32
-    g[0] = {(double)-((float)g[1].x + (float)g[2].x + (float)g[3].x),
-            (double)-((float)g[1].y + (float)g[2].y + (float)g[3].y),
-            (double)-((float)g[1].z + (float)g[2].z + (float)g[3].z)};
+    g[1] = {(R)q.z, (R)q.w, (R)r.x};
+    g[2] = {(R)r.y, (R)r.z, (R)r.w};
+    g[3] = {(R)c.x, (R)c.y, (R)c.z};
   } else {
     const double* G = geom64 + 12 * t;
-    g[1] = {G[3], G[4], G[5]};
-    g[2] = {G[6], G[7], G[8]};
-    g[3] = {G[9], G[10], G[11]};
-    g[0] = {-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z)};
+    g[1] = {(R)G[3], (R)G[4], (R)G[5]};
+    g[2] = {(R)G[6], (R)G[7], (R)G[8]};
+    g[3] = {(R)G[9], (R)G[10], (R)G[11]};
   }
-  const V3<double> E0b = {a[0], a[1], a[2]}, Wb = {a[3], a[4], a[5]}, B0b = {a[6], a[7], a[8]};
-  const double betab = a[9];
-  double epsb[6], betb[4];
+  // g_0 formed as in the forward pre-pass
+  g[0] = {-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z)};
+  const V3<R> E0b = {a[0], a[1], a[2]}, Wb = {a[3], a[4], a[5]}, B0b = {a[6], a[7], a[8]};
+  const R betab = a[9];
+  R epsb[6], betb[4];
 #pragma unroll
   for (int e = 0; e < 6; e++) epsb[e] = vdot(Wb, vcross(g[le1(e)], g[le0(e)]));
   epsb[0] += vdot(E0b, g[1]);
   epsb[1] += vdot(E0b, g[2]);
   epsb[2] += vdot(E0b, g[3]);
-  betb[0] = 0.0;
-  betb[1] = 2.0 * vdot(B0b, vcross(g[2], g[3]));
-  betb[2] = 2.0 * vdot(B0b, vcross(g[1], g[3]));
-  betb[3] = 2.0 * vdot(B0b, vcross(g[1], g[2]));
+  betb[0] = R(0);
+  betb[1] = R(2) * vdot(B0b, vcross(g[2], g[3]));
+  betb[2] = R(2) * vdot(B0b, vcross(g[1], g[3]));
+  betb[3] = R(2) * vdot(B0b, vcross(g[1], g[2]));
 #pragma unroll
-  for (int f = 0; f < 4; f++) betb[f] += 2.0 * betab * vdot(g[lf(f, 0)], vcross(g[lf(f, 1)], g[lf(f, 2)]));
-  const int4 e0 = te[2 * t], e1 = te[2 * t + 1], fi = tf[t];
-  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
-  const int32_t fid[4] = {fi.x, fi.y, fi.z, fi.w};
+  for (int f = 0; f < 4; f++) betb[f] += R(2) * betab * vdot(g[lf(f, 0)], vcross(g[lf(f, 1)], g[lf(f, 2)]));
 #pragma unroll
-  for (int e = 0; e < 6; e++) {
-    atomicAdd(egrad + 2 * (int64_t)eid[e], cre * epsb[e]);
-    atomicAdd(egrad + 2 * (int64_t)eid[e] + 1, -cim * epsb[e]);
+  for (int e = 0; e < 6; e++) o[e] = (double)epsb[e];
+#pragma unroll
+  for (int f = 0; f < 4; f++) o[6 + f] = (double)betb[f];
+}
+
+// Second half: each edge and each face gathers its tets' terms (adjacency
+// built once on the host: edge -> (tet, local edge), face -> (tet, local
+// face)) and adds dL/dRe + j dL/dIm through eps = c_re Re(e~) - c_im Im(e~):
+// one thread per edge or face, no atomics, a fixed summation order.
+__global__ void __launch_bounds__(kThreads) k_dof_grad(int64_t ne, int64_t nf, const int32_t* __restrict__ estart,
+                                                       const int32_t* __restrict__ eslot,
+                                                       const int32_t* __restrict__ fslot,
+                                                       const double* __restrict__ tadj, double cre, double cim,
+                                                       double* __restrict__ egrad, double* __restrict__ bgrad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < ne) {
+    double sum = 0.0;
+    for (int32_t j = estart[i]; j < estart[i + 1]; j++) {
+      const int32_t sl = eslot[j];
+      sum += tadj[(int64_t)(sl / 6) * 10 + sl % 6];
+    }
+    if (sum != 0.0) {
+      egrad[2 * i] += cre * sum;
+      egrad[2 * i + 1] += -cim * sum;
+    }
   }
+  if (i < nf) {
+    double sum = 0.0;
 #pragma unroll
-  for (int f = 0; f < 4; f++) {
-    atomicAdd(bgrad + 2 * (int64_t)fid[f], cre * betb[f]);
-    atomicAdd(bgrad + 2 * (int64_t)fid[f] + 1, -cim * betb[f]);
+    for (int k = 0; k < 2; k++) {
+      const int32_t sl = fslot[2 * i + k];
+      if (sl >= 0) sum += tadj[(int64_t)(sl >> 2) * 10 + 6 + (sl & 3)];
+    }
+    if (sum != 0.0) {
+      bgrad[2 * i] += cre * sum;
+      bgrad[2 * i + 1] += -cim * sum;
+    }
   }
 }
 
@@ -1945,6 +1977,10 @@ struct fempic_env {
   int32_t ns_last = 0;
   double* tetgrad = nullptr;        // adjoint of the per-tet affine field [nt][10]
   float* tetgrad32 = nullptr;       // mixed form: the same from per-lane atomics, [nt][12]
+  double* tadj = nullptr;           // per-tet DoF-adjoint terms of one adjoint step [nt][10]
+  int32_t* estart = nullptr;        // edge -> (tet, local edge) slots, CSR [ne + 1]
+  int32_t* eslot = nullptr;         // [6 nt], slot = 6 tet + local edge
+  int32_t* fslot = nullptr;         // face -> (tet, local face) slots [nf][2], 4 tet + local face or -1
   CrossRec* xrec = nullptr;         // mixed form crossing queue [xtiles * 256]
   CrossRec64* xrec64 = nullptr;     // FP64 form crossing queue [xtiles * 256]
   int32_t* xcount = nullptr;        // [xtiles]
@@ -2005,7 +2041,7 @@ static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
-                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->xrec, e->xrec64, e->xcount,
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->tadj, e->estart, e->eslot, e->fslot, e->xrec, e->xrec64, e->xcount,
                   e->dGe};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -2057,6 +2093,27 @@ static int upload(fempic_env* e) {
   FEMPIC_CUDA(cudaMemcpy(e->nb, nb.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->te, te.data(), 2 * nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->tf, tf.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
+  {
+    // adjacency of the adjoint's DoF-gradient gathers
+    std::vector<int32_t> estart(m.ne + 1, 0), eslot(6 * nt), fslot(2 * m.nf, -1);
+    for (int64_t i = 0; i < 6 * nt; i++) estart[m.te[i] + 1]++;
+    for (int64_t k = 0; k < m.ne; k++) estart[k + 1] += estart[k];
+    std::vector<int32_t> cur(estart.begin(), estart.end() - 1);
+    for (int64_t i = 0; i < 6 * nt; i++) eslot[cur[m.te[i]]++] = (int32_t)i;
+    for (int64_t i = 0; i < 4 * nt; i++) {
+      const int32_t f = m.tf[i];
+      if (fslot[2 * f] < 0)
+        fslot[2 * f] = (int32_t)i;
+      else
+        fslot[2 * f + 1] = (int32_t)i;
+    }
+    FEMPIC_CUDA(dalloc(&e->estart, m.ne + 1));
+    FEMPIC_CUDA(dalloc(&e->eslot, 6 * nt));
+    FEMPIC_CUDA(dalloc(&e->fslot, 2 * m.nf));
+    FEMPIC_CUDA(cudaMemcpy(e->estart, estart.data(), (m.ne + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    FEMPIC_CUDA(cudaMemcpy(e->eslot, eslot.data(), 6 * nt * sizeof(int32_t), cudaMemcpyHostToDevice));
+    FEMPIC_CUDA(cudaMemcpy(e->fslot, fslot.data(), 2 * m.nf * sizeof(int32_t), cudaMemcpyHostToDevice));
+  }
   if (e->opt.precision == FEMPIC_FP64) {
     FEMPIC_CUDA(dalloc(reinterpret_cast<double**>(&e->field), 10 * nt));
     FEMPIC_CUDA(dalloc(&e->dG, m.ne));
@@ -2849,10 +2906,18 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
     lt.kernels++;
     FEMPIC_CUDA(cudaGetLastError());
   }
-  k_field_adjoint<<<blocks_for(nt), kThreads, 0, st>>>(nt, mixed ? 1 : 0, env->geom64, env->tetrec, env->te, env->tf,
-                                                        cre, cim, env->tetgrad, env->tetgrad32,
-                                                        static_cast<double*>(e_grad),
-                                                        static_cast<double*>(b_grad));
+  if (!env->tadj) FEMPIC_CUDA(dalloc(&env->tadj, 10 * nt));
+  if (mixed)
+    k_field_adjoint<float><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->tetrec, env->tetgrad,
+                                                                env->tetgrad32, env->tadj);
+  else
+    k_field_adjoint<double><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->tetrec, env->tetgrad,
+                                                                 env->tetgrad32, env->tadj);
+  const int64_t ndof = std::max(env->h.ne, env->h.nf);
+  k_dof_grad<<<blocks_for(ndof), kThreads, 0, st>>>(env->h.ne, env->h.nf, env->estart, env->eslot, env->fslot,
+                                                     env->tadj, cre, cim, static_cast<double*>(e_grad),
+                                                     static_cast<double*>(b_grad));
+  lt.kernels++;
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
 }
