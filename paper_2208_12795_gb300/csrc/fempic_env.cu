@@ -1319,11 +1319,14 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t nt
 // ------------------------------------------------------- deposit finalize
 struct FinalizeArgs {
   int64_t ne;
+  int64_t nt;
+  const int32_t* estart;         // mixed form: edge -> (tet, local edge) slots
+  const int32_t* eslot;
   int32_t mixed;
   int32_t ns;
   double qwscale[kMaxSpecies];   // q w 2^-48 per species (mixed form)
   double* dG;
-  unsigned long long* dGe;       // mixed form: per-edge int64 sums [ns][ne] (from the slot flush)
+  const unsigned long long* dGq;  // mixed form: deposit slots [ns][nt][8]
   double* Gcum;
   double* dG_out;
   double* Gcum_out;
@@ -1331,42 +1334,27 @@ struct FinalizeArgs {
   double c, s;                   // cos, sin of omega0 t_next
 };
 
-// Mixed form, first half of the finalize: each (species, tet) slot of 6 local
-// edge sums is read coalesced, cleared, and added to its edges' int64 sums
-// (integer atomics: exact and independent of order).
-__global__ void __launch_bounds__(kThreads) k_slot_flush(int64_t nslots, int64_t nt, int64_t ne,
-                                                          unsigned long long* __restrict__ slots,
-                                                          const int4* __restrict__ te,
-                                                          unsigned long long* __restrict__ dGe) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nslots) return;
-  ulonglong2* sl = reinterpret_cast<ulonglong2*>(slots + 8 * i);
-  const ulonglong2 a = sl[0], b = sl[1], c = sl[2];
-  if ((a.x | a.y | b.x | b.y | c.x | c.y) == 0ull) return;
-  sl[0] = make_ulonglong2(0ull, 0ull);
-  sl[1] = make_ulonglong2(0ull, 0ull);
-  sl[2] = make_ulonglong2(0ull, 0ull);
-  const int64_t s = i / nt, t = i - s * nt;
-  const int4 e0 = te[2 * t], e1 = te[2 * t + 1];
-  unsigned long long* base = dGe + s * ne;
-  if (a.x) atomicAdd(base + e0.x, a.x);
-  if (a.y) atomicAdd(base + e0.y, a.y);
-  if (b.x) atomicAdd(base + e0.z, b.x);
-  if (b.y) atomicAdd(base + e0.w, b.y);
-  if (c.x) atomicAdd(base + e1.x, c.x);
-  if (c.y) atomicAdd(base + e1.y, c.y);
-}
-
+// Deposit finalize, one thread per edge.  Mixed form: the edge pulls its
+// exact int64 sums from the deposit slots of its tets (adjacency built once
+// on the host; integer sums, so the result does not depend on the order) and
+// scales them by q w 2^-48; the slots are cleared afterwards by one
+// coalesced memset.  FP64 form: the edge's FP64 accumulator.  Then G_cum +=
+// dG and the requested outputs (dG, G_cum, the envelope-frame G~).
 __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= A.ne) return;
   double d;
   if (A.mixed) {
     d = 0.0;
+    const int32_t j0 = A.estart[e], j1 = A.estart[e + 1];
     for (int s = 0; s < A.ns; s++) {
-      const long long q = (long long)A.dGe[(int64_t)s * A.ne + e];
+      long long q = 0;
+      const unsigned long long* sl = A.dGq + (int64_t)s * A.nt * 8;
+      for (int32_t j = j0; j < j1; j++) {
+        const int32_t k = A.eslot[j];
+        q += (long long)sl[(int64_t)(k / 6) * 8 + k % 6];
+      }
       d += A.qwscale[s] * (double)q;
-      A.dGe[(int64_t)s * A.ne + e] = 0ull;
     }
   } else {
     d = A.dG[e];
@@ -1968,7 +1956,6 @@ struct fempic_env {
   double* dG = nullptr;
   unsigned long long* dGq = nullptr;   // mixed form [dGq_species][nt][8]
   int32_t dGq_species = 0;
-  unsigned long long* dGe = nullptr;   // mixed form per-edge sums [dGq_species][ne]
   double* Gcum = nullptr;
   unsigned long long* stats = nullptr;
   int64_t* gstart = nullptr;
@@ -2042,7 +2029,7 @@ static void free_env(fempic_env* e) {
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
                   e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->tadj, e->estart, e->eslot, e->fslot, e->xrec, e->xrec64, e->xcount,
-                  e->dGe};
+                  nullptr};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete e;
@@ -2274,18 +2261,13 @@ static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
   // reallocates them, so a step must be finalized (fempic_deposit) before the
   // species table grows.
   unsigned long long* nq = nullptr;
-  unsigned long long* ne = nullptr;
   FEMPIC_CUDA(dalloc(&nq, (size_t)ns * env->h.nt * 8));
-  FEMPIC_CUDA(dalloc(&ne, (size_t)ns * env->h.ne));
   FEMPIC_CUDA(cudaMemsetAsync(nq, 0, (size_t)ns * env->h.nt * 8 * sizeof(unsigned long long), st));
-  FEMPIC_CUDA(cudaMemsetAsync(ne, 0, (size_t)ns * env->h.ne * sizeof(unsigned long long), st));
   if (env->dGq) {
     FEMPIC_CUDA(cudaStreamSynchronize(st));
     cudaFree(env->dGq);
-    cudaFree(env->dGe);
   }
   env->dGq = nq;
-  env->dGe = ne;
   env->dGq_species = ns;
   return FEMPIC_OK;
 }
@@ -2486,7 +2468,6 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
   A.ns = mixed ? (env->dGq ? env->ns_last : 0) : 0;
   for (int s = 0; s < kMaxSpecies; s++) A.qwscale[s] = env->qw_last[s] * 0x1p-48;
   A.dG = env->dG;
-  A.dGe = env->dGe;
   A.Gcum = env->Gcum;
   A.dG_out = dG_out;
   A.Gcum_out = G_cum_out;
@@ -2496,17 +2477,15 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
   A.s = std::sin(phi);
   {
     LaunchTimer lt(env, (cudaStream_t)stream, FEMPIC_K_FINALIZE);
-    if (mixed && env->dGq) {
-      const int64_t nslots = (int64_t)A.ns * env->h.nt;
-      if (nslots > 0)
-      {
-        k_slot_flush<<<blocks_for(nslots), kThreads, 0, (cudaStream_t)stream>>>(nslots, env->h.nt, env->h.ne, env->dGq,
-                                                                                env->te, env->dGe);
-        lt.kernels++;
-      }
-    }
+    A.nt = env->h.nt;
+    A.estart = env->estart;
+    A.eslot = env->eslot;
+    A.dGq = env->dGq;
     k_deposit_finalize<<<blocks_for(A.ne), kThreads, 0, (cudaStream_t)stream>>>(A);
     lt.kernels++;
+    if (mixed && env->dGq && A.ns > 0)
+      FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)A.ns * env->h.nt * 8 * sizeof(unsigned long long),
+                                  (cudaStream_t)stream));
   }
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
@@ -2520,7 +2499,6 @@ extern "C" int fempic_reset_deposit(fempic_env* env, void* stream) {
   if (env->dGq) {
     FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)env->dGq_species * env->h.nt * 8 * sizeof(unsigned long long),
                                 st));
-    FEMPIC_CUDA(cudaMemsetAsync(env->dGe, 0, (size_t)env->dGq_species * env->h.ne * sizeof(unsigned long long), st));
   }
   return FEMPIC_OK;
 }
