@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-particles", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--no-cpu-parallel", action="store_true", help="skip the all-cores oracle baseline")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient-window measurement")
     ap.add_argument("--no-levels3", action="store_true", help="skip the three-level envelope measurement")
     ap.add_argument("--workload", choices=("cube48", "jittered64", "large96"), default="cube48",
@@ -374,6 +375,8 @@ def run_ours(args):
     adj = None if (args.no_adjoint or args.workload != "cube48") else adjoint_window(rank)
     if rank == 0:
         cpu = None if (args.no_cpu or world > 1) else cpu_baseline(wl, args.cpu_particles, args.cpu_steps)
+        if cpu is not None and args.workload == "cube48" and not args.no_cpu_parallel:
+            cpu["all_cores"] = cpu_baseline_parallel(wl, 4 * args.cpu_particles, args.cpu_steps)
         report(args, world, n_p, out, cpu, adj)
     if world > 1:
         dist.barrier()
@@ -442,6 +445,58 @@ def cpu_baseline(wl, n_sample, steps):
     return {"value": n_sample * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"first {n_sample} of the 10M particles, {steps} steps, FP64 C oracle, 1 thread "
                       f"({el:.1f} s)"}
+
+
+_BARRIER = None
+
+
+def _init_worker(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_chunk(job):
+    """Worker of the parallel CPU baseline: the oracle as it stands on one
+    slice of the particles; all workers start their step loops together (a
+    barrier after the set-up); returns the wall-clock interval of the loop."""
+    nodes, tets, lo, hi, cols, sb, q, m, w, e, b, amps, omega0, dt = job
+    from oracle.oracle import OracleMesh, OracleState, push_step as oracle_push
+    from paper_2208_12795_gb300.inputs import Particles
+    om = OracleMesh(nodes, tets, lo, hi)
+    P = Particles(*cols, sb, q, m, w)
+    tet, _ = om.locate(P.x, P.y, P.z)
+    st = OracleState(P, tet)
+    G = np.zeros(om.n_edges)
+    _BARRIER.wait(timeout=900)
+    t0 = time.time()
+    for n, a in enumerate(amps):
+        oracle_push(om, st, e, b, a, omega0, n * dt, dt, G)
+    return t0, time.time()
+
+
+def cpu_baseline_parallel(wl, n_sample, steps):
+    """The FP64 oracle as it stands, one process per host core (spawned), each
+    on its slice of the first n_sample particles; the rate is all processes'
+    particle-steps over the wall-clock span of their step loops."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    P = wl.particles
+    amps = [wl.amp(n * wl.dt) for n in range(steps)]
+    bounds = np.linspace(0, n_sample, cores + 1).astype(np.int64)
+    jobs = []
+    for c in range(cores):
+        a, z = int(bounds[c]), int(bounds[c + 1])
+        cols = [np.ascontiguousarray(x[a:z]) for x in (P.x, P.y, P.z, P.vx, P.vy, P.vz)]
+        jobs.append((wl.mesh.nodes, wl.mesh.tets, wl.mesh.lo, wl.mesh.hi, cols, np.array([0, z - a], np.int64),
+                     P.q, P.m, P.w, wl.e_tilde, wl.b_tilde, amps, wl.omega0, wl.dt))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    with ctx.Pool(cores, initializer=_init_worker, initargs=(barrier,)) as pool:
+        spans = pool.map(_oracle_chunk, jobs, chunksize=1)
+    el = max(t1 for _, t1 in spans) - min(t0 for t0, _ in spans)
+    return {"value": n_sample * steps / el, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample} of the 10M particles in {cores} slices, {steps} steps, FP64 C oracle, "
+                      f"one spawned process per core ({el:.1f} s span of the step loops)"}
 
 
 def report(args, world, n_p, out, cpu, adj=None):
