@@ -586,34 +586,44 @@ __device__ __forceinline__ void cross64_finish(const PushArgs& A, const CrossSta
   ncr += (unsigned)c.nc;
 }
 
-// One warp per 256-particle tile region; lanes take the next record when
-// their particle is done (as in the mixed form's crossing pass).
+// One warp per group of tile regions (grid stride): the warp's tiles form one
+// record stream, and lanes take the next record, across tile boundaries,
+// when their particle is done.  The FP64 walk is FP64-pipe bound, so lanes
+// left idle at the end of a tile would cost pipe cycles (the latency-bound
+// mixed pass keeps the per-tile loop, which measured faster there).
 __global__ void __launch_bounds__(kThreads) k_cross_fp64(PushArgs A, int64_t ntiles) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   unsigned ncr = 0, nfrz = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
-    const int32_t cnt = A.xcount[t];
-    int32_t next = 0;
-    bool have = false;
-    CrossState64 c;
-    for (;;) {
-      const unsigned idle = __ballot_sync(full, !have);
-      if (next < cnt && idle) {
-        const int32_t idx = next + __popc(idle & lt);
-        if (!have && idx < cnt) {
-          cross64_begin(A, A.xrec64[t * kThreads + idx], c);
-          have = true;
-        }
-        next += __popc(idle);
+  int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int32_t cnt = tile < ntiles ? A.xcount[tile] : 0, next = 0;
+  bool have = false;
+  CrossState64 c;
+  for (;;) {
+    unsigned idle = __ballot_sync(full, !have);
+    while (idle && tile < ntiles) {   // warp-uniform: assigns records or advances a tile
+      const int32_t avail = cnt - next;
+      const int32_t want = __popc(idle);
+      const int32_t take = avail < want ? avail : want;
+      const int r = __popc(idle & lt);
+      if (!have && r < take) {
+        cross64_begin(A, A.xrec64[tile * kThreads + next + r], c);
+        have = true;
       }
-      if (!__any_sync(full, have)) break;
-      if (have && cross64_advance(A, c)) {
-        cross64_finish(A, c, ncr, nfrz);
-        have = false;
+      next += take;
+      idle = __ballot_sync(full, !have);
+      if (next == cnt) {
+        tile += warps;
+        cnt = tile < ntiles ? A.xcount[tile] : 0;
+        next = 0;
       }
+    }
+    if (!__any_sync(full, have)) break;
+    if (have && cross64_advance(A, c)) {
+      cross64_finish(A, c, ncr, nfrz);
+      have = false;
     }
   }
   ncr = __reduce_add_sync(full, ncr);
@@ -1187,6 +1197,8 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c) 
   if (c.nc > A.max_cross) {
     c.st = FEMPIC_P_CAP;
     c.moved = false;
+#pragma unroll
+    for (int j = 0; j < 4; j++) c.Qa[j] = Qp[j];   // where the deposited path ends
     return true;
   }
   const int4 nbv = __ldg(&A.nb[c.T]);
@@ -1232,6 +1244,8 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c) 
   } else {
     c.st = FEMPIC_P_ABSORBED;
     c.moved = false;
+#pragma unroll
+    for (int j = 0; j < 4; j++) c.Qa[j] = Qp[j];   // where the deposited path ends
     return true;
   }
   const Geo32 Gc = ld_geo(A.tetrec, c.T);
@@ -1252,9 +1266,20 @@ __device__ __forceinline__ void cross_finish(const PushArgs& A, const CrossState
     }
   } else {   // frozen at the last crossing point
     const double sd = (double)c.sacc;
-    A.x[p] = fma(sd, c.b[0] - c.a0[0], c.a0[0]);
-    A.y[p] = fma(sd, c.b[1] - c.a0[1], c.a0[1]);
-    A.z[p] = fma(sd, c.b[2] - c.a0[2], c.a0[2]);
+    const double r[3] = {fma(sd, c.b[0] - c.a0[0], c.a0[0]), fma(sd, c.b[1] - c.a0[1], c.a0[1]),
+                         fma(sd, c.b[2] - c.a0[2], c.a0[2])};
+    A.x[p] = r[0];
+    A.y[p] = r[1];
+    A.z[p] = r[2];
+    // The deposited path ended at the integer crossing point c.Qa, while the
+    // particle's charge is assigned from its stored FP64 position; deposit the
+    // tiny piece between the two, so that the edge divergence still equals
+    // the change of the nodal charge exactly.
+    int32_t Qf[4];
+    bary_q_at(A.tetrec, c.T, r, Qf);
+    long long g[6];
+    gq(c.Qa, Qf, g);
+    depositq_atomic(A, c.T, c.s, g);
   }
   if (c.reflected) {
     static_cast<float*>(A.vx)[p] = c.vn[0];
@@ -1567,11 +1592,11 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_unpermute(AdjPermArgs A) {
 // the sign of each velocity component after the step, and propagates the
 // adjoint (rbar, vbar) of the state after the step back to the state before
 // it.  The adjoint of the per-tet affine field (E0, W, B0, beta) is reduced
-// over runs of equal tets in each warp and added to tetgrad in FP64; in the
-// mixed form a warp whose particles fall into more than 4 runs (the state
-// drifts out of tet order between sorts, and the gradient window does not
-// sort) adds each lane's 10 values straight into an FP32 row per tet with
-// vector atomics instead.  The transposed pre-pass k_field_adjoint maps both
+// over runs of equal tets in each warp and added per tet: in FP64 (FP64
+// form) or into an FP32 row with vector atomics (mixed form, no FP64-pipe
+// work); in the mixed form a warp whose particles fall into more than 4 runs
+// (the order has drifted since the last sort) skips the reduction and adds
+// each lane's 10 values straight into the row.  The transposed pre-pass k_field_adjoint maps both
 // to the complex DoFs.  A
 // particle frozen during the step gets a zero adjoint (its later state no
 // longer depends on its earlier one through the step map).
@@ -1762,10 +1787,17 @@ __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
     }
   }
   if (head && key >= 0) {
-    double* tg = A.tetgrad + 10 * (int64_t)key;
+    if (sizeof(R) == 4) {   // mixed form: the run's sums into the tet's FP32 row
+      float* row = A.tetgrad32 + 12 * (int64_t)key;
+      atomicAdd(reinterpret_cast<float4*>(row), make_float4((float)g[0], (float)g[1], (float)g[2], (float)g[3]));
+      atomicAdd(reinterpret_cast<float4*>(row + 4), make_float4((float)g[4], (float)g[5], (float)g[6], (float)g[7]));
+      atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2((float)g[8], (float)g[9]));
+    } else {
+      double* tg = A.tetgrad + 10 * (int64_t)key;
 #pragma unroll
-    for (int i = 0; i < 10; i++)
-      if (g[i] != R(0)) atomicAdd(tg + i, (double)g[i]);
+      for (int i = 0; i < 10; i++)
+        if (g[i] != R(0)) atomicAdd(tg + i, (double)g[i]);
+    }
   }
 }
 
@@ -1783,18 +1815,23 @@ __global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, const do
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const bool mixed = sizeof(R) == 4;
-  double* tg = tetgrad + 10 * t;
   R a[10];
   bool any = false;
+  if (!mixed) {
+    double* tg = tetgrad + 10 * t;
 #pragma unroll
-  for (int i = 0; i < 10; i++) {
-    const double v = tg[i];
-    a[i] = (R)v;
-    any = any || v != 0.0;
-  }
-  if (any) {
+    for (int i = 0; i < 10; i++) {
+      const double v = tg[i];
+      a[i] = (R)v;
+      any = any || v != 0.0;
+    }
+    if (any) {
 #pragma unroll
-    for (int i = 0; i < 10; i++) tg[i] = 0.0;
+      for (int i = 0; i < 10; i++) tg[i] = 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 10; i++) a[i] = R(0);
   }
   if (mixed) {
     float4* r4 = reinterpret_cast<float4*>(tetgrad32 + 12 * t);
@@ -1849,9 +1886,9 @@ __global__ void __launch_bounds__(kThreads) k_field_adjoint(int64_t nt, const do
 #pragma unroll
   for (int f = 0; f < 4; f++) betb[f] += R(2) * betab * vdot(g[lf(f, 0)], vcross(g[lf(f, 1)], g[lf(f, 2)]));
 #pragma unroll
-  for (int e = 0; e < 6; e++) o[e] = (double)epsb[e];
+  for (int e = 0; e < 6; e++) o[e] = widen(epsb[e]);
 #pragma unroll
-  for (int f = 0; f < 4; f++) o[6 + f] = (double)betb[f];
+  for (int f = 0; f < 4; f++) o[6 + f] = widen(betb[f]);
 }
 
 // Second half: each edge and each face gathers its tets' terms (adjacency
