@@ -99,10 +99,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n_p):
-    """DRAM bytes per launch of the mixed push kernel from the committed ncu
-    summary, scaled to n_p particles; None when absent or when the kernel
-    source changed since the capture."""
+def _profile_value(key):
+    """A per-particle figure from the committed ncu summary; None when absent
+    or when the kernel source changed since the capture."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     kv = {}
@@ -113,9 +112,33 @@ def profiled_traffic(n_p):
     try:
         if kv.get("kernel_source_sha") != kernel_source_hash():
             return None
-        return float(kv["dram_bytes_per_particle"]) * n_p
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic(n_p):
+    """DRAM bytes per launch of the mixed push group, scaled to n_p particles."""
+    v = _profile_value("dram_bytes_per_particle")
+    return None if v is None else v * n_p
+
+
+def issue_roofline(n_p, t_launch_s, sm_mhz):
+    """Issue-slot roofline of the staged common path k_push_mixed_tma: its
+    warp instructions per launch (ncu count per particle, scaled to n_p) over
+    the launch time, against 4 warp instructions per clock on each of the
+    GPU's SMs at the sampled SM clock."""
+    ipp = _profile_value("tma_warp_instructions_per_particle")
+    if ipp is None or t_launch_s <= 0:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 4 * sm_mhz * 1e6
+    achieved = ipp * n_p / t_launch_s
+    return {"kernel": "k_push_mixed_tma", "bound": "issue", "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak, "warp_instructions_per_launch": ipp * n_p,
+            "avg_launch_ms": t_launch_s * 1e3,
+            "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz (median SM clock sampled in the timed region)"}
 
 
 class ClockSampler:
@@ -547,6 +570,9 @@ def report(args, world, n_p, out, cpu, adj=None):
         },
         "e2e": {"value": total / m["e2e_s"], "unit": "particle-steps/s",
                 "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]},
+        "roofline_issue": issue_roofline(
+            n_p, (push["ms"] - m["prof"]["cross"]["ms"]) / max(push["launches"], 1) / 1e3,
+            float(m["clocks"].get("sm_mhz") or 2070.0)),
         "gpu_launches": launches,
         "kernel_ms": {k: v["ms"] for k, v in m["prof"].items() if v["launches"]},
         "kernel_ms_note": "summed CUDA-event time over the timed steps per library call; 'cross' "
