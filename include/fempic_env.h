@@ -198,6 +198,14 @@ int fempic_lagrange3(const double* tau, double t, double* w_out);
 int fempic_deposit(fempic_env* env, double omega0, double t_next, double* dG_out, double* G_cum_out,
                    void* G_env_out, void* stream);
 
+/* Switch the deposit (f) of later push steps on (enable != 0, the default)
+ * or off.  Off, a step still gathers, pushes and tracks every particle
+ * exactly as with the deposit on, but adds nothing to dG: for callers that
+ * need only the trajectories, such as the gradient of a loss that does not
+ * depend on the deposited charge (the paper's method always deposits; this
+ * switch has no counterpart there).  Host only.  Errors: EINVAL. */
+int fempic_set_deposit(fempic_env* env, int32_t enable);
+
 /* Zero dG and G_cum (start of a run).  Errors: ECUDA. */
 int fempic_reset_deposit(fempic_env* env, void* stream);
 

@@ -12,7 +12,9 @@ Each checkpoint is taken after sorting the state by (species, tet)
 (`fempic_sort_perm`), so the steps of every segment run on tet-ordered
 particles; the reverse sweep carries the adjoint back across each of those
 sorts with `fempic_adjoint_unpermute`.  The gradient is returned in the
-particle order of the initial state.
+particle order of the initial state.  The window's steps run with the
+deposit off (`fempic_set_deposit`): the loss does not depend on the
+deposited charge, and the env's accumulated deposit is left untouched.
 
 The derivative is that of the piecewise smooth map for the tet sequence the
 forward run took (a particle that crosses a face keeps the crossing; a
@@ -84,10 +86,26 @@ class Schedule:
     t0: float = 0.0
 
 
+class _DepositOff:
+    """The loss does not depend on the deposited charge, so the window's
+    steps run with the deposit off (same trajectories, no dG work); the
+    env's accumulated deposit is left as it was."""
+
+    def __init__(self, env: FempicEnv):
+        self.env = env
+
+    def __enter__(self):
+        self.prev = self.env.deposit_on
+        self.env.set_deposit(False)
+
+    def __exit__(self, *exc):
+        self.env.set_deposit(self.prev)
+        return False
+
+
 def _step(env, st, e, b, sch: Schedule, k: int):
     t = sch.t0 + k * sch.dt
     env.push_step(st, e, b, sch.amp(t), sch.omega0, t, sch.dt)
-    env.reset_deposit()
 
 
 class Checkpoint:
@@ -104,17 +122,18 @@ def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule
     checkpoint (the final state is in the last checkpoint's order)."""
     st = st0 if (sort and sch.steps > 0) else clone_state(st0)
     ckpts = []
-    for k in range(sch.steps):
-        if k % sch.every == 0:
-            if sort:
-                srt = st.empty_like()
-                perm = torch.empty(st.n, dtype=torch.int32, device=st.x.device)
-                env.sort_perm(st, srt, perm)
-                ckpts.append(Checkpoint(srt, perm))
-                st = clone_state(srt)
-            else:
-                ckpts.append(Checkpoint(clone_state(st), None))
-        _step(env, st, e, b, sch, k)
+    with _DepositOff(env):
+        for k in range(sch.steps):
+            if k % sch.every == 0:
+                if sort:
+                    srt = st.empty_like()
+                    perm = torch.empty(st.n, dtype=torch.int32, device=st.x.device)
+                    env.sort_perm(st, srt, perm)
+                    ckpts.append(Checkpoint(srt, perm))
+                    st = clone_state(srt)
+                else:
+                    ckpts.append(Checkpoint(clone_state(st), None))
+            _step(env, st, e, b, sch, k)
     return st, ckpts
 
 
@@ -130,9 +149,10 @@ def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState)
         k1 = min(sch.steps, k0 + sch.every)
         stash = [ckpts[s].st]
         cur = clone_state(ckpts[s].st)
-        for k in range(k0, k1):
-            _step(env, cur, e, b, sch, k)
-            stash.append(clone_state(cur))
+        with _DepositOff(env):
+            for k in range(k0, k1):
+                _step(env, cur, e, b, sch, k)
+                stash.append(clone_state(cur))
         for k in range(k1 - 1, k0 - 1, -1):
             j = k - k0
             t = sch.t0 + k * sch.dt

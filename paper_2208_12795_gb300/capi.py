@@ -27,7 +27,7 @@ FEMPIC_WALL_ABSORB = 1
 # Every function declared in include/fempic_env.h.
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step", "fempic_push_step3",
            "fempic_lagrange3",
-           "fempic_deposit", "fempic_reset_deposit", "fempic_nodal_charge", "fempic_stats",
+           "fempic_deposit", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
            "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
            "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
 FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS, \
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         lib.fempic_deposit.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]
         lib.fempic_reset_deposit.argtypes = [C.c_void_p, C.c_void_p]
+        lib.fempic_set_deposit.argtypes = [C.c_void_p, C.c_int32]
         lib.fempic_nodal_charge.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p, C.c_void_p]
         lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_push_step_adjoint.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles),
@@ -161,6 +162,10 @@ def fempic_lagrange3(tau, t) -> tuple:
     w = (C.c_double * 3)()
     check(load().fempic_lagrange3(tau_c, float(t), w), "fempic_lagrange3")
     return tuple(w)
+
+
+def fempic_set_deposit(env, enable: bool):
+    check(load().fempic_set_deposit(env, 1 if enable else 0), "fempic_set_deposit")
 
 
 def fempic_deposit(env, omega0, t_next, dG_out=0, G_cum_out=0, G_env_out=0, stream=0):

@@ -345,6 +345,7 @@ __device__ __forceinline__ bool negative_bits(double r) {   // r < 0 for finite 
 
 __device__ __forceinline__ void deposit64(const PushArgs& A, int32_t T, const double la[4], const double lb[4],
                                           double qw) {
+  if (!A.dG) return;   // deposits off
   const int4 e0 = __ldg(&A.te[2 * (int64_t)T]), e1 = __ldg(&A.te[2 * (int64_t)T + 1]);
   const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
 #pragma unroll
@@ -740,6 +741,7 @@ __device__ __forceinline__ unsigned long long* tet_slot(const PushArgs& A, int s
 }
 
 __device__ __forceinline__ void depositq_atomic(const PushArgs& A, int32_t T, int s, const long long g[6]) {
+  if (!A.dGq) return;   // deposits off
   unsigned long long* base = tet_slot(A, s, T);
 #pragma unroll
   for (int e = 0; e < 6; e++)
@@ -928,24 +930,26 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
       r.p = (int32_t)p;
     }
   }
-  const int32_t prev = __shfl_up_sync(full, o.key, 1);
-  const bool head = lane == 0 || prev != o.key;
-  const unsigned heads = __ballot_sync(full, head);
-  const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
-  const int run_end = above ? (__ffs(above) - 2) : 31;
+  if (A.dGq) {   // deposits on (kernel parameter: the same branch for every lane)
+    const int32_t prev = __shfl_up_sync(full, o.key, 1);
+    const bool head = lane == 0 || prev != o.key;
+    const unsigned heads = __ballot_sync(full, head);
+    const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
+    const int run_end = above ? (__ffs(above) - 2) : 31;
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
+    for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
-    for (int e = 0; e < 6; e++) {
-      const long long v = __shfl_down_sync(full, o.gh[e], off);
-      if (lane + off <= run_end) o.gh[e] += v;
+      for (int e = 0; e < 6; e++) {
+        const long long v = __shfl_down_sync(full, o.gh[e], off);
+        if (lane + off <= run_end) o.gh[e] += v;
+      }
     }
-  }
-  if (head && o.key >= 0) {
-    unsigned long long* base = tet_slot(A, o.shome, o.Thome);
+    if (head && o.key >= 0) {
+      unsigned long long* base = tet_slot(A, o.shome, o.Thome);
 #pragma unroll
-    for (int e = 0; e < 6; e++)
-      if (o.gh[e]) atomicAdd(base + e, (unsigned long long)o.gh[e]);
+      for (int e = 0; e < 6; e++)
+        if (o.gh[e]) atomicAdd(base + e, (unsigned long long)o.gh[e]);
+    }
   }
   const unsigned nf = __reduce_add_sync(full, o.nfrz);
   if (lane == 0 && nf) atomicAdd(A.stats + 1, (unsigned long long)nf);
@@ -2020,6 +2024,7 @@ struct fempic_env {
   };
   int32_t* sort_counts = nullptr;   // [sort_cap] per-key counters, then cursors
   int32_t* sort_offsets = nullptr;  // [sort_cap]
+  bool deposit_on = true;           // fempic_set_deposit
   int32_t* sort_sums = nullptr;     // [sort_cap / 2048 + 1]
   int64_t sort_cap = 0;
   bool profiling = false;
@@ -2402,8 +2407,8 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
   A.nb = env->nb;
   A.te = env->te;
   A.field = env->field;
-  A.dG = env->dG;
-  A.dGq = env->dGq;
+  A.dG = env->deposit_on ? env->dG : nullptr;
+  A.dGq = env->deposit_on ? env->dGq : nullptr;
   A.stats = env->stats;
   rc = ensure_xqueue(env, p->n, st);
   if (rc) return rc;
@@ -2525,6 +2530,12 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
                                   (cudaStream_t)stream));
   }
   FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_set_deposit(fempic_env* env, int32_t enable) {
+  if (!env) return fail(FEMPIC_EINVAL, "set_deposit: NULL env");
+  env->deposit_on = enable != 0;
   return FEMPIC_OK;
 }
 

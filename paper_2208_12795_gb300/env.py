@@ -185,6 +185,15 @@ class FempicEnv:
         capi.fempic_deposit(self.h, omega0, t_next, _ptr(dG_out), _ptr(G_cum_out), _ptr(G_env_out),
                             _stream(stream))
 
+    @property
+    def deposit_on(self) -> bool:
+        return getattr(self, "_deposit_on", True)
+
+    def set_deposit(self, enable: bool):
+        """Deposit on (default) or off for later push steps (tracking unchanged)."""
+        capi.fempic_set_deposit(self.h, enable)
+        self._deposit_on = bool(enable)
+
     def reset_deposit(self, stream=None):
         capi.fempic_reset_deposit(self.h, _stream(stream))
 

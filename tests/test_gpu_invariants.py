@@ -101,3 +101,37 @@ def test_reflecting_walls_keep_every_particle_inside(prec):
     lam = _bary(wl.mesh.nodes, tn, g["tet"], r)
     assert lam.min() >= -1e-5
     assert res <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_deposit_off_leaves_trajectories_unchanged_and_adds_nothing(prec):
+    """fempic_set_deposit(0): the same particle states, bit for bit, and no
+    deposit; switching back on deposits again."""
+    from paper_2208_12795_gb300.env import FempicEnv, ParticleState
+    wl = I.workload_hot_small(jitter=0.2, n_particles=2000)
+    res = []
+    for on in (True, False):
+        env = FempicEnv.from_mesh(wl.mesh, precision=prec)
+        st = ParticleState.from_host(wl.particles, prec)
+        env.locate(st)
+        e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+        b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+        env.set_deposit(on)
+        G = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+        for n in range(6):
+            t = n * wl.dt
+            env.push_step(st, e, b, wl.amp(t), wl.omega0, t, wl.dt)
+            env.deposit(wl.omega0, t + wl.dt, G_cum_out=G)
+        torch.cuda.synchronize()
+        res.append((st.to_numpy(), G.cpu().numpy()))
+        if not on:
+            env.set_deposit(True)
+            env.push_step(st, e, b, wl.amp(0.0), wl.omega0, 6 * wl.dt, wl.dt)
+            env.deposit(wl.omega0, 7 * wl.dt, G_cum_out=G)
+            torch.cuda.synchronize()
+            assert np.abs(G.cpu().numpy()).max() > 0
+    (a, Ga), (b_, Gb) = res
+    for k in a:
+        if a[k] is not None:
+            assert np.array_equal(a[k], b_[k]), k
+    assert np.abs(Ga).max() > 0 and not Gb.any()
