@@ -74,7 +74,7 @@ def test_adjoint_matches_oracle_jvp(prec, tol, maker, K, every):
     env, st0, e, b, sch, L, eg, bg, adj = _gpu_grad(wl, P, prec, K, every)
     tet0 = st0.tet.cpu().numpy()
     rng = np.random.default_rng(77)
-    for trial in range(3):
+    for trial in range(8):
         de, db, tr, tv = _directions(rng, wl, P.n, env.n_edges, env.n_faces)
         jv, ost = _oracle_jvp(wl, P, tet0, K, de, db, tr, tv)
         g = A.grad_dot(eg, bg, adj, de, db, tr, tv)
@@ -83,17 +83,19 @@ def test_adjoint_matches_oracle_jvp(prec, tol, maker, K, every):
 
 
 def test_adjoint_matches_central_differences_fp64():
-    """GPU FP64 gradient vs central differences of the GPU FP64 forward run."""
+    """GPU FP64 gradient vs central differences of the GPU FP64 forward run on
+    64 random directions of (e~, b~, r0, v0).  The derivative is that of the
+    map for a fixed tet sequence: a direction whose +h and -h runs take
+    different sequences is retried with h/10 and, if they still differ,
+    left out and counted (at most 2 of 64 allowed)."""
     A, FempicEnv, ParticleState = _mods()
     wl = I.workload_small()
     P = wl.particles.subset(500)
     K, every = 30, 7
     env, st0, e, b, sch, L, eg, bg, adj = _gpu_grad(wl, P, FP64, K, every)
     rng = np.random.default_rng(5)
-    h = 1e-6
-    for trial in range(4):
-        de, db, tr, tv = _directions(rng, wl, P.n, env.n_edges, env.n_faces)
-        g = A.grad_dot(eg, bg, adj, de, db, tr, tv)
+
+    def run(h, de, db, tr, tv):
         vals, seqs = [], []
         for sgn in (1, -1):
             Pp = I.Particles(P.x + sgn * h * tr[:, 0], P.y + sgn * h * tr[:, 1], P.z + sgn * h * tr[:, 2],
@@ -105,14 +107,26 @@ def test_adjoint_matches_central_differences_fp64():
             bp = torch.from_numpy(wl.b_tilde + sgn * h * db).cuda()
             final, _ = A.forward_checkpointed(env, st, ep, bp, sch)
             vals.append(float(A.kinetic_energy(env, final).item()))
-            seqs.append((final.tet.cpu().numpy(), final.n_cross.cpu().numpy()))
-        # same tet sequence on both sides (the checkpoint sorts may order particles of
-        # one tet differently, so compare the sorted (tet, crossings) pairs)
-        pa, pb = (np.sort(sq[0].astype(np.int64) * 2 ** 32 + sq[1]) for sq in seqs)
-        assert np.array_equal(pa, pb)
-        fd = (vals[0] - vals[1]) / (2 * h)
-        print(f"\n[adjoint vs FD] <g,d> {g:.10e} fd {fd:.10e} rel {abs(g - fd) / abs(fd):.2e}")
-        assert abs(g - fd) <= 1e-5 * abs(fd)
+            # the checkpoint sorts may order particles of one tet differently:
+            # compare the sorted (tet, crossings) pairs
+            seqs.append(np.sort(final.tet.cpu().numpy().astype(np.int64) * 2 ** 32 + final.n_cross.cpu().numpy()))
+        return (vals[0] - vals[1]) / (2 * h), np.array_equal(seqs[0], seqs[1])
+
+    excluded, worst = 0, 0.0
+    for trial in range(64):
+        de, db, tr, tv = _directions(rng, wl, P.n, env.n_edges, env.n_faces)
+        g = A.grad_dot(eg, bg, adj, de, db, tr, tv)
+        fd, same = run(1e-6, de, db, tr, tv)
+        if not same:
+            fd, same = run(1e-7, de, db, tr, tv)
+        if not same:
+            excluded += 1
+            continue
+        rel = abs(g - fd) / abs(fd)
+        worst = max(worst, rel)
+        assert rel <= 1e-5, (trial, g, fd)
+    print(f"\n[adjoint vs FD, 64 directions] worst rel {worst:.2e}, excluded {excluded}")
+    assert excluded <= 2
 
 
 def test_autograd_function_matches_driver():
