@@ -491,3 +491,33 @@ def test_kinetic_energy_closed_form():
     P = _single(np.array([0.5, 0.5, 0.5]), np.array([3.0, 4.0, 12.0]), mass=2.0, w=5.0)
     st = OracleState(P, np.array([0], np.int32))
     assert kinetic_energy(st) == 0.5 * 2.0 * 5.0 * 169.0
+
+
+def test_te101_gather_converges_at_first_order():
+    """Whitney-1/2 interpolation of the TE101 mode (de Rham DoFs) reproduces
+    E = E0 sin(pi x) sin(pi z) y^ and B = (j/omega0) curl E with an error
+    that halves with h (first order): RMS error over random points on Kuhn
+    meshes of 8^3, 16^3 and 32^3 hexes."""
+    E0 = 1e3
+    om0 = I.te101_omega0()
+    errs_e, errs_b = [], []
+    for n in (8, 16, 32):
+        m = I.kuhn_cube_mesh(n)
+        om = OracleMesh(m.nodes, m.tets)
+        tb = om.tables()
+        e_dof, b_dof = I.te101_dofs(m.nodes, tb["edge_nodes"], tb["face_nodes"], E0, om0)
+        rng = np.random.default_rng(100 + n)
+        se, sb = [], []
+        for t in rng.choice(om.n_tets, 400, replace=False):
+            r, _ = _rand_point_in_tet(rng, m.nodes[tb["tet_nodes"][t]])
+            Et, Bt = om.gather(t, r, e_dof, b_dof)
+            x, _, z = r
+            E = np.array([0.0, E0 * math.sin(math.pi * x) * math.sin(math.pi * z), 0.0])
+            B = (1j / om0) * E0 * math.pi * np.array([-math.sin(math.pi * x) * math.cos(math.pi * z), 0.0,
+                                                      math.cos(math.pi * x) * math.sin(math.pi * z)])
+            se.append(np.sum(np.abs(Et - E) ** 2) / E0 ** 2)
+            sb.append(np.sum(np.abs(Bt - B) ** 2) / (E0 * math.pi / om0) ** 2)
+        errs_e.append(math.sqrt(np.mean(se)))
+        errs_b.append(math.sqrt(np.mean(sb)))
+    for errs in (errs_e, errs_b):
+        assert 1.7 <= errs[0] / errs[1] <= 2.5 and 1.7 <= errs[1] / errs[2] <= 2.5, errs
