@@ -1205,7 +1205,12 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c) 
     for (int j = 0; j < 4; j++) c.Qa[j] = Qp[j];   // where the deposited path ends
     return true;
   }
-  const int4 nbv = __ldg(&A.nb[c.T]);
+  // neighbour ids from the last 16 B of the tet's record, whose line the
+  // walk has just read for the geometry (one round trip less than the
+  // separate neighbour table)
+  const float4 nbf = __ldg(A.tetrec + 8 * (int64_t)c.T + 7);
+  const int4 nbv = make_int4(__float_as_int(nbf.x), __float_as_int(nbf.y), __float_as_int(nbf.z),
+                             __float_as_int(nbf.w));
   const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
   if (nbt >= 0) {
     const int4 o4 = __ldg(&A.tn[c.T]), n4 = __ldg(&A.tn[nbt]);
