@@ -1151,8 +1151,8 @@ struct CrossState {
   bool moved, reflected;
 };
 
-// Start from the record: rebuild b bit for bit (the common path's sequence)
-// and the integer barycentrics of both ends in the home tet.
+// Start from the record: rebuild b bit for bit (the common path's sequence).
+// The barycentrics follow in the first step (cross_advance with fresh).
 __device__ __forceinline__ void cross_begin(const PushArgs& A, const CrossRec& r, CrossState& c) {
   c.p = r.p;
   c.T = r.T;
@@ -1165,13 +1165,6 @@ __device__ __forceinline__ void cross_begin(const PushArgs& A, const CrossRec& r
     c.b[k] = advance(r.a[k], dt32, r.v[k]);
     c.bs[k] = split_f64(c.b[k]);
   }
-  const Geo32 G = ld_geo(A.tetrec, c.T);
-  const FF rs[3] = {split_f64(c.a0[0]), split_f64(c.a0[1]), split_f64(c.a0[2])};
-  float dx, dy, dz;
-  dpos32(G, rs, dx, dy, dz);
-  bary_q(G, dx, dy, dz, c.Qa);
-  dpos32(G, c.bs, dx, dy, dz);
-  bary_q(G, dx, dy, dz, c.Qb);
   c.entry = -1;
   c.nc = 0;
   c.sacc = 0.f;
@@ -1183,7 +1176,21 @@ __device__ __forceinline__ void cross_begin(const PushArgs& A, const CrossRec& r
 // Deposit the current piece up to its exit face (or to b) and move on: into
 // the neighbour, back from a reflecting wall, or stop (absorbed, capped).
 // Returns true when the particle's step is complete.
-__device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c) {
+__device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c, bool fresh) {
+  {
+    // the current tet's record and the end point's barycentrics in it; a
+    // fresh particle also needs its start point's (every busy lane runs this
+    // body together, only the start point is particular to fresh lanes)
+    const Geo32 G = ld_geo(A.tetrec, c.T);
+    float dx, dy, dz;
+    if (fresh) {
+      const FF rs[3] = {split_f64(c.a0[0]), split_f64(c.a0[1]), split_f64(c.a0[2])};
+      dpos32(G, rs, dx, dy, dz);
+      bary_q(G, dx, dy, dz, c.Qa);
+    }
+    dpos32(G, c.bs, dx, dy, dz);
+    bary_q(G, dx, dy, dz, c.Qb);
+  }
   float smin;
   const int kx = exit_face(c.Qa, c.Qb, c.entry, smin);
   long long g[6];
@@ -1257,11 +1264,7 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c) 
     for (int j = 0; j < 4; j++) c.Qa[j] = Qp[j];   // where the deposited path ends
     return true;
   }
-  const Geo32 Gc = ld_geo(A.tetrec, c.T);
-  float ex, ey, ez;
-  dpos32(Gc, c.bs, ex, ey, ez);
-  bary_q(Gc, ex, ey, ez, c.Qb);
-  return false;
+  return false;   // the next call reads the new tet and the end point's barycentrics in it
 }
 
 // Final state of a finished walk.
@@ -1323,7 +1326,7 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t nt
   for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
     const int32_t cnt = A.xcount[t];
     int32_t next = 0;
-    bool have = false;
+    bool have = false, fresh = false;
     CrossState c;
     for (;;) {
       const unsigned idle = __ballot_sync(full, !have);
@@ -1332,13 +1335,18 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t nt
         if (!have && idx < cnt) {
           cross_begin(A, A.xrec[t * kThreads + idx], c);
           have = true;
+          fresh = true;
         }
         next += __popc(idle);
       }
       if (!__any_sync(full, have)) break;
-      if (have && cross_advance(A, c)) {
-        cross_finish(A, c, ncr, nfrz);
-        have = false;
+      if (have) {
+        const bool done = cross_advance(A, c, fresh);
+        fresh = false;
+        if (done) {
+          cross_finish(A, c, ncr, nfrz);
+          have = false;
+        }
       }
     }
   }
