@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_field_f32(int64_t nt, float4* __re
   field_coeffs<float, float2, NL>(g, L, eid, fid, out);
   rec[8 * t + 4] = make_float4(out[0], out[1], out[2], out[3]);
   rec[8 * t + 5] = make_float4(out[4], out[5], out[6], out[7]);
-  rec[8 * t + 6] = make_float4(out[8], out[9], 0.f, 0.f);
+  reinterpret_cast<float2*>(rec + 8 * t + 6)[0] = make_float2(out[8], out[9]);   // z, w: face maps
 }
 
 // ------------------------------------------------------------ FP64 push
@@ -1220,21 +1220,19 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c, 
                              __float_as_int(nbf.w));
   const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
   if (nbt >= 0) {
-    const int4 o4 = __ldg(&A.tn[c.T]), n4 = __ldg(&A.tn[nbt]);
-    const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nnd[4] = {n4.x, n4.y, n4.z, n4.w};
-    int ent = 0;
+    // the face map (same record line) says which of this tet's nodes each of
+    // the neighbour's nodes is, and which one it enters through
+    const float2 fm2 = __ldg(reinterpret_cast<const float2*>(A.tetrec + 8 * (int64_t)c.T + 6) + 1);
+    const uint32_t fm = ((kx < 2 ? __float_as_uint(fm2.x) : __float_as_uint(fm2.y)) >> (16 * (kx & 1))) & 0xffffu;
+    const int ent = (int)(fm & 3u);
 #pragma unroll
     for (int i2 = 0; i2 < 4; i2++) {
+      const int j = (int)((fm >> (2 + 2 * i2)) & 3u);
       int32_t val = 0;
-      bool hit = false;
 #pragma unroll
-      for (int j = 0; j < 4; j++)
-        if (on[j] == nnd[i2]) {
-          val = Qp[j];
-          hit = true;
-        }
-      c.Qa[i2] = val;
-      if (!hit) ent = i2;
+      for (int jj = 0; jj < 4; jj++)
+        if (jj == j) val = Qp[jj];
+      c.Qa[i2] = (i2 == ent) ? 0 : val;
     }
     c.T = nbt;
     c.entry = ent;
@@ -2113,6 +2111,30 @@ static int upload(fempic_env* e) {
     geo[8 * t + 2] = make_float4(g[2], g[3], g[4], g[5]);
     geo[8 * t + 3] = make_float4(g[6], g[7], g[8], 0.f);
     for (int k = 4; k < 7; k++) geo[8 * t + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+      // face maps of the mixed crossing walk, 16 bits per local face k with a
+      // neighbour: bits 0-1 the neighbour's local node that is not in this
+      // tet (its entry face), bits 2+2i the local node of this tet that is
+      // the neighbour's local node i (any value for the entry node)
+      uint32_t fmap[2] = {0u, 0u};
+      for (int k = 0; k < 4; k++) {
+        const int32_t nbt = m.nb[4 * t + k];
+        if (nbt < 0) continue;
+        uint32_t code = 0u;
+        for (int i2 = 0; i2 < 4; i2++) {
+          int hit = -1;
+          for (int j = 0; j < 4; j++)
+            if (m.tn[4 * t + j] == m.tn[4 * (int64_t)nbt + i2]) hit = j;
+          if (hit < 0)
+            code |= (uint32_t)i2;
+          else
+            code |= (uint32_t)hit << (2 + 2 * i2);
+        }
+        fmap[k >> 1] |= code << (16 * (k & 1));
+      }
+      std::memcpy(&geo[8 * t + 6].z, &fmap[0], 4);
+      std::memcpy(&geo[8 * t + 6].w, &fmap[1], 4);
+    }
     int32_t nbk[4] = {m.nb[4 * t], m.nb[4 * t + 1], m.nb[4 * t + 2], m.nb[4 * t + 3]};
     float4 nbf;
     std::memcpy(&nbf, nbk, sizeof(nbf));
