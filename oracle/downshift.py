@@ -187,10 +187,10 @@ def push_step_downshift(mesh: OracleMesh, st: OracleState, hist: History, e_dof,
         E, B = mesh.gather(int(st.tet[p]), np.array([st.x[p], st.y[p], st.z[p]]), e_dof, b_dof)
         e_n[p] = amp * E
         b_n[p] = amp * B
-    if not hist.started:                      # D5
-        hist.v[:] = v_n
-        hist.e[:] = e_n
-        hist.b[:] = b_n
+    if not hist.started:                      # D5 (particles already frozen keep no history)
+        hist.v[:, active] = v_n[active]
+        hist.e[:, active] = e_n[active]
+        hist.b[:, active] = b_n[active]
         hist.started = True
     W = ml_weights(t, dt, omega0, lag)
     v_next = v_n.copy()

@@ -1,6 +1,6 @@
 """Build libfempic_env.so in-tree for sm_103a (nvcc + g++, no cmake).
 
-The CUDA translation unit and the host mesh builder compile in parallel, then
+The CUDA translation units and the host mesh builder compile in parallel, then
 nvcc links the shared library next to this file.
 """
 from __future__ import annotations
@@ -17,9 +17,10 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfempic_env.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES_CU = ["fempic_env.cu"]
+SOURCES_CU = ["fempic_env.cu", "fempic_downshift.cu"]
 SOURCES_CPP = ["fempic_mesh.cpp"]
-HEADERS = [os.path.join(CSRC, "fempic_internal.h"), os.path.join(INCLUDE, "fempic_env.h")]
+HEADERS = [os.path.join(CSRC, "fempic_internal.h"), os.path.join(INCLUDE, "fempic_env.h"),
+           os.path.join(INCLUDE, "fempic_downshift.h")]
 
 
 def _nvcc() -> str:

@@ -30,6 +30,10 @@ EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_pus
            "fempic_deposit", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
            "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
            "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
+# Every function declared in include/fempic_downshift.h.
+DS_EXPORTS = ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift",
+              "fempic_downshift_last_error", "fempic_downshift_destroy")
+FEMPIC_DS_VH, FEMPIC_DS_F, FEMPIC_DS_VN, FEMPIC_DS_U, FEMPIC_DS_PLANES = 0, 9, 33, 36, 39
 FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS, \
     FEMPIC_K_ADJOINT = range(8)
 FEMPIC_K_COUNT = 8
@@ -65,6 +69,10 @@ class fempic_envelope(C.Structure):
 class fempic_envelope3(C.Structure):
     _fields_ = [("e_tilde", C.c_void_p * 3), ("b_tilde", C.c_void_p * 3), ("weight", C.c_double * 3),
                 ("amp", C.c_double)]
+
+
+class fempic_downshift_history(C.Structure):
+    _fields_ = [("n", C.c_int64), ("planes", C.c_void_p)]
 
 
 class FempicError(RuntimeError):
@@ -112,6 +120,17 @@ def load(path: str = LIB_PATH):
                                                  C.c_void_p]
         lib.fempic_profile_enable.argtypes = [C.c_void_p, C.c_int32]
         lib.fempic_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_downshift_create.argtypes = [P(fempic_mesh_desc), P(C.c_void_p)]
+        lib.fempic_downshift_weights.argtypes = [C.c_double, C.c_double, C.c_double, C.c_void_p]
+        lib.fempic_push_step_downshift.argtypes = [C.c_void_p, C.c_void_p, P(fempic_particles),
+                                                   P(fempic_downshift_history), P(fempic_envelope), C.c_double,
+                                                   C.c_double, C.c_double, C.c_int32, C.c_void_p]
+        lib.fempic_downshift_last_error.restype = C.c_char_p
+        lib.fempic_downshift_last_error.argtypes = []
+        lib.fempic_downshift_destroy.argtypes = [C.c_void_p]
+        lib.fempic_downshift_destroy.restype = None
+        for name in ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift"):
+            getattr(lib, name).restype = C.c_int
         lib.fempic_last_error.restype = C.c_char_p
         lib.fempic_last_error.argtypes = []
         lib.fempic_env_destroy.argtypes = [C.c_void_p]
@@ -230,3 +249,40 @@ def fempic_last_error() -> str:
 def fempic_env_destroy(env):
     if env:
         load().fempic_env_destroy(env)
+
+
+# Downshifted integrator (include/fempic_downshift.h) ----------------------
+def check_ds(rc: int, what: str):
+    if rc != FEMPIC_OK:
+        msg = load().fempic_downshift_last_error().decode(errors="replace")
+        raise FempicError(f"{what} failed ({rc}): {msg}")
+
+
+def fempic_downshift_create(mesh: fempic_mesh_desc) -> int:
+    h = C.c_void_p()
+    check_ds(load().fempic_downshift_create(C.byref(mesh), C.byref(h)), "fempic_downshift_create")
+    return h.value
+
+
+def fempic_downshift_weights(t, dt, omega0) -> tuple:
+    """(M^r[3], M^i[3], L^r[3][3], L^i[3][3]) of the step [t, t + dt]."""
+    w = (C.c_double * 24)()
+    check_ds(load().fempic_downshift_weights(float(t), float(dt), float(omega0), w), "fempic_downshift_weights")
+    w = list(w)
+    return (w[0:3], w[3:6], [w[6 + 3 * j:9 + 3 * j] for j in range(3)],
+            [w[15 + 3 * j:18 + 3 * j] for j in range(3)])
+
+
+def fempic_push_step_downshift(env, ds, parts: fempic_particles, hist: fempic_downshift_history,
+                               envl: fempic_envelope, omega0, t, dt, start: bool, stream=0):
+    check_ds(load().fempic_push_step_downshift(env, ds, C.byref(parts), C.byref(hist), C.byref(envl),
+                                               float(omega0), float(t), float(dt), 1 if start else 0, stream),
+             "fempic_push_step_downshift")
+
+
+def fempic_downshift_last_error() -> str:
+    return load().fempic_downshift_last_error().decode(errors="replace")
+
+
+def fempic_downshift_destroy(ds):
+    load().fempic_downshift_destroy(ds)

@@ -1,0 +1,422 @@
+// Downshifted particle integrator of Sec. III-D on the FP64 form: the
+// velocity rule with the carrier integrated analytically (M and L weights)
+// and AB4 positions.  The AB4 segment is tracked and deposited by the env's
+// own FP64 step, run with a zero field, between the two kernels of this file.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <string>
+
+#include "fempic_downshift.h"
+#include "fempic_internal.h"
+
+namespace {
+
+using fempic::HostMesh;
+using fempic::kMaxSpecies;
+
+thread_local std::string g_ds_error;
+
+int fail(int code, const std::string& msg) {
+  g_ds_error = msg;
+  return code;
+}
+
+#define DS_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(FEMPIC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kThreads = 256;
+
+// Local edge e joins sorted local nodes (le0, le1) in the order 01,02,03,12,
+// 13,23; local face f is opposite node f and its i-th node is lf(f, i).
+__host__ __device__ constexpr int le0(int e) { return e < 3 ? 0 : (e < 5 ? 1 : 2); }
+__host__ __device__ constexpr int le1(int e) { return e < 3 ? e + 1 : (e == 3 ? 2 : 3); }
+__host__ __device__ constexpr int lf(int f, int i) { return i < f ? i : i + 1; }
+
+struct DsArgs {
+  int64_t n;
+  const double* x;
+  const double* y;
+  const double* z;
+  double* vx;
+  double* vy;
+  double* vz;
+  const int32_t* tet;
+  double* h;                    // history planes [FEMPIC_DS_PLANES][n]
+  int64_t nt;
+  const double* geom;           // [nt][12]: x0, grad l1, grad l2, grad l3
+  const int32_t* te;            // [nt][6]
+  const int32_t* tf;            // [nt][4]
+  const double2* e;             // complex128 [ne]
+  const double2* b;             // complex128 [nf]
+  double amp;
+  int32_t ns;
+  int32_t start;
+  int64_t begin[kMaxSpecies + 1];
+  double qm[kMaxSpecies];
+  double w[24];                 // M^r[3], M^i[3], L^r[3][3], L^i[3][3]
+};
+
+__device__ __forceinline__ int species_of(const DsArgs& A, int64_t p) {
+  int s = 0;
+#pragma unroll 1
+  while (s + 1 < A.ns && p >= A.begin[s + 1]) s++;
+  return s;
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Complex envelope at r in tet T (Sec. III-A): E~ = sum_e e~_e W1_e with
+// W1_ij = l_i grad l_j - l_j grad l_i, B~ = sum_f b~_f W2_f with
+// W2_ijk = 2 (l_i grad l_j x grad l_k + l_j grad l_k x grad l_i + l_k grad l_i x grad l_j);
+// out[12] = Re E~, Im E~, Re B~, Im B~.
+__device__ void envelope_at(const DsArgs& A, int32_t T, double rx, double ry, double rz, double out[12]) {
+  const double* G = A.geom + 12 * (int64_t)T;
+  double g[4][3];
+#pragma unroll
+  for (int k = 1; k < 4; k++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) g[k][a] = G[3 * k + a];
+#pragma unroll
+  for (int a = 0; a < 3; a++) g[0][a] = -(g[1][a] + g[2][a] + g[3][a]);
+  const double d[3] = {rx - G[0], ry - G[1], rz - G[2]};
+  double lam[4];
+#pragma unroll
+  for (int k = 1; k < 4; k++) lam[k] = g[k][0] * d[0] + g[k][1] * d[1] + g[k][2] * d[2];
+  lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+#pragma unroll
+  for (int c = 0; c < 12; c++) out[c] = 0.0;
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const int i = le0(e), j = le1(e);
+    const double2 c = A.e[A.te[6 * (int64_t)T + e]];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const double w = lam[i] * g[j][a] - lam[j] * g[i][a];
+      out[a] += c.x * w;
+      out[3 + a] += c.y * w;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < 4; f++) {
+    const int i = lf(f, 0), j = lf(f, 1), k = lf(f, 2);
+    double cjk[3], cki[3], cij[3];
+    cross3(g[j], g[k], cjk);
+    cross3(g[k], g[i], cki);
+    cross3(g[i], g[j], cij);
+    const double2 c = A.b[A.tf[4 * (int64_t)T + f]];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const double w = 2.0 * (lam[i] * cjk[a] + lam[j] * cki[a] + lam[k] * cij[a]);
+      out[6 + a] += c.x * w;
+      out[9 + a] += c.y * w;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 12; c++) out[c] *= A.amp;
+}
+
+// Before the env's step: the envelope sample at r^n, the velocity rule, the
+// AB4 velocity u (left in v for the env's zero-field step to track), the new
+// velocity and u kept in the scratch planes, and the history shifted.
+__global__ void __launch_bounds__(kThreads) k_ds_pre(DsArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.n) return;
+  const int64_t n = A.n;
+  double* H = A.h;
+  const double v0[3] = {A.vx[p], A.vy[p], A.vz[p]};
+  const int32_t T = A.tet[p];
+  if (T < 0 || T >= A.nt) {   // inactive: the state is kept (the env's step flags an out-of-range tet)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      H[(FEMPIC_DS_VN + a) * n + p] = v0[a];
+      H[(FEMPIC_DS_U + a) * n + p] = v0[a];
+    }
+    return;
+  }
+  double cur[12];
+  envelope_at(A, T, A.x[p], A.y[p], A.z[p], cur);
+  double vh[3][3], f1[12], f2[12];
+  if (A.start) {
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) vh[i][a] = v0[a];
+#pragma unroll
+    for (int c = 0; c < 12; c++) f1[c] = f2[c] = cur[c];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) vh[i][a] = H[(FEMPIC_DS_VH + 3 * i + a) * n + p];
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      f1[c] = H[(FEMPIC_DS_F + c) * n + p];
+      f2[c] = H[(FEMPIC_DS_F + 12 + c) * n + p];
+    }
+  }
+  const double* S[3] = {cur, f1, f2};
+  const double* V[3] = {v0, vh[0], vh[1]};
+  const double* Mr = A.w;
+  const double* Mi = A.w + 3;
+  const double* Lr = A.w + 6;
+  const double* Li = A.w + 15;
+  double dv[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) dv[a] += S[k][a] * Mr[k] + S[k][3 + a] * Mi[k];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    double C[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+#pragma unroll
+      for (int a = 0; a < 3; a++) C[a] += S[k][6 + a] * Lr[3 * j + k] + S[k][9 + a] * Li[3 * j + k];
+    double vc[3];
+    cross3(V[j], C, vc);
+#pragma unroll
+    for (int a = 0; a < 3; a++) dv[a] += vc[a];
+  }
+  const double qm = A.qm[species_of(A, p)];
+  double u[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    u[a] = (55.0 * v0[a] - 59.0 * vh[0][a] + 37.0 * vh[1][a] - 9.0 * vh[2][a]) / 24.0;
+    H[(FEMPIC_DS_VN + a) * n + p] = v0[a] + qm * dv[a];
+    H[(FEMPIC_DS_U + a) * n + p] = u[a];
+    H[(FEMPIC_DS_VH + 6 + a) * n + p] = vh[1][a];
+    H[(FEMPIC_DS_VH + 3 + a) * n + p] = vh[0][a];
+    H[(FEMPIC_DS_VH + a) * n + p] = v0[a];
+  }
+#pragma unroll
+  for (int c = 0; c < 12; c++) {
+    H[(FEMPIC_DS_F + 12 + c) * n + p] = f1[c];
+    H[(FEMPIC_DS_F + c) * n + p] = cur[c];
+  }
+  A.vx[p] = u[0];
+  A.vy[p] = u[1];
+  A.vz[p] = u[2];
+}
+
+// After the env's step: an axis in which the tracked velocity came back
+// negated was mirrored by a wall (an odd number of times; a zero component
+// cannot reach a wall), so the new velocity and the velocity history are
+// mirrored in it; then v <- v^{n+1}.
+__global__ void __launch_bounds__(kThreads) k_ds_post(DsArgs A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.n) return;
+  const int64_t n = A.n;
+  double* H = A.h;
+  double* vp[3] = {A.vx, A.vy, A.vz};
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const double va = vp[a][p];
+    const double u = H[(FEMPIC_DS_U + a) * n + p];
+    double vn = H[(FEMPIC_DS_VN + a) * n + p];
+    if (u != 0.0 && va == -u) {
+      vn = -vn;
+#pragma unroll
+      for (int i = 0; i < 3; i++) {
+        double& h = H[(FEMPIC_DS_VH + 3 * i + a) * n + p];
+        h = -h;
+      }
+    }
+    vp[a][p] = vn;
+  }
+}
+
+// int_0^1 x^m e^{j theta x} dx, m = 0..4: the power series of the exponential
+// integrated term by term for |theta| <= 1, else the integration-by-parts
+// recurrence J_m = (e^{j theta} - m J_{m-1}) / (j theta).
+void moments(double theta, std::complex<double> J[5]) {
+  using cd = std::complex<double>;
+  if (std::fabs(theta) <= 1.0) {
+    for (int m = 0; m < 5; m++) {
+      cd term(1.0, 0.0), sum(0.0, 0.0);   // term = (j theta)^l / l!
+      for (int l = 0; l < 40; l++) {
+        sum += term / double(m + l + 1);
+        term *= cd(0.0, theta) / double(l + 1);
+      }
+      J[m] = sum;
+    }
+  } else {
+    const cd e = std::polar(1.0, theta), jt(0.0, theta);
+    J[0] = (e - 1.0) / jt;
+    for (int m = 1; m < 5; m++) J[m] = (e - double(m) * J[m - 1]) / jt;
+  }
+}
+
+void compute_weights(double t, double dt, double omega0, double* w) {
+  using cd = std::complex<double>;
+  // basis on the nodes x_k = -k (x = (t' - t) / dt) as coefficient vectors
+  double c[3][3];
+  for (int k = 0; k < 3; k++) {
+    double poly[3] = {1.0, 0.0, 0.0};
+    for (int j = 0; j < 3; j++) {
+      if (j == k) continue;
+      const double xk = -double(k), xj = -double(j), den = xk - xj;
+      double nxt[3] = {0.0, 0.0, 0.0};   // poly * (x - xj) / den
+      for (int m = 0; m < 3; m++) {
+        if (m + 1 < 3) nxt[m + 1] += poly[m] / den;
+        nxt[m] -= poly[m] * xj / den;
+      }
+      for (int m = 0; m < 3; m++) poly[m] = nxt[m];
+    }
+    for (int m = 0; m < 3; m++) c[k][m] = poly[m];
+  }
+  cd J[5];
+  moments(omega0 * dt, J);
+  const cd f = dt * std::polar(1.0, omega0 * t);
+  for (int k = 0; k < 3; k++) {
+    cd I(0.0, 0.0);
+    for (int m = 0; m < 3; m++) I += c[k][m] * J[m];
+    I *= f;
+    w[k] = I.real();
+    w[3 + k] = -I.imag();
+  }
+  for (int j = 0; j < 3; j++)
+    for (int k = 0; k < 3; k++) {
+      double prod[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) prod[a + b] += c[j][a] * c[k][b];
+      cd I(0.0, 0.0);
+      for (int m = 0; m < 5; m++) I += prod[m] * J[m];
+      I *= f;
+      w[6 + 3 * j + k] = I.real();
+      w[15 + 3 * j + k] = -I.imag();
+    }
+}
+
+unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+struct fempic_downshift {
+  int64_t nn = 0, ne = 0, nf = 0, nt = 0;
+  double* geom = nullptr;
+  int32_t* te = nullptr;
+  int32_t* tf = nullptr;
+};
+
+static void free_ds(fempic_downshift* d) {
+  if (!d) return;
+  cudaFree(d->geom);
+  cudaFree(d->te);
+  cudaFree(d->tf);
+  delete d;
+}
+
+extern "C" const char* fempic_downshift_last_error(void) { return g_ds_error.c_str(); }
+
+extern "C" void fempic_downshift_destroy(fempic_downshift* ds) { free_ds(ds); }
+
+extern "C" int fempic_downshift_create(const fempic_mesh_desc* mesh, fempic_downshift** out) {
+  if (!mesh || !out) return fail(FEMPIC_EINVAL, "downshift_create: NULL argument");
+  *out = nullptr;
+  HostMesh m;
+  std::string err;
+  const int rc = fempic::build_host_mesh(*mesh, &m, &err);
+  if (rc != FEMPIC_OK) return fail(rc, "downshift_create: " + err);
+  fempic_downshift* d = new (std::nothrow) fempic_downshift();
+  if (!d) return fail(FEMPIC_ENOMEM, "downshift_create: host allocation");
+  d->nn = m.nn;
+  d->ne = m.ne;
+  d->nf = m.nf;
+  d->nt = m.nt;
+  const size_t sg = sizeof(double) * 12 * (size_t)m.nt, se = sizeof(int32_t) * 6 * (size_t)m.nt,
+               sf = sizeof(int32_t) * 4 * (size_t)m.nt;
+  if (cudaMalloc(&d->geom, sg) != cudaSuccess || cudaMalloc(&d->te, se) != cudaSuccess ||
+      cudaMalloc(&d->tf, sf) != cudaSuccess) {
+    free_ds(d);
+    cudaGetLastError();
+    return fail(FEMPIC_ENOMEM, "downshift_create: device allocation");
+  }
+  if (cudaMemcpy(d->geom, m.geom.data(), sg, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d->te, m.te.data(), se, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d->tf, m.tf.data(), sf, cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_ds(d);
+    return fail(FEMPIC_ECUDA, "downshift_create: upload");
+  }
+  *out = d;
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_downshift_weights(double t, double dt, double omega0, double* w_out) {
+  if (!w_out) return fail(FEMPIC_EINVAL, "downshift_weights: NULL output");
+  if (!std::isfinite(t) || !std::isfinite(dt) || !std::isfinite(omega0) || !(dt > 0.0))
+    return fail(FEMPIC_EINVAL, "downshift_weights: non-finite scalar or dt <= 0");
+  compute_weights(t, dt, omega0, w_out);
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds, const fempic_particles* p,
+                                          const fempic_downshift_history* hist, const fempic_envelope* envl,
+                                          double omega0, double t, double dt, int32_t start, void* stream) {
+  if (!env || !ds || !p || !hist || !envl) return fail(FEMPIC_EINVAL, "push_step_downshift: NULL argument");
+  if (p->n < 0 || hist->n != p->n) return fail(FEMPIC_EINVAL, "push_step_downshift: history size != particles");
+  if (!envl->e_tilde || !envl->b_tilde) return fail(FEMPIC_EINVAL, "push_step_downshift: NULL DoF arrays");
+  if (!std::isfinite(t) || !std::isfinite(dt) || !(dt > 0.0) || !std::isfinite(omega0) ||
+      !std::isfinite(envl->amp))
+    return fail(FEMPIC_EINVAL, "push_step_downshift: non-finite scalar or dt <= 0");
+  if (start != 0 && start != 1) return fail(FEMPIC_EINVAL, "push_step_downshift: start must be 0 or 1");
+  int64_t counts[4];
+  if (fempic_env_query(env, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr) != FEMPIC_OK ||
+      counts[3] != ds->nt || counts[1] != ds->ne || counts[2] != ds->nf)
+    return fail(FEMPIC_EINVAL, "push_step_downshift: env and downshift tables are of different meshes");
+  if (p->n == 0) return FEMPIC_OK;
+  if (!hist->planes || !p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->tet || !p->status)
+    return fail(FEMPIC_EINVAL, "push_step_downshift: NULL particle or history array");
+  if (p->n_species < 1 || p->n_species > kMaxSpecies || !p->species_begin || !p->q || !p->m)
+    return fail(FEMPIC_EINVAL, "push_step_downshift: species table (1..8 ranges, q, m)");
+  if (p->species_begin[0] != 0 || p->species_begin[p->n_species] != p->n)
+    return fail(FEMPIC_EINVAL, "push_step_downshift: species ranges must cover [0, n)");
+  DsArgs A{};
+  A.ns = p->n_species;
+  for (int s = 0; s <= kMaxSpecies; s++) A.begin[s] = s <= p->n_species ? p->species_begin[s] : p->n;
+  for (int s = 0; s < p->n_species; s++) {
+    if (s > 0 && A.begin[s] < A.begin[s - 1]) return fail(FEMPIC_EINVAL, "push_step_downshift: species ranges decrease");
+    if (!(p->m[s] > 0.0) || !std::isfinite(p->q[s])) return fail(FEMPIC_EINVAL, "push_step_downshift: q, m");
+    A.qm[s] = p->q[s] / p->m[s];
+  }
+  if (A.begin[p->n_species] < A.begin[p->n_species - 1])
+    return fail(FEMPIC_EINVAL, "push_step_downshift: species ranges decrease");
+  A.n = p->n;
+  A.x = p->x;
+  A.y = p->y;
+  A.z = p->z;
+  A.vx = static_cast<double*>(p->vx);
+  A.vy = static_cast<double*>(p->vy);
+  A.vz = static_cast<double*>(p->vz);
+  A.tet = p->tet;
+  A.h = hist->planes;
+  A.nt = ds->nt;
+  A.geom = ds->geom;
+  A.te = ds->te;
+  A.tf = ds->tf;
+  A.e = static_cast<const double2*>(envl->e_tilde);
+  A.b = static_cast<const double2*>(envl->b_tilde);
+  A.amp = envl->amp;
+  A.start = start;
+  compute_weights(t, dt, omega0, A.w);
+  cudaStream_t st = (cudaStream_t)stream;
+  k_ds_pre<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  DS_CUDA(cudaGetLastError());
+  // the AB4 segment: the env's own step under a zero field tracks, reflects
+  // or absorbs and deposits r^n -> r^n + dt u
+  fempic_envelope zero = *envl;
+  zero.amp = 0.0;
+  const int rc = fempic_push_step(env, p, &zero, omega0, t, dt, stream);
+  if (rc != FEMPIC_OK) return fail(rc, std::string("push_step_downshift: env step: ") + fempic_last_error());
+  k_ds_post<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  DS_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}

@@ -27,6 +27,16 @@ def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
 
+def _mesh_desc(nodes: np.ndarray, tets: np.ndarray, lo, hi) -> capi.fempic_mesh_desc:
+    """Describe host arrays the caller keeps alive for the duration of the call."""
+    desc = capi.fempic_mesh_desc()
+    desc.n_nodes, desc.n_tets = nodes.shape[0], tets.shape[0]
+    desc.nodes_xyz, desc.tet_nodes = nodes.ctypes.data, tets.ctypes.data
+    for a in range(3):
+        desc.bbox_lo[a], desc.bbox_hi[a] = float(lo[a]), float(hi[a])
+    return desc
+
+
 class ParticleState:
     """Particle SoA on the device: x, y, z (f64), vx, vy, vz (f64 or f32), tet
     (i32), status (u8), n_cross (i32), plus the host species table."""
@@ -101,11 +111,8 @@ class FempicEnv:
                  precision: int = FEMPIC_FP64, max_crossings: int = 4096, wall_mode: int = 0):
         nodes = np.ascontiguousarray(nodes, dtype=np.float64)
         tets = np.ascontiguousarray(tets, dtype=np.int32)
-        desc = capi.fempic_mesh_desc()
-        desc.n_nodes, desc.n_tets = nodes.shape[0], tets.shape[0]
-        desc.nodes_xyz, desc.tet_nodes = nodes.ctypes.data, tets.ctypes.data
-        for a in range(3):
-            desc.bbox_lo[a], desc.bbox_hi[a] = float(lo[a]), float(hi[a])
+        self._mesh = (nodes, tets, tuple(lo), tuple(hi))
+        desc = _mesh_desc(*self._mesh)
         opt = capi.fempic_options(precision, max_crossings, wall_mode, 0)
         torch.cuda.init()
         self.precision = precision
@@ -233,3 +240,50 @@ class FempicEnv:
         capi.fempic_profile_read(self.h, ms.ctypes.data, calls.ctypes.data, kern.ctypes.data)
         names = ("locate", "field", "push", "finalize", "charge", "sort", "cross", "adjoint")
         return {nm: dict(ms=float(ms[i]), launches=int(calls[i]), kernels=int(kern[i])) for i, nm in enumerate(names)}
+
+
+class Downshift:
+    """The downshifted integrator of Sec. III-D on an FP64-form env.
+
+    Velocity rule with the carrier integrated analytically over each step (M
+    and L weights on the newest three envelope samples) and fourth-order
+    Adams-Bashforth positions; the segment is tracked and deposited by the
+    env's own step.  Holds the per-tet gather tables and the particles'
+    history planes ([FEMPIC_DS_PLANES, n] f64 on the device).  Velocities are
+    at integer levels (v^n), not half steps.  The history follows the
+    particle order, so the particle set must not be re-sorted between steps."""
+
+    def __init__(self, env: FempicEnv, n: int, device="cuda"):
+        if env.precision != FEMPIC_FP64:
+            raise capi.FempicError("the downshifted integrator runs on the FP64 form")
+        self.env = env
+        self.h = capi.fempic_downshift_create(_mesh_desc(*env._mesh))
+        self.planes = torch.zeros((capi.FEMPIC_DS_PLANES, n), dtype=torch.float64, device=device)
+        self.started = False
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.fempic_downshift_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, st: ParticleState, e_dof: torch.Tensor, b_dof: torch.Tensor, amp: float, omega0: float,
+             t: float, dt: float, stream=None):
+        """One step from t to t + dt; amp = a(t).  The first call fills the history."""
+        env = self.env
+        if e_dof.dtype != torch.complex128 or b_dof.dtype != torch.complex128:
+            raise capi.FempicError("DoFs must be complex128 on the FP64 form")
+        if e_dof.numel() != env.n_edges or b_dof.numel() != env.n_faces or not e_dof.is_cuda or not b_dof.is_cuda:
+            raise capi.FempicError("DoF arrays must be device tensors of length n_edges / n_faces")
+        if st.vx.dtype != torch.float64 or st.n != self.planes.shape[1]:
+            raise capi.FempicError("velocities must be float64 and the history sized for this particle set")
+        hist = capi.fempic_downshift_history(st.n, _ptr(self.planes))
+        envl = capi.fempic_envelope(_ptr(e_dof), _ptr(b_dof), float(amp))
+        capi.fempic_push_step_downshift(env.h, self.h, st.cstruct(), hist, envl, omega0, t, dt,
+                                        not self.started, _stream(stream))
+        self.started = True

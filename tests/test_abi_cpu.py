@@ -19,19 +19,44 @@ def lib():
     return capi.load()
 
 
-def _declared():
-    txt = open(os.path.join(ROOT, "include", "fempic_env.h")).read()
+def _declared(header="fempic_env.h"):
+    txt = open(os.path.join(ROOT, "include", header)).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(fempic_\w+)\s*\(", txt)))
 
 
 def test_header_declares_what_binding_exports():
     assert sorted(capi.EXPORTS) == _declared()
+    assert sorted(capi.DS_EXPORTS) == _declared("fempic_downshift.h")
+
+
+def test_every_header_is_covered():
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["fempic_downshift.h", "fempic_env.h"]
 
 
 def test_library_exports_every_declared_symbol(lib):
-    for name in _declared():
+    for name in _declared() + _declared("fempic_downshift.h"):
         assert hasattr(lib, name), name
+
+
+def test_downshift_plane_layout_matches_header():
+    txt = open(os.path.join(ROOT, "include", "fempic_downshift.h")).read()
+    got = {k: int(v) for k, v in re.findall(r"#define FEMPIC_DS_(\w+) (\d+)", txt)}
+    assert got == {"VH": capi.FEMPIC_DS_VH, "F": capi.FEMPIC_DS_F, "VN": capi.FEMPIC_DS_VN,
+                   "U": capi.FEMPIC_DS_U, "PLANES": capi.FEMPIC_DS_PLANES}
+    # 3 velocity levels + 2 complex E~, B~ sample levels + 2 scratch vectors
+    assert got["F"] == 9 and got["VN"] == 9 + 24 and got["PLANES"] == got["U"] + 3
+
+
+def test_downshift_null_arguments_rejected_on_host(lib):
+    assert lib.fempic_downshift_create(None, None) == capi.FEMPIC_EINVAL
+    assert "NULL" in capi.fempic_downshift_last_error()
+    assert lib.fempic_push_step_downshift(None, None, None, None, None, 0.0, 0.0, 1e-9, 1, None) == \
+        capi.FEMPIC_EINVAL
+    w = (C.c_double * 24)()
+    assert lib.fempic_downshift_weights(0.0, -1.0, 1.0, w) == capi.FEMPIC_EINVAL
+    assert lib.fempic_downshift_weights(float("nan"), 1.0, 1.0, w) == capi.FEMPIC_EINVAL
+    lib.fempic_downshift_destroy(None)   # safe on NULL
 
 
 def test_null_arguments_rejected_on_host(lib):

@@ -3,7 +3,8 @@ the carrier integrated analytically through the M and L weights, AB4
 positions) against what the mathematics fixes, independent of its formulas:
 symbolic integrals, Adams-Bashforth coefficients, closed-form trajectories,
 the closed-form gyration, a high-accuracy ODE solution, the mesh-free form of
-the same rule, and the deposit's charge identity."""
+the same rule, and the deposit's charge identity.  Also the library's host
+weight function against the oracle's."""
 import math
 
 import numpy as np
@@ -68,6 +69,21 @@ def test_weights_sum_to_the_carrier_integral():
         assert abs(Mi.sum() - (math.cos(b) - math.cos(a)) / om) < 1e-12 * dt
         np.testing.assert_allclose(Lr.sum(1), Mr, atol=1e-13 * dt)
         np.testing.assert_allclose(Li.sum(0), Mi, atol=1e-13 * dt)
+
+
+def test_library_weights_match_the_oracle_on_the_host():
+    from paper_2208_12795_gb300 import build, capi
+    build.build()
+    rng = np.random.default_rng(12)
+    dt = 0.5e-9
+    for theta in [0.0, 1e-7, 0.3, 1.0, 1.0000001, 2.5, 6.0, -0.8]:
+        t = rng.uniform(0.0, 1e-7)
+        got = capi.fempic_downshift_weights(t, dt, theta / dt)
+        want = ml_weights(t, dt, theta / dt)
+        for g, w in zip(got, want):
+            np.testing.assert_allclose(np.array(g), np.asarray(w), rtol=0, atol=1e-13 * dt)
+    with pytest.raises(capi.FempicError):
+        capi.fempic_downshift_weights(0.0, 0.0, 1.0)
 
 
 @pytest.mark.parametrize("lag", [0, 1])
