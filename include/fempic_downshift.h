@@ -41,7 +41,8 @@
 extern "C" {
 #endif
 
-typedef struct fempic_downshift fempic_downshift;   /* opaque: the per-tet gather tables */
+typedef struct fempic_downshift fempic_downshift;   /* opaque: per-tet geometry, edge and face
+                                                       ids, and the per-tet envelope coefficients */
 
 /* History planes of a particle set: one device f64 array [FEMPIC_DS_PLANES][n]
  * (plane-major, particle index fastest), owned by the caller:
@@ -62,9 +63,9 @@ typedef struct {
 } fempic_downshift_history;
 
 /* Build the gather tables (FP64 barycentric geometry, tet edges and faces)
- * from the same mesh description the env was created from, and upload them
- * to the current device.  Errors: EINVAL, EMESH, ENOMEM, ECUDA.
- * Synchronizes the device. */
+ * from the same mesh description the env was created from, upload them to
+ * the current device and allocate the per-tet coefficient buffer (20 f64 per
+ * tet).  Errors: EINVAL, EMESH, ENOMEM, ECUDA.  Synchronizes the device. */
 int fempic_downshift_create(const fempic_mesh_desc* mesh, fempic_downshift** out);
 
 /* Host only, no GPU work: the weights of the step [t, t + dt] at carrier
@@ -77,7 +78,8 @@ int fempic_downshift_weights(double t, double dt, double omega0, double* w_out);
 
 /* One downshifted step from t to t + dt of every particle with tet >= 0, on
  * an env created with FEMPIC_FP64 from the mesh of ds: envelope samples at
- * r^n (Whitney sums of envl's complex128 DoFs times envl->amp = a(t)), the
+ * r^n (Whitney sums of envl's complex128 DoFs times envl->amp = a(t), built
+ * per tet as the affine form E~ = E0 + d x W, B~ = B0 + beta d), the
  * velocity rule, the AB4 segment tracked and deposited into the env's dG
  * (added to, not cleared), the history shifted.  start = 1 fills the history
  * with this step's own values first (constant extrapolation backwards).

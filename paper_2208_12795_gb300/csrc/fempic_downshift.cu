@@ -49,11 +49,7 @@ struct DsArgs {
   double* h;                    // history planes [FEMPIC_DS_PLANES][n]
   int64_t nt;
   const double* geom;           // [nt][12]: x0, grad l1, grad l2, grad l3
-  const int32_t* te;            // [nt][6]
-  const int32_t* tf;            // [nt][4]
-  const double2* e;             // complex128 [ne]
-  const double2* b;             // complex128 [nf]
-  double amp;
+  const double* coef;           // [nt][20]: per-tet envelope coefficients of this step (k_ds_field)
   int32_t ns;
   int32_t start;
   int64_t begin[kMaxSpecies + 1];
@@ -74,12 +70,24 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// Complex envelope at r in tet T (Sec. III-A): E~ = sum_e e~_e W1_e with
-// W1_ij = l_i grad l_j - l_j grad l_i, B~ = sum_f b~_f W2_f with
-// W2_ijk = 2 (l_i grad l_j x grad l_k + l_j grad l_k x grad l_i + l_k grad l_i x grad l_j);
-// out[12] = Re E~, Im E~, Re B~, Im B~.
-__device__ void envelope_at(const DsArgs& A, int32_t T, double rx, double ry, double rz, double out[12]) {
-  const double* G = A.geom + 12 * (int64_t)T;
+// Per-tet complex envelope coefficients of one step (Sec. III-A).  Inside a
+// tet both Whitney sums are affine in d = r - x0 (x0 = the tet's node 0,
+// lambda_k = delta_k0 + g_k . d with g_k = grad lambda_k):
+//   W1_ij = const + d x (g_j x g_i), so E~ = E0 + d x W with
+//     E0 = sum_j e~_0j g_j,  W = sum_{i<j} e~_ij (g_j x g_i);
+//   W2_ijk = const + 2 det[g_i, g_j, g_k] d, so B~ = B0 + beta d with
+//     B0 = 2 sum over the faces (0, j, k) of b~_f g_j x g_k,
+//     beta = 2 sum_f b~_f det[g_i, g_j, g_k].
+// coef[20 t ..]: Re (E0, W, B0, beta), then Im (E0, W, B0, beta), times a(t).
+__global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double* __restrict__ geom,
+                                                       const int32_t* __restrict__ te,
+                                                       const int32_t* __restrict__ tf,
+                                                       const double2* __restrict__ e,
+                                                       const double2* __restrict__ b, double amp,
+                                                       double* __restrict__ coef) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double* G = geom + 12 * t;
   double g[4][3];
 #pragma unroll
   for (int k = 1; k < 4; k++)
@@ -87,41 +95,72 @@ __device__ void envelope_at(const DsArgs& A, int32_t T, double rx, double ry, do
     for (int a = 0; a < 3; a++) g[k][a] = G[3 * k + a];
 #pragma unroll
   for (int a = 0; a < 3; a++) g[0][a] = -(g[1][a] + g[2][a] + g[3][a]);
-  const double d[3] = {rx - G[0], ry - G[1], rz - G[2]};
-  double lam[4];
+  double o[20];
 #pragma unroll
-  for (int k = 1; k < 4; k++) lam[k] = g[k][0] * d[0] + g[k][1] * d[1] + g[k][2] * d[2];
-  lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+  for (int c = 0; c < 20; c++) o[c] = 0.0;
 #pragma unroll
-  for (int c = 0; c < 12; c++) out[c] = 0.0;
-#pragma unroll
-  for (int e = 0; e < 6; e++) {
-    const int i = le0(e), j = le1(e);
-    const double2 c = A.e[A.te[6 * (int64_t)T + e]];
+  for (int k = 0; k < 6; k++) {
+    const int i = le0(k), j = le1(k);
+    const double2 c = e[te[6 * t + k]];
+    double gji[3];
+    cross3(g[j], g[i], gji);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      const double w = lam[i] * g[j][a] - lam[j] * g[i][a];
-      out[a] += c.x * w;
-      out[3 + a] += c.y * w;
+      if (i == 0) {
+        o[a] += c.x * g[j][a];
+        o[10 + a] += c.y * g[j][a];
+      }
+      o[3 + a] += c.x * gji[a];
+      o[13 + a] += c.y * gji[a];
     }
   }
 #pragma unroll
   for (int f = 0; f < 4; f++) {
     const int i = lf(f, 0), j = lf(f, 1), k = lf(f, 2);
-    double cjk[3], cki[3], cij[3];
-    cross3(g[j], g[k], cjk);
-    cross3(g[k], g[i], cki);
-    cross3(g[i], g[j], cij);
-    const double2 c = A.b[A.tf[4 * (int64_t)T + f]];
+    const double2 c = b[tf[4 * t + f]];
+    double gjk[3];
+    cross3(g[j], g[k], gjk);
+    const double det = g[i][0] * gjk[0] + g[i][1] * gjk[1] + g[i][2] * gjk[2];
+    if (i == 0) {
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-      const double w = 2.0 * (lam[i] * cjk[a] + lam[j] * cki[a] + lam[k] * cij[a]);
-      out[6 + a] += c.x * w;
-      out[9 + a] += c.y * w;
+      for (int a = 0; a < 3; a++) {
+        o[6 + a] += 2.0 * c.x * gjk[a];
+        o[16 + a] += 2.0 * c.y * gjk[a];
+      }
     }
+    o[9] += 2.0 * c.x * det;
+    o[19] += 2.0 * c.y * det;
+  }
+  double2* out = reinterpret_cast<double2*>(coef + 20 * t);
+#pragma unroll
+  for (int c = 0; c < 10; c++) out[c] = make_double2(amp * o[2 * c], amp * o[2 * c + 1]);
+}
+
+// The envelope sample at r in tet T from the per-tet coefficients:
+// out[12] = Re E~, Im E~, Re B~, Im B~.
+__device__ __forceinline__ void envelope_at(const DsArgs& A, int32_t T, double rx, double ry, double rz,
+                                            double out[12]) {
+  const double* G = A.geom + 12 * (int64_t)T;
+  const double d[3] = {rx - __ldg(G), ry - __ldg(G + 1), rz - __ldg(G + 2)};
+  const double2* C = reinterpret_cast<const double2*>(A.coef + 20 * (int64_t)T);
+  double c[20];
+#pragma unroll
+  for (int i = 0; i < 10; i++) {
+    const double2 v = __ldg(C + i);
+    c[2 * i] = v.x;
+    c[2 * i + 1] = v.y;
   }
 #pragma unroll
-  for (int c = 0; c < 12; c++) out[c] *= A.amp;
+  for (int part = 0; part < 2; part++) {
+    const double* q = c + 10 * part;
+    double dw[3];
+    cross3(d, q + 3, dw);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      out[3 * part + a] = q[a] + dw[a];
+      out[6 + 3 * part + a] = q[6 + a] + q[9] * d[a];
+    }
+  }
 }
 
 // Before the env's step: the envelope sample at r^n, the velocity rule, the
@@ -305,6 +344,7 @@ struct fempic_downshift {
   double* geom = nullptr;
   int32_t* te = nullptr;
   int32_t* tf = nullptr;
+  double* coef = nullptr;       // [nt][20]
 };
 
 static void free_ds(fempic_downshift* d) {
@@ -312,6 +352,7 @@ static void free_ds(fempic_downshift* d) {
   cudaFree(d->geom);
   cudaFree(d->te);
   cudaFree(d->tf);
+  cudaFree(d->coef);
   delete d;
 }
 
@@ -335,7 +376,8 @@ extern "C" int fempic_downshift_create(const fempic_mesh_desc* mesh, fempic_down
   const size_t sg = sizeof(double) * 12 * (size_t)m.nt, se = sizeof(int32_t) * 6 * (size_t)m.nt,
                sf = sizeof(int32_t) * 4 * (size_t)m.nt;
   if (cudaMalloc(&d->geom, sg) != cudaSuccess || cudaMalloc(&d->te, se) != cudaSuccess ||
-      cudaMalloc(&d->tf, sf) != cudaSuccess) {
+      cudaMalloc(&d->tf, sf) != cudaSuccess ||
+      cudaMalloc(&d->coef, sizeof(double) * 20 * (size_t)m.nt) != cudaSuccess) {
     free_ds(d);
     cudaGetLastError();
     return fail(FEMPIC_ENOMEM, "downshift_create: device allocation");
@@ -400,14 +442,15 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
   A.h = hist->planes;
   A.nt = ds->nt;
   A.geom = ds->geom;
-  A.te = ds->te;
-  A.tf = ds->tf;
-  A.e = static_cast<const double2*>(envl->e_tilde);
-  A.b = static_cast<const double2*>(envl->b_tilde);
-  A.amp = envl->amp;
+  A.coef = ds->coef;
   A.start = start;
   compute_weights(t, dt, omega0, A.w);
   cudaStream_t st = (cudaStream_t)stream;
+  k_ds_field<<<blocks_for(ds->nt), kThreads, 0, st>>>(ds->nt, ds->geom, ds->te, ds->tf,
+                                                        static_cast<const double2*>(envl->e_tilde),
+                                                        static_cast<const double2*>(envl->b_tilde), envl->amp,
+                                                        ds->coef);
+  DS_CUDA(cudaGetLastError());
   k_ds_pre<<<blocks_for(p->n), kThreads, 0, st>>>(A);
   DS_CUDA(cudaGetLastError());
   // the AB4 segment: the env's own step under a zero field tracks, reflects
