@@ -1,7 +1,9 @@
 // Downshifted particle integrator of Sec. III-D on the FP64 form: the
 // velocity rule with the carrier integrated analytically (M and L weights)
-// and AB4 positions.  The AB4 segment is tracked and deposited by the env's
-// own FP64 step, run with a zero field, between the two kernels of this file.
+// and AB4 positions.  Per step: k_ds_field (per-tet envelope coefficients),
+// k_ds_pre (sample, velocity rule, AB4 velocity, history shift), the env's
+// own FP64 step under a zero field (tracking, walls, deposit of the AB4
+// segment), then k_ds_post (wall mirrors of the velocity history).
 #include <cuda_runtime.h>
 
 #include <cmath>
