@@ -61,6 +61,27 @@ def test_bench_line_has_the_contract_keys(monkeypatch):
     assert d["gpu_launches"] == sum(v["kernels"] for v in _fake_out(100)["mixed"]["prof"].values())
 
 
+def test_downshift_object_is_carried_when_measured(monkeypatch):
+    monkeypatch.setattr(bench, "issue_roofline", lambda *a: {"frac": 0.5})
+    args = argparse.Namespace(steps=10, warmup=3, workload="cube48", sort_every=4)
+    out = _fake_out(10)
+    out["downshift"] = {"value": 1.5e9, "unit": "particle-steps/s", "ms_per_step": 6.5}
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.report(args, 1, 10_000_000, out, None, None)
+    d = json.loads(buf.getvalue().strip())
+    assert d["downshift"] == out["downshift"] and "cpu_baseline" not in d
+
+
+def test_downshift_algorithmic_bytes():
+    counts = (117649, 795024, 1340928, 663552)
+    nn, ne, nf, nt = counts
+    b = bench.bytes_alg_per_step_downshift(10_000_000, counts)
+    # FP64 state (52 B) plus the history the rule needs: 3 past velocities
+    # (72 B) and 2 past complex E~, B~ samples (192 B), each read and written
+    assert b == 10_000_000 * 2 * (52 + 3 * 24 + 2 * 12 * 8) + 72 * nt + 24 * nn + 24 * ne + 16 * nf
+
+
 def test_algorithmic_bytes_per_step_match_the_stated_formula():
     counts = (117649, 795024, 1340928, 663552)
     nn, ne, nf, nt = counts
