@@ -84,8 +84,10 @@ int fempic_downshift_weights(double t, double dt, double omega0, double* w_out);
  * (added to, not cleared), the history shifted.  start = 1 fills the history
  * with this step's own values first (constant extrapolation backwards).
  * Velocities are v^n on entry and v^{n+1} on exit (not half steps).
- * Particles with tet < 0 keep their state.  Errors: EINVAL (NULL, sizes,
- * species, scalars), ECUDA, and any error of the env's step. */
+ * Particles with tet < 0 keep their state.  The per-tet coefficients live in
+ * ds, so steps of one ds that overlap on the GPU (different streams) race;
+ * give each concurrent particle set its own ds.  Errors: EINVAL (NULL,
+ * sizes, species, scalars), ECUDA, and any error of the env's step. */
 int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds, const fempic_particles* p,
                                const fempic_downshift_history* hist, const fempic_envelope* envl,
                                double omega0, double t, double dt, int32_t start, void* stream);
