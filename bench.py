@@ -320,63 +320,6 @@ def run_ours(args):
         out["fp64"] = f64
         f64["env"].close()
 
-    # The downshifted integrator (Sec. III-D: M/L velocity rule, AB4
-    # positions) on the FP64 form, device resident.  No re-sort: the history
-    # planes follow the particle order (the set is tet-sorted once, untimed).
-    if not args.no_downshift and args.workload == "cube48":
-        env_d = FempicEnv.from_mesh(mesh, precision=0)
-        st_d = particle_state(0)
-        env_d.locate(st_d)
-        env_d.sort(st_d, st_d.empty_like())
-        ds = Downshift(env_d, st_d.n)
-        e_d = torch.from_numpy(wl.e_tilde).to(torch.complex128).cuda()
-        b_d = torch.from_numpy(wl.b_tilde).to(torch.complex128).cuda()
-        dG_d = torch.zeros(env_d.n_edges, dtype=torch.float64, device="cuda")
-
-        def step_ds(n):
-            t = n * wl.dt
-            ds.step(st_d, e_d, b_d, wl.amp(t), wl.omega0, t, wl.dt)
-            env_d.deposit(wl.omega0, t + wl.dt, dG_out=dG_d if world > 1 else None)
-            if world > 1:
-                dist.all_reduce(dG_d)
-
-        for n in range(max(3, args.warmup)):
-            step_ds(n)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        env_d.profile(True)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for n in range(max(3, args.warmup), max(3, args.warmup) + args.steps):
-            step_ds(n)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        env_d.profile(False)
-        ms_d = ev0.elapsed_time(ev1)
-        if world > 1:
-            tt = torch.tensor([ms_d], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_d = float(tt.item())
-        pr = env_d.profile_read()
-        env_ms = pr["field"]["ms"] + pr["push"]["ms"]
-        counts_d = (env_d.n_nodes, env_d.n_edges, env_d.n_faces, env_d.n_tets)
-        b_ds = bytes_alg_per_step_downshift(n_p, counts_d)
-        t_step = ms_d / args.steps / 1e3
-        out["downshift"] = {
-            "value": n_p * world * args.steps / (ms_d / 1e3), "unit": "particle-steps/s",
-            "ms_per_step": ms_d / args.steps,
-            "env_step_ms_per_step": env_ms / args.steps,
-            "downshift_kernels_ms_per_step": (ms_d - env_ms - pr["finalize"]["ms"]) / args.steps,
-            "algorithmic_bytes_per_step": b_ds,
-            "hbm_frac_of_step": b_ds / t_step / 1e9 / measured_peaks()[0],
-            "what": "fempic_push_step_downshift (FP64): envelope samples + M/L velocity rule + AB4 "
-                    "(k_ds_pre), the env's FP64 step under a zero field for tracking/deposit, wall "
-                    "mirrors of the history (k_ds_post); no re-sort"}
-        ds.close()
-        env_d.close()
-        del st_d, ds
-
     # e2e through the public API with host buffers: per step, the envelope
     # DoFs arrive from pinned host memory (the field solver's output) and the
     # step's edge deposit dG goes back to pinned host memory.
@@ -462,6 +405,64 @@ def run_ours(args):
                        "Lagrange weights at each fine step (field step = 21 fine steps)"}
     mixed["levels3"] = lv3
     env.close()
+
+    # The downshifted integrator (Sec. III-D: M/L velocity rule, AB4
+    # positions) on the FP64 form, device resident, after the other legs.  No
+    # re-sort: the history planes follow the particle order (the set is
+    # tet-sorted once, untimed).
+    if not args.no_downshift and args.workload == "cube48":
+        env_d = FempicEnv.from_mesh(mesh, precision=0)
+        st_d = particle_state(0)
+        env_d.locate(st_d)
+        env_d.sort(st_d, st_d.empty_like())
+        ds = Downshift(env_d, st_d.n)
+        e_d = torch.from_numpy(wl.e_tilde).to(torch.complex128).cuda()
+        b_d = torch.from_numpy(wl.b_tilde).to(torch.complex128).cuda()
+        dG_d = torch.zeros(env_d.n_edges, dtype=torch.float64, device="cuda")
+
+        def step_ds(n):
+            t = n * wl.dt
+            ds.step(st_d, e_d, b_d, wl.amp(t), wl.omega0, t, wl.dt)
+            env_d.deposit(wl.omega0, t + wl.dt, dG_out=dG_d if world > 1 else None)
+            if world > 1:
+                dist.all_reduce(dG_d)
+
+        for n in range(max(3, args.warmup)):
+            step_ds(n)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        env_d.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for n in range(max(3, args.warmup), max(3, args.warmup) + args.steps):
+            step_ds(n)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        env_d.profile(False)
+        ms_d = ev0.elapsed_time(ev1)
+        if world > 1:
+            tt = torch.tensor([ms_d], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms_d = float(tt.item())
+        pr = env_d.profile_read()
+        env_ms = pr["field"]["ms"] + pr["push"]["ms"]
+        counts_d = (env_d.n_nodes, env_d.n_edges, env_d.n_faces, env_d.n_tets)
+        b_ds = bytes_alg_per_step_downshift(n_p, counts_d)
+        t_step = ms_d / args.steps / 1e3
+        out["downshift"] = {
+            "value": n_p * world * args.steps / (ms_d / 1e3), "unit": "particle-steps/s",
+            "ms_per_step": ms_d / args.steps,
+            "env_step_ms_per_step": env_ms / args.steps,
+            "downshift_kernels_ms_per_step": (ms_d - env_ms - pr["finalize"]["ms"]) / args.steps,
+            "algorithmic_bytes_per_step": b_ds,
+            "hbm_frac_of_step": b_ds / t_step / 1e9 / measured_peaks()[0],
+            "what": "fempic_push_step_downshift (FP64): envelope samples + M/L velocity rule + AB4 "
+                    "(k_ds_pre), the env's FP64 step under a zero field for tracking/deposit, wall "
+                    "mirrors of the history (k_ds_post); no re-sort"}
+        ds.close()
+        env_d.close()
+        del st_d, ds
 
     adj = None if (args.no_adjoint or args.workload != "cube48") else adjoint_window(rank)
     if rank == 0:
