@@ -333,6 +333,47 @@ def test_reflection_off_a_wall(cube4):
     np.testing.assert_allclose(om.edge_divergence(dG), rho1 - rho0, atol=1e-15 * abs(P.q[0] * P.w[0]))
 
 
+def test_segments_ending_on_a_face_do_not_ping_pong(cube4j):
+    """Segments from inside a tet to a point of one of its interior faces
+    (on the face up to rounding), field free.  Either end of the rounding is
+    correct, so each particle ends in that tet or in the neighbour across the
+    face after at most one crossing, at the segment's end.  The entry face of
+    the new tet is not a candidate exit (the tie rule): without it, a point
+    that both tets' barycentrics put outside bounces between them up to the
+    crossing cap."""
+    m, om = cube4j
+    tb = om.tables()
+    nb, tn = tb["tet_nbr"], tb["tet_nodes"]
+    rng = np.random.default_rng(5)
+    dt = 1e-9
+    xs, vs, home, other = [], [], [], []
+    for t in range(om.n_tets):
+        for k in range(4):
+            if nb[t, k] < 0:
+                continue
+            X = m.nodes[[tn[t, i] for i in range(4) if i != k]]
+            inner = m.nodes[tn[t]].mean(0)
+            for _ in range(4):
+                b = rng.dirichlet(np.ones(3)) @ X
+                a = b + (inner - b) * rng.uniform(0.05, 0.5)
+                xs.append(a); vs.append((b - a) / dt); home.append(t); other.append(nb[t, k])
+    xs, vs = np.array(xs), np.array(vs)
+    n = len(xs)
+    P = I.Particles(*(np.ascontiguousarray(c) for c in (xs[:, 0], xs[:, 1], xs[:, 2], vs[:, 0], vs[:, 1], vs[:, 2])),
+                    np.array([0, n], np.int64), np.array([-I.E_CHARGE]), np.array([I.M_ELECTRON]), np.array([1.0]))
+    tet, _ = om.locate(P.x, P.y, P.z)
+    assert np.array_equal(tet, home)
+    st = OracleState(P, tet)
+    dG = np.zeros(om.n_edges)
+    push_step(om, st, np.zeros(om.n_edges, complex), np.zeros(om.n_faces, complex), 1.0, 0.0, 0.0, dt, dG,
+              max_crossings=16)
+    assert (st.status == 0).all() and st.n_cross.max() <= 1
+    assert np.all((st.tet == home) | (st.tet == other))
+    assert (st.n_cross == 1).sum() > n // 10 and (st.n_cross == 0).sum() > n // 10
+    b = xs + dt * vs
+    np.testing.assert_allclose(np.stack([st.x, st.y, st.z], 1), b, rtol=0, atol=1e-15)
+
+
 def test_absorbing_wall_and_crossing_cap(cube4):
     m, om = cube4
     a = np.array([0.9, 0.37, 0.61]); v = np.array([2e8, 1e7, -3e7]); dt = 1e-9
