@@ -89,3 +89,31 @@ def test_missing_library_fails_loudly(tmp_path):
             capi.load(str(tmp_path / "nope.so"))
         finally:
             capi._lib = capi._lib_backup
+
+
+def _desc(nodes, tets):
+    nodes = np.ascontiguousarray(nodes, float)
+    tets = np.ascontiguousarray(tets, np.int32)
+    d = capi.fempic_mesh_desc(nodes.shape[0], tets.shape[0], nodes.ctypes.data, tets.ctypes.data,
+                              (C.c_double * 3)(0, 0, 0), (C.c_double * 3)(1, 1, 1))
+    return d, (nodes, tets)
+
+
+@pytest.mark.parametrize("what,nodes,tets,code,msg", [
+    ("zero volume", [[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], [[0, 1, 2, 3]], capi.FEMPIC_EMESH, "zero-volume"),
+    ("repeated node", [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], [[0, 0, 1, 2]], capi.FEMPIC_EMESH, "repeated"),
+    ("face in three tets", [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.2, 0.2, 1], [0.2, 0.2, -1], [0.3, 0.3, 0.5]],
+     [[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]], capi.FEMPIC_EMESH, "non-conforming"),
+    ("node id out of range", [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], [[0, 1, 2, 7]], None, "out of range"),
+])
+def test_bad_meshes_rejected_by_the_host_builder(lib, what, nodes, tets, code, msg):
+    """The library's host mesh builder (shared by fempic_env_create and
+    fempic_downshift_create) rejects degenerate and non-conforming meshes
+    with an error code and a message, before any device work."""
+    d, keep = _desc(nodes, tets)
+    h = C.c_void_p()
+    rc = lib.fempic_downshift_create(C.byref(d), C.byref(h))
+    assert rc != capi.FEMPIC_OK and not h.value, what
+    if code is not None:
+        assert rc == code, (what, rc)
+    assert msg in capi.fempic_downshift_last_error(), capi.fempic_downshift_last_error()

@@ -374,6 +374,45 @@ def test_segments_ending_on_a_face_do_not_ping_pong(cube4j):
     np.testing.assert_allclose(np.stack([st.x, st.y, st.z], 1), b, rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("nodes,tets,code", [
+    ([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], [[0, 1, 2, 3]], 2),                       # zero volume
+    ([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.2, 0.2, 1], [0.2, 0.2, -1], [0.3, 0.3, 0.5]],
+     [[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]], 3),                                          # face in 3 tets
+])
+def test_degenerate_and_nonconforming_meshes_rejected(nodes, tets, code):
+    with pytest.raises(ValueError, match=f"code {code}"):
+        OracleMesh(np.array(nodes, float), np.array(tets, np.int32))
+
+
+def test_boundary_face_inside_the_box_absorbs_in_reflect_mode():
+    """A mesh with a hole (one interior tet removed): the hole's faces are
+    boundary faces off the bounding-box planes, so a particle reaching one
+    is absorbed on it even with reflecting walls."""
+    m = I.kuhn_cube_mesh(4)
+    c_all = m.nodes[m.tets].mean(1)
+    hole = int(np.argmin(np.linalg.norm(c_all - 0.5 + 0.01, axis=1)))
+    tets = np.delete(m.tets, hole, axis=0)
+    om = OracleMesh(m.nodes, tets)
+    tb = om.tables()
+    assert (tb["tet_nbr"] == -7).sum() == 4
+    t_nb, k_nb = np.argwhere(tb["tet_nbr"] == -7)[0]
+    a = m.nodes[tb["tet_nodes"][t_nb]].mean(0)
+    face = m.nodes[[tb["tet_nodes"][t_nb][i] for i in range(4) if i != k_nb]].mean(0)
+    dt = 1e-9
+    v = 3.0 * (face - a) / dt                                        # well past the face, into the hole
+    P = I.Particles(np.array([a[0]]), np.array([a[1]]), np.array([a[2]]), np.array([v[0]]), np.array([v[1]]),
+                    np.array([v[2]]), np.array([0, 1], np.int64), np.array([-I.E_CHARGE]),
+                    np.array([I.M_ELECTRON]), np.array([1.0]))
+    tet, _ = om.locate(P.x, P.y, P.z)
+    assert tet[0] == t_nb
+    st = OracleState(P, tet)
+    push_step(om, st, np.zeros(om.n_edges, complex), np.zeros(om.n_faces, complex), 1.0, 0.0, 0.0, dt,
+              np.zeros(om.n_edges), wall_mode=0)
+    assert st.status[0] == 2 and st.tet[0] == -2 - t_nb
+    lam = om.bary(t_nb, np.array([st.x[0], st.y[0], st.z[0]]))
+    assert abs(lam[k_nb]) < 1e-14 and (lam > -1e-14).all()
+
+
 def test_absorbing_wall_and_crossing_cap(cube4):
     m, om = cube4
     a = np.array([0.9, 0.37, 0.61]); v = np.array([2e8, 1e7, -3e7]); dt = 1e-9
