@@ -87,7 +87,10 @@ int fempic_downshift_weights(double t, double dt, double omega0, double* w_out);
  * Particles with tet < 0 keep their state.  The per-tet coefficients live in
  * ds, so steps of one ds that overlap on the GPU (different streams) race;
  * give each concurrent particle set its own ds.  Errors: EINVAL (NULL,
- * sizes, species, scalars), ECUDA, and any error of the env's step. */
+ * sizes, species, scalars, an env not in the FP64 form), ECUDA, and any
+ * error of the env's step.  Every argument is checked on the host before
+ * the first launch, so an EINVAL leaves the particles and the history
+ * untouched. */
 int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds, const fempic_particles* p,
                                const fempic_downshift_history* hist, const fempic_envelope* envl,
                                double omega0, double t, double dt, int32_t start, void* stream);

@@ -53,12 +53,20 @@ extern "C" {
 #define FEMPIC_ECUDA (-2)    /* a CUDA runtime call failed */
 #define FEMPIC_EMESH (-3)    /* degenerate (zero-volume) or non-conforming mesh */
 #define FEMPIC_ENOMEM (-4)   /* host or device allocation failed */
+#define FEMPIC_EINCOMPLETE (-5) /* a step did not finish all its particles (fempic_error_count) */
 
 /* ---- precision forms ---- */
 #define FEMPIC_FP64 0   /* every step in FP64; velocities f64, DoFs complex128 */
-#define FEMPIC_MIXED 1  /* gather, carrier product and push in FP32; velocities f32,
-                           DoFs complex64; FP64 positions, exit parameter and
-                           crossing point; deposit exactly charge conserving */
+#define FEMPIC_MIXED 1  /* gather, carrier product and push in FP32 (velocities f32,
+                           DoFs complex64); positions and the position update in
+                           FP64; the deposit, the barycentrics of tracking, the exit
+                           parameter and the crossing barycentrics at FP64 accuracy
+                           (exact products and double-float, 48-bit significands)
+                           with FP64 crossing points and FP64 edge accumulation */
+#define FEMPIC_MIXED_Q24 2 /* as FEMPIC_MIXED, but tracking and deposit on 24-bit
+                           integer barycentrics: exit parameter in FP32, deposit
+                           exact in int64 at a resolution of 2^-24 of a tet (charge
+                           conserved exactly at that resolution) */
 
 /* ---- per-particle status (uint8) ---- */
 #define FEMPIC_P_OK 0
@@ -86,7 +94,7 @@ typedef struct {
 } fempic_mesh_desc;
 
 typedef struct {
-  int32_t precision;         /* FEMPIC_FP64 or FEMPIC_MIXED */
+  int32_t precision;         /* FEMPIC_FP64, FEMPIC_MIXED or FEMPIC_MIXED_Q24 */
   int32_t max_crossings;     /* face crossings allowed per particle per step, 0 .. 2^20 */
   int32_t wall_mode;         /* FEMPIC_WALL_REFLECT or FEMPIC_WALL_ABSORB */
   int32_t reserved;          /* must be 0 */
@@ -97,7 +105,7 @@ typedef struct {
   double* x;                 /* device f64 [n] positions (m) */
   double* y;
   double* z;
-  void* vx;                  /* device velocities (m/s): f64 [n] (FP64 form) or f32 [n] (mixed) */
+  void* vx;                  /* device velocities (m/s): f64 [n] (FP64 form) or f32 [n] (mixed forms) */
   void* vy;
   void* vz;
   int32_t* tet;              /* device i32 [n] current tet (see status convention) */
@@ -112,7 +120,7 @@ typedef struct {
 
 typedef struct {
   const void* e_tilde;       /* device complex [Ne] edge DoFs (interleaved re,im):
-                                complex128 (FP64 form) or complex64 (mixed) */
+                                complex128 (FP64 form) or complex64 (mixed forms) */
   const void* b_tilde;       /* device complex [Nf] face DoFs, same dtype */
   double amp;                /* host scalar: slow envelope amplitude a(t) at this step */
 } fempic_envelope;
@@ -223,6 +231,28 @@ int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, double* rho,
  * early, so any non-zero value means that step's results are incomplete.
  * Synchronizes the stream.  Errors: EINVAL, ECUDA. */
 int fempic_stats(fempic_env* env, int64_t* out4, void* stream);
+
+/* Error report of the steps since the last call (or since create), for
+ * callers of the asynchronous push step (Sec. III-D particle step; the paper
+ * has no error path).  Synchronizes `stream`, then sets *n_bad to the number
+ * of particles those steps froze (status CAP, ABSORBED, NONFINITE or LOST)
+ * and returns FEMPIC_OK, or FEMPIC_EINCOMPLETE when, in one of those steps, a
+ * CTA of the staged mixed push gave up its bounded wait (about 1 s) for a
+ * bulk copy: the particles of its remaining tiles were then not advanced and
+ * their deposit is missing, so the step must be redone from a saved state.
+ * fempic_stats keeps the cumulative counters.  Errors: EINVAL, ECUDA,
+ * EINCOMPLETE. */
+int fempic_error_count(fempic_env* env, int64_t* n_bad, void* stream);
+
+/* Test support for the bounded waits (no counterpart in the paper): in the
+ * next push step only, CTA `cta` of the staged mixed push kernel (if that
+ * launch has such a CTA) waits, after its first tile's copies have landed, on
+ * a barrier that no copy completes, with every bounded wait of that launch
+ * limited to limit_ns (1e3 .. 1e9).  The wait runs out, the CTA drains its
+ * copies in flight and stops, and fempic_error_count reports
+ * FEMPIC_EINCOMPLETE: the give-up path runs without any device fault.
+ * Host only.  Errors: EINVAL. */
+int fempic_debug_stall(fempic_env* env, int32_t cta, int64_t limit_ns);
 
 /* Reverse mode of one fempic_push_step (gradients of a loss of the particle
  * state after some steps, with respect to the envelope DoFs and the initial

@@ -18,8 +18,10 @@ FEMPIC_EINVAL = -1
 FEMPIC_ECUDA = -2
 FEMPIC_EMESH = -3
 FEMPIC_ENOMEM = -4
+FEMPIC_EINCOMPLETE = -5
 FEMPIC_FP64 = 0
 FEMPIC_MIXED = 1
+FEMPIC_MIXED_Q24 = 2
 FEMPIC_P_OK, FEMPIC_P_CAP, FEMPIC_P_ABSORBED, FEMPIC_P_NONFINITE, FEMPIC_P_LOST = range(5)
 FEMPIC_WALL_REFLECT = 0
 FEMPIC_WALL_ABSORB = 1
@@ -28,7 +30,7 @@ FEMPIC_WALL_ABSORB = 1
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step", "fempic_push_step3",
            "fempic_lagrange3",
            "fempic_deposit", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
-           "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
+           "fempic_error_count", "fempic_debug_stall", "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
            "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
 # Every function declared in include/fempic_downshift.h.
 DS_EXPORTS = ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift",
@@ -107,6 +109,8 @@ def load(path: str = LIB_PATH):
         lib.fempic_set_deposit.argtypes = [C.c_void_p, C.c_int32]
         lib.fempic_nodal_charge.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p, C.c_void_p]
         lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_error_count.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_debug_stall.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
         lib.fempic_push_step_adjoint.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles),
                                                  P(fempic_envelope), C.c_double, C.c_double, C.c_double,
                                                  P(fempic_adjoint), C.c_void_p, C.c_void_p, C.c_void_p]
@@ -202,6 +206,20 @@ def fempic_nodal_charge(env, parts: fempic_particles, rho, stream=0):
 
 def fempic_stats(env, out4, stream=0):
     check(load().fempic_stats(env, out4, stream), "fempic_stats")
+
+
+def fempic_error_count(env, stream=0) -> tuple:
+    """(return code, particles frozen since the last call); the code is
+    FEMPIC_OK or FEMPIC_EINCOMPLETE (any other code raises)."""
+    n = C.c_int64(0)
+    rc = load().fempic_error_count(env, C.byref(n), stream)
+    if rc not in (FEMPIC_OK, FEMPIC_EINCOMPLETE):
+        check(rc, "fempic_error_count")
+    return rc, n.value
+
+
+def fempic_debug_stall(env, cta: int, limit_ns: int):
+    check(load().fempic_debug_stall(env, int(cta), int(limit_ns)), "fempic_debug_stall")
 
 
 def fempic_push_step_adjoint(env, before: fempic_particles, after: fempic_particles, envl: fempic_envelope,

@@ -416,6 +416,14 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
       !std::isfinite(envl->amp))
     return fail(FEMPIC_EINVAL, "push_step_downshift: non-finite scalar or dt <= 0");
   if (start != 0 && start != 1) return fail(FEMPIC_EINVAL, "push_step_downshift: start must be 0 or 1");
+  if (fempic::env_precision(env) != FEMPIC_FP64)
+    return fail(FEMPIC_EINVAL, "push_step_downshift: the env must use the FP64 form (f64 velocities, "
+                               "complex128 DoFs)");
+  // the env step it runs checks its arguments only after this step has
+  // launched its own kernels: run those checks first, so that an error
+  // leaves the particles and the history untouched
+  if (fempic::validate_push_step(p, envl, omega0, t, dt) != FEMPIC_OK)
+    return fail(FEMPIC_EINVAL, std::string("push_step_downshift: ") + fempic_last_error());
   int64_t counts[4];
   if (fempic_env_query(env, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr) != FEMPIC_OK ||
       counts[3] != ds->nt || counts[1] != ds->ne || counts[2] != ds->nf)

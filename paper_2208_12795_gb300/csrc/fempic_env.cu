@@ -113,12 +113,19 @@ struct PushArgs {
   const int4* te;
   const void* field;
   double* dG;                   // FP64 form accumulator [Ne]
-  unsigned long long* dGq;      // mixed form: per (species, tet) slots of the 6 local edges,
+  unsigned long long* dGq;      // 24-bit form: per (species, tet) slots of the 6 local edges,
                                 // [ns][nt][8] int64 in units of 2^-48 (q w)
+  double* mom;                  // contract form: per (species, tet) moment slots [ns][nt][8]:
+                                // sum of D (3), sum of u x D (3), FP64
+  double* xhi;                  // contract form: crossing-pass edge deposits [ns][nt][8], FP64 part
+  float* xlo;                   // and their low FP32 parts [ns][nt][8]
+  const float4* tetdf;          // contract form: low FP32 parts of grad lambda_1..3, [nt][4] float4
   unsigned long long* stats;    // [0] crossings, [1] frozen, [2] staging wait timeouts
   CrossRec* xrec;               // mixed form: crossing records, 256-slot region per tile
   CrossRec64* xrec64;           // FP64 form: the same, FP64 records
   int32_t* xcount;              // mixed form: records per tile
+  unsigned long long wait_ns;   // limit of each bounded wait of the staged kernel
+  int32_t stall_cta;            // test support: this CTA waits on a barrier nothing completes (-1: none)
 };
 
 __device__ __forceinline__ int species_of(const Species& sp, int64_t p) {
@@ -636,21 +643,30 @@ __global__ void __launch_bounds__(kThreads) k_cross_fp64(PushArgs A, int64_t nti
 }
 
 // ------------------------------------------------------------ mixed push
-// FP32 gather, carrier product and Boris; FP64 positions.  Barycentrics for
-// tracking and deposit are FP32 values fixed to 24-bit integers Q with
-// Q_0 = 2^24 - Q_1 - Q_2 - Q_3, so sum(Q) = 2^24 exactly and the per-segment
-// deposit g_ij = Qa_i Qb_j - Qa_j Qb_i is exact in int64: its edge divergence
-// is exactly 2^24 (Qb - Qa) at the nodes, so charge is conserved exactly.
+// Two FP32-mixed forms share the per-tet record, the gather, the carrier
+// product and the Boris push in FP32 and keep positions in FP64:
 //
-// GB300 issues FP64 at 1/64 of the FP32 rate, so the only FP64 arithmetic on
-// the common path is the position update r + dt v.  r - x0 is formed in FP32
-// from an exact split of each FP64 coordinate into a 24-bit head and the
-// rest (integer bit operations), minus the tet origin held as an FP32 pair.
+//  * the contract form (FEMPIC_MIXED) keeps the quantities charge
+//    conservation and tracking rest on at FP64 accuracy: r - x0 is one FP64
+//    subtraction, the deposit of a particle that stays in its tet is the
+//    exact moment form (below), and the face walk computes barycentrics,
+//    exit parameters and crossing barycentrics in double-float (FP32 pairs,
+//    a 48-bit significand) with the crossing point itself in FP64;
+//  * the 24-bit form (FEMPIC_MIXED_Q24) fixes barycentrics to 24-bit integers
+//    Q with Q_0 = 2^24 - Q_1 - Q_2 - Q_3, so sum(Q) = 2^24 exactly and the
+//    per-segment deposit g_ij = Qa_i Qb_j - Qa_j Qb_i is exact in int64: its
+//    edge divergence is exactly 2^24 (Qb - Qa) at the nodes, and charge is
+//    conserved exactly at the resolution of the integers.
 //
-// Mixed per-tet record tetrec (8 x float4 = 128 B), first 64 B:
-//   (x0h.x, x0h.y, x0h.z, x0l.x), (x0l.y, x0l.z, g1.x, g1.y),
-//   (g1.z, g2.x, g2.y, g2.z), (g3.x, g3.y, g3.z, 0)
-// with x0 = x0h + x0l and g_k = grad lambda_k.
+// GB300 issues FP64 at 1/64 of the FP32 rate, so the common path's only FP64
+// arithmetic is r - x0 and the position update r + dt v.
+//
+// Mixed per-tet record tetrec (8 x float4 = 128 B):
+//   bytes   0-23  x0 (node 0 of the tet) as 3 x f64, exact
+//   bytes  24-59  grad lambda_1..3 in FP32 (9 floats)
+//   bytes  60-63  kappa: error bound of the FP32 inside test (contract form)
+//   bytes  64-103 the step's affine field (10 floats, k_field_f32)
+//   bytes 104-111 four 16-bit face maps;  bytes 112-127 neighbour ids
 struct FF {
   float hi, lo;
 };
@@ -672,8 +688,8 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 
 // r = hi + lo: hi keeps the leading 24 bits of the FP64 significand
 // (truncated, so exactly a float), lo the remaining 29 bits rounded to FP32.
-// |r| outside [2^-126, 2^128) maps to 0 (positions are never that small or
-// large; non-finite values are rejected before this is called).
+// |r| outside [2^-126, 2^128) maps to 0 (non-finite values are rejected
+// before this is called).
 __device__ __forceinline__ FF split_f64(double r) {
   const unsigned hi = (unsigned)__double2hiint(r), lo = (unsigned)__double2loint(r);
   const unsigned e = (hi >> 20) & 0x7ffu;
@@ -685,26 +701,41 @@ __device__ __forceinline__ FF split_f64(double r) {
   return FF{fhi, sign ? -flo : flo};
 }
 
-
 struct Geo32 {
-  float4 a, b, c, d;
+  double x0[3];
+  float g[9];    // grad lambda_1, _2, _3
+  float kappa;
 };
 
 __device__ __forceinline__ Geo32 ld_geo(const float4* __restrict__ rec, int64_t T) {
-  return Geo32{__ldg(rec + 8 * T), __ldg(rec + 8 * T + 1), __ldg(rec + 8 * T + 2), __ldg(rec + 8 * T + 3)};
+  const float4 a = __ldg(rec + 8 * T), b = __ldg(rec + 8 * T + 1), c = __ldg(rec + 8 * T + 2),
+               d = __ldg(rec + 8 * T + 3);
+  Geo32 G;
+  G.x0[0] = __hiloint2double(__float_as_int(a.y), __float_as_int(a.x));
+  G.x0[1] = __hiloint2double(__float_as_int(a.w), __float_as_int(a.z));
+  G.x0[2] = __hiloint2double(__float_as_int(b.y), __float_as_int(b.x));
+  G.g[0] = b.z; G.g[1] = b.w; G.g[2] = c.x;
+  G.g[3] = c.y; G.g[4] = c.z; G.g[5] = c.w;
+  G.g[6] = d.x; G.g[7] = d.y; G.g[8] = d.z;
+  G.kappa = d.w;
+  return G;
 }
 
-// d = r - x0 in FP32 from the split position and the split tet origin.
-__device__ __forceinline__ void dpos32(const Geo32& G, const FF r[3], float& dx, float& dy, float& dz) {
-  dx = __fadd_rn(__fsub_rn(r[0].hi, G.a.x), __fsub_rn(r[0].lo, G.a.w));
-  dy = __fadd_rn(__fsub_rn(r[1].hi, G.a.y), __fsub_rn(r[1].lo, G.b.x));
-  dz = __fadd_rn(__fsub_rn(r[2].hi, G.a.z), __fsub_rn(r[2].lo, G.b.y));
+// d = r - x0: one FP64 subtraction (exact for points in or near the tet,
+// whose coordinates are close to x0's), split into an FP32 pair d = hi + lo
+// (lo keeps d to 2^-48 relative), and rounded to FP32 in d32.
+__device__ __forceinline__ void dpos(const Geo32& G, double rx, double ry, double rz, FF dd[3], float d32[3]) {
+  dd[0] = split_f64(__dsub_rn(rx, G.x0[0]));
+  dd[1] = split_f64(__dsub_rn(ry, G.x0[1]));
+  dd[2] = split_f64(__dsub_rn(rz, G.x0[2]));
+#pragma unroll
+  for (int k = 0; k < 3; k++) d32[k] = __fadd_rn(dd[k].hi, dd[k].lo);
 }
 
-__device__ __forceinline__ void bary_q(const Geo32& G, float dx, float dy, float dz, int32_t Q[4]) {
-  const float l1 = __fmaf_rn(G.c.x, dz, __fmaf_rn(G.b.w, dy, __fmul_rn(G.b.z, dx)));
-  const float l2 = __fmaf_rn(G.c.w, dz, __fmaf_rn(G.c.z, dy, __fmul_rn(G.c.y, dx)));
-  const float l3 = __fmaf_rn(G.d.z, dz, __fmaf_rn(G.d.y, dy, __fmul_rn(G.d.x, dx)));
+__device__ __forceinline__ void bary_q(const Geo32& G, const float d[3], int32_t Q[4]) {
+  const float l1 = __fmaf_rn(G.g[2], d[2], __fmaf_rn(G.g[1], d[1], __fmul_rn(G.g[0], d[0])));
+  const float l2 = __fmaf_rn(G.g[5], d[2], __fmaf_rn(G.g[4], d[1], __fmul_rn(G.g[3], d[0])));
+  const float l3 = __fmaf_rn(G.g[8], d[2], __fmaf_rn(G.g[7], d[1], __fmul_rn(G.g[6], d[0])));
   // |lambda| <= 32 keeps Q_0 = 2^24 - Q_1 - Q_2 - Q_3 inside int32 for points
   // up to 32 tet diameters away (a clamped point still tracks cell by cell).
   Q[1] = __float2int_rn(__fmul_rn(fminf(fmaxf(l1, -kQClamp), kQClamp), kQScale));
@@ -718,10 +749,10 @@ __device__ __forceinline__ void bary_q(const Geo32& G, float dx, float dy, float
 __device__ __forceinline__ void bary_q_at(const float4* __restrict__ geo, int64_t T, const double r[3],
                                           int32_t Q[4]) {
   const Geo32 G = ld_geo(geo, T);
-  const FF s[3] = {split_f64(r[0]), split_f64(r[1]), split_f64(r[2])};
-  float dx, dy, dz;
-  dpos32(G, s, dx, dy, dz);
-  bary_q(G, dx, dy, dz, Q);
+  FF dd[3];
+  float d[3];
+  dpos(G, r[0], r[1], r[2], dd, d);
+  bary_q(G, d, Q);
 }
 
 __device__ __forceinline__ void gq(const int32_t a[4], const int32_t b[4], long long g[6]) {
@@ -789,22 +820,131 @@ __device__ __forceinline__ void crossing_q(const int32_t Qa[4], const int32_t Qb
     if (j == last) Qp[j] += kQOne - acc;
 }
 
-// Position after the push: the one FP64 operation of the common path.  Both
-// mixed kernels form it with this exact sequence, so the crossing kernel can
-// rebuild b from the stored start point and velocity bit for bit.
+// Position after the push: the one FP64 addition per coordinate of the
+// common path.  Every mixed kernel forms it with this exact sequence, so the
+// crossing kernels rebuild b from the stored start point and velocity bit
+// for bit.
 __device__ __forceinline__ double advance(double a, float dt32, float v) {
   return __dadd_rn(a, f32_to_f64(__fmul_rn(dt32, v)));
 }
 
+// ------------------------------------------------- double-float arithmetic
+// A value h + l held as an FP32 pair (|l| below an ulp of h): a 48-bit
+// significand at FP32 speed.  Built on the error-free transformations of
+// Knuth (two-sum), Dekker (fast two-sum, |a| >= |b|) and the fused
+// multiply-add product; the _rn intrinsics keep the compiler from
+// contracting or reassociating the error terms away.
+struct DF {
+  float h, l;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return DF{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.h, -a.l}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const DF p = two_prod(a.h, b.h);
+  return fast_two_sum(p.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const DF p = two_prod(q1, b.h);
+  // remainder a - q1 b, to first order in the low parts
+  const float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.h, p.h), p.l), a.l), __fmul_rn(q1, b.l));
+  return fast_two_sum(q1, __fdiv_rn(r, b.h));
+}
+__device__ __forceinline__ bool df_lt(DF a, DF b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+__device__ __forceinline__ DF df_dot3(const DF a[3], const DF b[3]) {
+  return df_add(df_add(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+}
+// FP64 value of h + l; the FP64 addition is exact (the pair spans at most
+// 48 bits).
+__device__ __forceinline__ double df_to_f64(DF a) { return __dadd_rn(f32_to_f64(a.h), f32_to_f64(a.l)); }
+__device__ __forceinline__ DF f64_to_df(double r) {
+  const FF s = split_f64(r);
+  return DF{s.hi, s.lo};
+}
+
+// ------------------------------------------------- contract-form deposit
+// Moment form of the exact path integral of a straight segment a -> b that
+// stays in one tet (Sec. III-D eq. G_integral with the Whitney-1 functions
+// of Sec. III-A).  With u = a - x0 and D = b - a, lambda is affine, so
+//   g_ij = lambda_i(a) lambda_j(b) - lambda_j(a) lambda_i(b)
+//        = [i = 0] (G_j . D) + (G_i x G_j) . (u x D)      (G_k = grad lambda_k)
+// (Binet-Cauchy).  Per particle only D and the moment u x D are needed, in
+// physical units: D is exactly the FP32 displacement dt v of the mixed
+// position update, u is exact from the FP64 subtraction, and u x D is
+// formed as an FP32 pair from exact products.  The gradients enter once per
+// tet per step, in double-float, in k_tet_finalize: FP64 accuracy without
+// FP64 arithmetic per particle.
+//
+// Warp reduction: the 6 values of each lane (D and u x D) are scaled to
+// integers by a quantum common to the warp (2^-50 of the warp's largest
+// |D|, resp. |u x D|), summed exactly over runs of equal (tet, species)
+// like the 24-bit form's integers, and the run head adds the sums, as FP64,
+// to the tet's moment slot with FP64 atomics.
+
+// x / 2^(emax - 177) as an integer (rounded), emax the biased exponent of
+// the warp's largest |x|: |result| < 2^51, so 32 lanes sum below 2^56.
+__device__ __forceinline__ long long fx_scaled(float x, unsigned emax) {
+  const unsigned u = __float_as_uint(x);
+  const int ex = (int)((u >> 23) & 0xffu);
+  if (ex == 0) return 0;   // zero or below 2^-126
+  const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
+  const int sh = ex - (int)emax + 27;
+  long long v = 0;
+  if (sh >= 0)
+    v = m << sh;
+  else if (sh > -25)
+    v = (m + (1ll << (-sh - 1))) >> (-sh);
+  return (u >> 31) ? -v : v;
+}
+
+// v 2^e2 as a double, rounded to nearest (ties up), with integer operations
+// only; |v| < 2^62.
+__device__ __forceinline__ double i64_to_f64(long long v, int e2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  a <<= lz;                                          // leading one at bit 63
+  unsigned long long mant = (a >> 11) + ((a >> 10) & 1ull);
+  int e = 63 - lz + e2;
+  if (mant >> 53) {
+    mant >>= 1;
+    e++;
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) |
+                                          (mant & 0xfffffffffffffull)));
+}
+
+__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
 // Per-lane result of the common path, consumed by the warp epilogue.
 struct LaneOut {
-  long long gh[6];     // one-segment deposit (home tet)
+  long long gh[6];     // 24-bit form: one-segment deposit (home tet), int64
+  float mv[9];         // contract form: D (3), u x D as pairs (hi 3, lo 3)
   int32_t key;         // (home tet, species) run key; negative = no deposit
   int32_t Thome;
   int shome;
-  bool queue;          // leaves its tet: tracked in the CTA's crossing phase
+  bool queue;          // leaves its tet (or may): tracked by the crossing pass
   unsigned nfrz;
-  double a[3];         // start point and new velocity of a leaving particle
+  double a[3];         // start point and new velocity of a queued particle
   float v[3];
   int32_t T;
 };
@@ -816,6 +956,8 @@ struct CrossList {
 __device__ __forceinline__ void lane_init(LaneOut& o, int lane) {
 #pragma unroll
   for (int e = 0; e < 6; e++) o.gh[e] = 0;
+#pragma unroll
+  for (int e = 0; e < 9; e++) o.mv[e] = 0.f;
   o.key = -1 - lane;
   o.Thome = 0;
   o.shome = 0;
@@ -824,11 +966,16 @@ __device__ __forceinline__ void lane_init(LaneOut& o, int lane) {
 }
 
 // Common path of one particle with its state already loaded: gather, carrier,
-// Boris, position update and the barycentric integers of both ends in the
-// home tet.  A particle that stays in its tet writes its new state and keeps
-// its one-segment deposit for the warp reduction; a particle that leaves it
-// stores its new velocity and hands (start point, velocity, tet) to the
-// CTA's crossing list.
+// Boris, position update, then the inside test of the end point in the home
+// tet.  A particle that stays in its tet writes its new state and keeps its
+// one-segment deposit for the warp reduction; any other hands (start point,
+// velocity, tet) to the CTA's crossing list.
+//   24-bit form: inside = all four integer barycentrics of b >= 0.
+//   contract form: inside = all four FP32 barycentrics of b >= kappa, the
+//   tet's bound on their error, so that the FP64 barycentrics are >= 0 too;
+//   a particle within kappa of a face goes to the crossing pass, which
+//   decides in double-float.
+template <bool Q24>
 __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int32_t T, double ax, double ay,
                                                double az, float v0, float v1, float v2, LaneOut& o) {
   if (T >= A.nt) {
@@ -841,16 +988,16 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   const int s = species_of(A.sp, p);
   const float kq = (float)A.sp.kq[s];
   const float4* R = A.tetrec + 8 * (int64_t)T;
-  const Geo32 G = Geo32{__ldg(R), __ldg(R + 1), __ldg(R + 2), __ldg(R + 3)};
+  const Geo32 G = ld_geo(A.tetrec, T);
   const float4 f0 = __ldg(R + 4), f1 = __ldg(R + 5), f2 = __ldg(R + 6);
-  const FF rs[3] = {split_f64(ax), split_f64(ay), split_f64(az)};
-  float dx, dy, dz;
-  dpos32(G, rs, dx, dy, dz);
+  FF dd[3];
+  float d[3];
+  dpos(G, ax, ay, az, dd, d);
   // f0 = (E0x, E0y, E0z, Wx), f1 = (Wy, Wz, B0x, B0y), f2 = (B0z, beta, -, -)
-  const float Ex = f0.x + (dy * f1.y - dz * f1.x);
-  const float Ey = f0.y + (dz * f0.w - dx * f1.y);
-  const float Ez = f0.z + (dx * f1.x - dy * f0.w);
-  const float Bx = f1.z + f2.y * dx, By = f1.w + f2.y * dy, Bz = f2.x + f2.y * dz;
+  const float Ex = f0.x + (d[1] * f1.y - d[2] * f1.x);
+  const float Ey = f0.y + (d[2] * f0.w - d[0] * f1.y);
+  const float Ez = f0.z + (d[0] * f1.x - d[1] * f0.w);
+  const float Bx = f1.z + f2.y * d[0], By = f1.w + f2.y * d[1], Bz = f2.x + f2.y * d[2];
   const float vmx = v0 + kq * Ex, vmy = v1 + kq * Ey, vmz = v2 + kq * Ez;
   const float tx = kq * Bx, ty = kq * By, tz = kq * Bz;
   const float t2 = tx * tx + ty * ty + tz * tz;
@@ -863,7 +1010,10 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   const float vn1 = vmy + (vpz * sx - vpx * sz) + kq * Ey;
   const float vn2 = vmz + (vpx * sy - vpy * sx) + kq * Ez;
   const float dt32 = (float)A.dt;
-  const double b0 = advance(ax, dt32, vn0), b1 = advance(ay, dt32, vn1), b2 = advance(az, dt32, vn2);
+  // the FP32 displacement and the FP64 position update (advance's sequence)
+  const float D0 = __fmul_rn(dt32, vn0), D1 = __fmul_rn(dt32, vn1), D2 = __fmul_rn(dt32, vn2);
+  const double b0 = __dadd_rn(ax, f32_to_f64(D0)), b1 = __dadd_rn(ay, f32_to_f64(D1)),
+               b2 = __dadd_rn(az, f32_to_f64(D2));
   if (!(isfinite(vn0) && isfinite(vn1) && isfinite(vn2) && finite_bits(b0) && finite_bits(b1) && finite_bits(b2))) {
     A.status[p] = FEMPIC_P_NONFINITE;
     A.tet[p] = -2 - T;
@@ -871,12 +1021,23 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
     return;
   }
   int32_t Qa[4], Qb[4];
-  bary_q(G, dx, dy, dz, Qa);
-  const FF bs[3] = {split_f64(b0), split_f64(b1), split_f64(b2)};
-  float bx, by, bz;
-  dpos32(G, bs, bx, by, bz);
-  bary_q(G, bx, by, bz, Qb);
-  // Every lane stores its full new state, a leaving particle included (its b
+  bool inside;
+  if (Q24) {
+    bary_q(G, d, Qa);
+    FF bd[3];
+    float db[3];
+    dpos(G, b0, b1, b2, bd, db);
+    bary_q(G, db, Qb);
+    inside = (Qb[0] | Qb[1] | Qb[2] | Qb[3]) >= 0;
+  } else {
+    const float e0 = __fadd_rn(d[0], D0), e1 = __fadd_rn(d[1], D1), e2 = __fadd_rn(d[2], D2);
+    const float l1 = __fmaf_rn(G.g[2], e2, __fmaf_rn(G.g[1], e1, __fmul_rn(G.g[0], e0)));
+    const float l2 = __fmaf_rn(G.g[5], e2, __fmaf_rn(G.g[4], e1, __fmul_rn(G.g[3], e0)));
+    const float l3 = __fmaf_rn(G.g[8], e2, __fmaf_rn(G.g[7], e1, __fmul_rn(G.g[6], e0)));
+    const float l0 = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, l1), l2), l3);
+    inside = fminf(fminf(l0, l1), fminf(l2, l3)) >= G.kappa;
+  }
+  // Every lane stores its full new state, a queued particle included (its b
   // is final unless it reflects or freezes), so the warp's stores cover whole
   // sectors and the crossing kernel rarely rewrites positions.
   static_cast<float*>(A.vx)[p] = vn0;
@@ -885,10 +1046,10 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   A.x[p] = b0;
   A.y[p] = b1;
   A.z[p] = b2;
-  if ((Qb[0] | Qb[1] | Qb[2] | Qb[3]) < 0) {
-    // leaves its tet: the crossing pass deposits all its pieces (doing the
-    // home piece here instead measured slower: the divergent exit search
-    // costs the common path more than the crossing pass saves)
+  if (!inside) {
+    // the crossing pass deposits all its pieces (doing the home piece here
+    // instead measured slower: the divergent exit search costs the common
+    // path more than the crossing pass saves)
     o.queue = true;
     o.a[0] = ax;
     o.a[1] = ay;
@@ -899,17 +1060,34 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
     o.T = T;
     return;
   }
-  gq(Qa, Qb, o.gh);
+  if (Q24) {
+    gq(Qa, Qb, o.gh);
+  } else {
+    // u x D as FP32 pairs: exact products of the high parts, first-order low parts
+    const float D[3] = {D0, D1, D2};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const int i = (k + 1) % 3, j = (k + 2) % 3;   // (u x D)_k = u_i D_j - u_j D_i
+      const DF p1 = two_prod(dd[i].hi, D[j]), p2 = two_prod(dd[j].hi, D[i]);
+      const DF sd = two_sum(p1.h, -p2.h);
+      o.mv[3 + k] = sd.h;
+      o.mv[6 + k] = __fmaf_rn(dd[i].lo, D[j], __fmaf_rn(-dd[j].lo, D[i], __fadd_rn(sd.l, __fsub_rn(p1.l, p2.l))));
+      o.mv[k] = D[k];
+    }
+  }
   o.key = T * kMaxSpecies + s;
   o.Thome = T;
   o.shome = s;
 }
 
-// Warp epilogue (all 32 lanes): append the lanes that leave their tet to the
-// CTA's crossing list (one shared-memory atomic per warp), reduce the
-// one-segment deposits over runs of equal (tet, species)
-// keys (particles are sorted by tet, so neighbouring lanes usually share
-// one), and flush one int64 atomic per edge and run.
+// Warp epilogue (all 32 lanes): append the queued lanes to the CTA's
+// crossing list (one shared-memory atomic per warp), reduce the one-segment
+// deposits over runs of equal (tet, species) keys (particles are sorted by
+// tet, so neighbouring lanes usually share one), and flush them from the run
+// head: int64 atomics into the tet's integer slot (24-bit form), or FP64
+// atomics of the exactly summed moments into the tet's moment slot
+// (contract form).
+template <bool Q24>
 __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p, int lane, LaneOut& o,
                                                     CrossList& cl) {
   const unsigned full = 0xffffffffu;
@@ -930,7 +1108,24 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
       r.p = (int32_t)p;
     }
   }
-  if (A.dGq) {   // deposits on (kernel parameter: the same branch for every lane)
+  const bool dep_on = Q24 ? (A.dGq != nullptr) : (A.mom != nullptr);
+  if (dep_on) {   // deposits on (kernel parameter: the same branch for every lane)
+    unsigned eD = 0u, eM = 0u;
+    if (!Q24) {
+      // the warp's quanta, then every lane's values as integers
+      unsigned uD = 0u, uM = 0u;
+      if (o.key >= 0) {
+        uD = max(max(abs_bits(o.mv[0]), abs_bits(o.mv[1])), abs_bits(o.mv[2]));
+        uM = max(max(abs_bits(o.mv[3]), abs_bits(o.mv[4])), abs_bits(o.mv[5]));
+      }
+      eD = __reduce_max_sync(full, uD) >> 23;
+      eM = __reduce_max_sync(full, uM) >> 23;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        o.gh[k] = fx_scaled(o.mv[k], eD);
+        o.gh[3 + k] = fx_scaled(o.mv[3 + k], eM) + fx_scaled(o.mv[6 + k], eM);
+      }
+    }
     const int32_t prev = __shfl_up_sync(full, o.key, 1);
     const bool head = lane == 0 || prev != o.key;
     const unsigned heads = __ballot_sync(full, head);
@@ -945,10 +1140,17 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
       }
     }
     if (head && o.key >= 0) {
-      unsigned long long* base = tet_slot(A, o.shome, o.Thome);
+      if (Q24) {
+        unsigned long long* base = A.dGq + ((int64_t)o.shome * A.nt + o.Thome) * 8;
 #pragma unroll
-      for (int e = 0; e < 6; e++)
-        if (o.gh[e]) atomicAdd(base + e, (unsigned long long)o.gh[e]);
+        for (int e = 0; e < 6; e++)
+          if (o.gh[e]) atomicAdd(base + e, (unsigned long long)o.gh[e]);
+      } else {
+        double* base = A.mom + ((int64_t)o.shome * A.nt + o.Thome) * 8;
+#pragma unroll
+        for (int e = 0; e < 6; e++)
+          if (o.gh[e]) atomicAdd(base + e, i64_to_f64(o.gh[e], (int)(e < 3 ? eD : eM) - 177));
+      }
     }
   }
   const unsigned nf = __reduce_add_sync(full, o.nfrz);
@@ -968,6 +1170,7 @@ __device__ __forceinline__ void publish_tile(const PushArgs& A, CrossList& cl, i
 // Common path, one particle per thread, state read straight from global
 // memory.  Used when the particle arrays are not 16-byte aligned (so bulk
 // copies cannot stage them) and for a ragged last tile.
+template <bool Q24>
 __global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A, int64_t p0) {
   __shared__ CrossList cl;
   const int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -982,12 +1185,12 @@ __global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A, int64_t p0)
       const float* vx = static_cast<const float*>(A.vx);
       const float* vy = static_cast<const float*>(A.vy);
       const float* vz = static_cast<const float*>(A.vz);
-      mixed_particle(A, p, T, A.x[p], A.y[p], A.z[p], vx[p], vy[p], vz[p], o);
+      mixed_particle<Q24>(A, p, T, A.x[p], A.y[p], A.z[p], vx[p], vy[p], vz[p], o);
     } else {
-      mixed_particle(A, p, T, 0.0, 0.0, 0.0, 0.f, 0.f, 0.f, o);
+      mixed_particle<Q24>(A, p, T, 0.0, 0.0, 0.0, 0.f, 0.f, 0.f, o);
     }
   }
-  mixed_warp_epilogue(A, p, lane, o, cl);
+  mixed_warp_epilogue<Q24>(A, p, lane, o, cl);
   publish_tile(A, cl, (p0 >> 8) + blockIdx.x);
 }
 
@@ -998,8 +1201,9 @@ __global__ void __launch_bounds__(kThreads) k_push_mixed(PushArgs A, int64_t p0)
 // mbarrier, in a ring of three stages filled two tiles ahead, so HBM latency
 // overlaps the arithmetic.  A stage is refilled only after the iteration
 // that read it has finished on every thread.
-// Every wait is bounded by the global timer (about 1 s); a CTA that times
-// out records it in stats[2], drains the copies it issued, and stops.
+// Every wait is bounded by the global timer (about 1 s by default); a CTA
+// that times out records it in stats[2], drains the copies it issued, and
+// stops.
 constexpr int kTile = kThreads;
 constexpr int kStageBytes = kTile * (3 * 8 + 3 * 4 + 4);   // 10240
 constexpr int kStages = 3;
@@ -1046,12 +1250,12 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false after about one second.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait for phase `parity` of `bar`; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
   if (mbar_test(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_test(bar, parity)) {
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -1074,13 +1278,16 @@ __device__ __forceinline__ void stage_tile(const PushArgs& A, unsigned char* sta
 #ifndef FEMPIC_TMA_MIN_BLOCKS
 #define FEMPIC_TMA_MIN_BLOCKS 3
 #endif
+template <bool Q24>
 __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_tma(PushArgs A, int64_t ntiles) {
   __shared__ __align__(128) unsigned char smem[kStages][kStageBytes];
-  __shared__ __align__(8) uint64_t bar[kStages];
+  // bar[kStages] is test support: a barrier no copy ever completes, for the
+  // CTA that fempic_debug_stall names
+  __shared__ __align__(8) uint64_t bar[kStages + 1];
   __shared__ CrossList cl;
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) {
-    for (int k = 0; k < kStages; k++) mbar_init(&bar[k], 1);
+    for (int k = 0; k <= kStages; k++) mbar_init(&bar[k], 1);
     mbar_fence_init();
     cl.total = 0;
   }
@@ -1097,7 +1304,8 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_
     // this barrier; the proxy fence orders those shared-memory reads before
     // the bulk copy that refills that stage below.
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const bool ok = mbar_wait_bounded(&bar[st], (phase >> st) & 1u);
+    bool ok = mbar_wait_bounded(&bar[st], (phase >> st) & 1u, A.wait_ns);
+    if (it == 0 && (int)blockIdx.x == A.stall_cta) ok = ok && mbar_wait_bounded(&bar[kStages], 0u, A.wait_ns);
     if (__syncthreads_or(!ok)) {
       // give up: record it, wait (bounded) for this CTA's copies still in
       // flight (stages of tiles it .. it+kStages-1 not yet consumed), stop
@@ -1106,7 +1314,7 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_
         for (int64_t t = tile; t < ntiles; t += stride) A.xcount[t] = 0;   // no stale records
         for (int k = 0; k < kStages; k++) {
           const int sk = (st + k) % kStages;
-          if (tile + k * stride < ntiles) mbar_wait_bounded(&bar[sk], (phase >> sk) & 1u);
+          if (tile + k * stride < ntiles) mbar_wait_bounded(&bar[sk], (phase >> sk) & 1u, A.wait_ns);
         }
       }
       return;
@@ -1128,8 +1336,8 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_
     const int64_t p = tile * kTile + tid;
     LaneOut o;
     lane_init(o, lane);
-    mixed_particle(A, p, T, ax, ay, az, v0, v1, v2, o);
-    mixed_warp_epilogue(A, p, lane, o, cl);
+    mixed_particle<Q24>(A, p, T, ax, ay, az, v0, v1, v2, o);
+    mixed_warp_epilogue<Q24>(A, p, lane, o, cl);
     publish_tile(A, cl, tile);
     st = (st + 1) % kStages;
   }
@@ -1141,7 +1349,6 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_
 // came in through.
 struct CrossState {
   double a0[3], b[3];
-  FF bs[3];
   float vn[3];
   int32_t Qa[4], Qb[4];
   int32_t T, p;
@@ -1163,7 +1370,6 @@ __device__ __forceinline__ void cross_begin(const PushArgs& A, const CrossRec& r
     c.a0[k] = r.a[k];
     c.vn[k] = r.v[k];
     c.b[k] = advance(r.a[k], dt32, r.v[k]);
-    c.bs[k] = split_f64(c.b[k]);
   }
   c.entry = -1;
   c.nc = 0;
@@ -1182,14 +1388,14 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c, 
     // fresh particle also needs its start point's (every busy lane runs this
     // body together, only the start point is particular to fresh lanes)
     const Geo32 G = ld_geo(A.tetrec, c.T);
-    float dx, dy, dz;
+    FF dd[3];
+    float d[3];
     if (fresh) {
-      const FF rs[3] = {split_f64(c.a0[0]), split_f64(c.a0[1]), split_f64(c.a0[2])};
-      dpos32(G, rs, dx, dy, dz);
-      bary_q(G, dx, dy, dz, c.Qa);
+      dpos(G, c.a0[0], c.a0[1], c.a0[2], dd, d);
+      bary_q(G, d, c.Qa);
     }
-    dpos32(G, c.bs, dx, dy, dz);
-    bary_q(G, dx, dy, dz, c.Qb);
+    dpos(G, c.b[0], c.b[1], c.b[2], dd, d);
+    bary_q(G, d, c.Qb);
   }
   float smin;
   const int kx = exit_face(c.Qa, c.Qb, c.entry, smin);
@@ -1249,7 +1455,6 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c, 
         const double L = side ? A.hi[k] : A.lo[k];
         c.b[k] = 2.0 * L - c.b[k];
         c.vn[k] = -c.vn[k];
-        c.bs[k] = split_f64(c.b[k]);
       }
     c.reflected = true;
 #pragma unroll
@@ -1307,7 +1512,7 @@ __device__ __forceinline__ void cross_finish(const PushArgs& A, const CrossState
   ncr += (unsigned)c.nc;
 }
 
-// Crossing pass of the mixed form: one warp per 256-particle tile region of
+// Crossing pass of the 24-bit form: one warp per 256-particle tile region of
 // the record queue.  Each loop iteration advances every busy lane by one
 // face; a lane whose particle is done takes the tile's next record, so a
 // particle that crosses many faces (a fast beam particle) does not hold 31
@@ -1315,7 +1520,7 @@ __device__ __forceinline__ void cross_finish(const PushArgs& A, const CrossState
 // warp's tet records and deposit slots stay in cache.
 constexpr int kCrossWarpsPerSm = 64;
 
-__global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t ntiles) {
+__global__ void __launch_bounds__(kThreads) k_cross_q24(PushArgs A, int64_t ntiles) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -1356,17 +1561,358 @@ __global__ void __launch_bounds__(kThreads) k_cross_mixed(PushArgs A, int64_t nt
   }
 }
 
+// ------------------------------------------- contract-form crossing pass
+// The walk of the FP64 oracle (exit face = argmin over the faces with
+// lambda_k(b) < 0, entry face excluded, of s_k = lambda_k(a) / (lambda_k(a) -
+// lambda_k(b)) clamped at 0, lowest k on ties; crossing barycentrics
+// lambda(a) + s (lambda(b) - lambda(a)) with 0 on the exit face; the shared
+// nodes' values carried into the neighbour) with every barycentric, every
+// exit parameter and every crossing barycentric in double-float, and the
+// in-tet pieces deposited in edge form, g_ij = la_i lb_j - la_j lb_i (Sec. II
+// eq. g_def), as FP64 atomics of the high parts and FP32 atomics of the low
+// parts.  The crossing point itself is FP64 where it is stored (a wall
+// reflection, a frozen particle).  GB300 runs FP64 at 1/64 of the FP32 rate,
+// so the pass does in FP32 pairs what would otherwise be FP64-pipe bound.
+struct CrossStateDF {
+  double a0[3], b[3];   // the current straight run goes from a0 to b ...
+  DF S;                 // ... and the current piece starts at a0 + S (b - a0)
+  DF la[4];             // barycentrics of the piece start in T
+  float vn[3];
+  int32_t T, p;
+  int entry, nc, s;
+  uint8_t st;
+  bool moved, reflected;
+};
+
+// lambda(r) in tet T in double-float: d = r - x0 exact in FP64 and split into
+// FP32 pairs, lambda_k = (G_k,hi + G_k,lo) . d for k = 1..3 from exact
+// products of the high parts, lambda_0 = 1 - lambda_1 - lambda_2 - lambda_3.
+__device__ __forceinline__ void lambda_df(const Geo32& G, const float glo[9], const double r[3], DF lam[4]) {
+  FF dd[3];
+  float d32[3];
+  dpos(G, r[0], r[1], r[2], dd, d32);
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const float* gh = G.g + 3 * k;
+    const float* gl = glo + 3 * k;
+    const DF p0 = two_prod(gh[0], dd[0].hi), p1 = two_prod(gh[1], dd[1].hi), p2 = two_prod(gh[2], dd[2].hi);
+    const DF s1 = two_sum(p0.h, p1.h);
+    const DF s2 = two_sum(s1.h, p2.h);
+    float err = __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(p0.l, p1.l), p2.l));
+#pragma unroll
+    for (int j = 0; j < 3; j++) err = __fmaf_rn(gh[j], dd[j].lo, __fmaf_rn(gl[j], dd[j].hi, err));
+    lam[k + 1] = fast_two_sum(s2.h, err);
+  }
+  lam[0] = df_sub(DF{1.0f, 0.0f}, df_add(df_add(lam[1], lam[2]), lam[3]));
+}
+
+__device__ __forceinline__ void ld_glo(const float4* __restrict__ tetdf, int64_t T, float glo[9]) {
+  const float4 a = __ldg(tetdf + 4 * T), b = __ldg(tetdf + 4 * T + 1), c = __ldg(tetdf + 4 * T + 2);
+  glo[0] = a.x; glo[1] = a.y; glo[2] = a.z; glo[3] = a.w;
+  glo[4] = b.x; glo[5] = b.y; glo[6] = b.z; glo[7] = b.w;
+  glo[8] = c.x;
+}
+
+// Edge-form deposit of the piece la -> lb in tet T (species s).
+__device__ __forceinline__ void deposit_df(const PushArgs& A, int32_t T, int s, const DF la[4], const DF lb[4]) {
+  if (!A.xhi) return;   // deposits off
+  const int64_t slot = ((int64_t)s * A.nt + T) * 8;
+  float lo[6];
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const int i = le0(e), j = le1(e);
+    const DF g = df_sub(df_mul(la[i], lb[j]), df_mul(la[j], lb[i]));
+    atomicAdd(A.xhi + slot + e, f32_to_f64(g.h));
+    lo[e] = g.l;
+  }
+  atomicAdd(reinterpret_cast<float4*>(A.xlo + slot), make_float4(lo[0], lo[1], lo[2], lo[3]));
+  atomicAdd(reinterpret_cast<float2*>(A.xlo + slot + 4), make_float2(lo[4], lo[5]));
+}
+
+__device__ __forceinline__ void cross_begin_df(const PushArgs& A, const CrossRec& r, CrossStateDF& c) {
+  c.p = r.p;
+  c.T = r.T;
+  c.s = species_of(A.sp, r.p);
+  const float dt32 = (float)A.dt;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    c.a0[k] = r.a[k];
+    c.vn[k] = r.v[k];
+    c.b[k] = advance(r.a[k], dt32, r.v[k]);
+  }
+  c.S = DF{0.f, 0.f};
+  c.entry = -1;
+  c.nc = 0;
+  c.st = FEMPIC_P_OK;
+  c.moved = true;
+  c.reflected = false;
+}
+
+// The FP64 point a0 + S (b - a0) (a wall point or a frozen particle's stop).
+__device__ __forceinline__ void cross_point_df(const CrossStateDF& c, double r[3]) {
+  const double sd = df_to_f64(c.S);
+#pragma unroll
+  for (int k = 0; k < 3; k++) r[k] = fma(sd, c.b[k] - c.a0[k], c.a0[k]);
+}
+
+// One piece of the walk: deposit up to the exit face (or to b) and move on.
+// Returns true when the particle's step is complete.
+__device__ __forceinline__ bool cross_advance_df(const PushArgs& A, CrossStateDF& c, bool fresh) {
+  DF lb[4];
+  {
+    const Geo32 G = ld_geo(A.tetrec, c.T);
+    float glo[9];
+    ld_glo(A.tetdf, c.T, glo);
+    if (fresh) lambda_df(G, glo, c.a0, c.la);
+    lambda_df(G, glo, c.b, lb);
+  }
+  int kx = -1;
+  DF smin = DF{INFINITY, 0.f};
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (k == c.entry || !(lb[k].h < 0.f)) continue;
+    const DF den = df_sub(c.la[k], lb[k]);
+    DF sk = den.h != 0.f ? df_div(c.la[k], den) : DF{0.f, 0.f};
+    if (sk.h < 0.f) sk = DF{0.f, 0.f};
+    if (df_lt(sk, smin)) {
+      smin = sk;
+      kx = k;
+    }
+  }
+  if (kx < 0) {
+    deposit_df(A, c.T, c.s, c.la, lb);
+    return true;
+  }
+  DF lp[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    lp[i] = (i == kx) ? DF{0.f, 0.f} : df_add(c.la[i], df_mul(smin, df_sub(lb[i], c.la[i])));
+  deposit_df(A, c.T, c.s, c.la, lp);
+  c.nc++;
+  c.S = df_add(c.S, df_mul(smin, df_sub(DF{1.0f, 0.0f}, c.S)));
+  if (c.nc > A.max_cross) {
+    c.st = FEMPIC_P_CAP;
+    c.moved = false;
+    return true;
+  }
+  const float4 nbf = __ldg(A.tetrec + 8 * (int64_t)c.T + 7);
+  const int4 nbv = make_int4(__float_as_int(nbf.x), __float_as_int(nbf.y), __float_as_int(nbf.z),
+                             __float_as_int(nbf.w));
+  const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+  if (nbt >= 0) {
+    // the face map says which of this tet's nodes each of the neighbour's
+    // nodes is, and which one it enters through
+    const float2 fm2 = __ldg(reinterpret_cast<const float2*>(A.tetrec + 8 * (int64_t)c.T + 6) + 1);
+    const uint32_t fm = ((kx < 2 ? __float_as_uint(fm2.x) : __float_as_uint(fm2.y)) >> (16 * (kx & 1))) & 0xffffu;
+    const int ent = (int)(fm & 3u);
+#pragma unroll
+    for (int i2 = 0; i2 < 4; i2++) {
+      const int j = (int)((fm >> (2 + 2 * i2)) & 3u);
+      DF val = DF{0.f, 0.f};
+#pragma unroll
+      for (int jj = 0; jj < 4; jj++)
+        if (jj == j) val = lp[jj];
+      c.la[i2] = (i2 == ent) ? DF{0.f, 0.f} : val;
+    }
+    c.T = nbt;
+    c.entry = ent;
+  } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
+    // the wall point in FP64 starts the mirrored rest of the step
+    double w[3];
+    cross_point_df(c, w);
+#pragma unroll
+    for (int k = 0; k < 3; k++) c.a0[k] = w[k];
+    c.S = DF{0.f, 0.f};
+    const int code = -1 - nbt, ax = code >> 1, side = code & 1;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      if (k == ax) {
+        const double L = side ? A.hi[k] : A.lo[k];
+        c.b[k] = 2.0 * L - c.b[k];
+        c.vn[k] = -c.vn[k];
+      }
+    c.reflected = true;
+#pragma unroll
+    for (int j = 0; j < 4; j++) c.la[j] = lp[j];
+    c.entry = kx;
+  } else {
+    c.st = FEMPIC_P_ABSORBED;
+    c.moved = false;
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void cross_finish_df(const PushArgs& A, const CrossStateDF& c, unsigned& ncr,
+                                                unsigned& nfrz) {
+  const int64_t p = c.p;
+  if (!c.moved) {   // frozen at the last crossing point
+    double r[3];
+    cross_point_df(c, r);
+    A.x[p] = r[0];
+    A.y[p] = r[1];
+    A.z[p] = r[2];
+  } else if (c.reflected) {   // otherwise b is what the common path already stored
+    A.x[p] = c.b[0];
+    A.y[p] = c.b[1];
+    A.z[p] = c.b[2];
+  }
+  if (c.reflected) {
+    static_cast<float*>(A.vx)[p] = c.vn[0];
+    static_cast<float*>(A.vy)[p] = c.vn[1];
+    static_cast<float*>(A.vz)[p] = c.vn[2];
+  }
+  int32_t T = c.T;
+  if (c.st != FEMPIC_P_OK) {
+    A.status[p] = c.st;
+    T = -2 - T;
+    nfrz++;
+  }
+  A.tet[p] = T;
+  if (A.ncross) A.ncross[p] += c.nc;
+  ncr += (unsigned)c.nc;
+}
+
+// Same record hand-out as k_cross_q24: one warp per tile region, each loop
+// iteration advances every busy lane by one piece, idle lanes take the
+// tile's next record.
+__global__ void __launch_bounds__(kThreads) k_cross_df(PushArgs A, int64_t ntiles) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned ncr = 0, nfrz = 0;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
+    const int32_t cnt = A.xcount[t];
+    int32_t next = 0;
+    bool have = false, fresh = false;
+    CrossStateDF c;
+    for (;;) {
+      const unsigned idle = __ballot_sync(full, !have);
+      if (next < cnt && idle) {
+        const int32_t idx = next + __popc(idle & lt);
+        if (!have && idx < cnt) {
+          cross_begin_df(A, A.xrec[t * kThreads + idx], c);
+          have = true;
+          fresh = true;
+        }
+        next += __popc(idle);
+      }
+      if (!__any_sync(full, have)) break;
+      if (have) {
+        const bool done = cross_advance_df(A, c, fresh);
+        fresh = false;
+        if (done) {
+          cross_finish_df(A, c, ncr, nfrz);
+          have = false;
+        }
+      }
+    }
+  }
+  ncr = __reduce_add_sync(full, ncr);
+  nfrz = __reduce_add_sync(full, nfrz);
+  if (lane == 0) {
+    if (ncr) atomicAdd(A.stats, (unsigned long long)ncr);
+    if (nfrz) atomicAdd(A.stats + 1, (unsigned long long)nfrz);
+  }
+}
+
 // ------------------------------------------------------- deposit finalize
+// Contract form, per tet: the moment slots (sum of D, sum of u x D, FP64)
+// become the 6 local-edge values through the tet's gradients,
+//   g_0j = G_j . sum D + (G_0 x G_j) . sum(u x D),  g_ij = (G_i x G_j) . sum(u x D),
+// in double-float from the FP64 gradients' FP32 pairs; the crossing pass's
+// edge-form deposits are added, each species scaled by its q w, and the sum
+// is written as FP32 pairs for the per-edge pull.  The slots are cleared.
+struct TetFinalizeArgs {
+  int64_t nt;
+  int32_t ns;
+  const float4* tetrec;
+  const float4* tetdf;
+  double* mom;
+  double* xhi;
+  float* xlo;
+  float qwh[kMaxSpecies], qwl[kMaxSpecies];   // q w per species as FP32 pairs
+  float4* out;                                // [nt][3]: (h, l) of local edges 0..5
+};
+
+__device__ __forceinline__ void df_cross(const DF a[3], const DF b[3], DF c[3]) {
+  c[0] = df_sub(df_mul(a[1], b[2]), df_mul(a[2], b[1]));
+  c[1] = df_sub(df_mul(a[2], b[0]), df_mul(a[0], b[2]));
+  c[2] = df_sub(df_mul(a[0], b[1]), df_mul(a[1], b[0]));
+}
+
+__global__ void __launch_bounds__(kThreads) k_tet_finalize(TetFinalizeArgs A) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= A.nt) return;
+  DF acc[6];
+#pragma unroll
+  for (int e = 0; e < 6; e++) acc[e] = DF{0.f, 0.f};
+  bool have_geo = false;
+  DF G[4][3];
+  for (int s = 0; s < A.ns; s++) {
+    const int64_t slot = ((int64_t)s * A.nt + t) * 8;
+    double2* m2 = reinterpret_cast<double2*>(A.mom + slot);
+    double2* x2 = reinterpret_cast<double2*>(A.xhi + slot);
+    const double2 m01 = m2[0], m23 = m2[1], m45 = m2[2];
+    const double2 x01 = x2[0], x23 = x2[1], x45 = x2[2];
+    float4* l4 = reinterpret_cast<float4*>(A.xlo + slot);
+    const float4 lA = l4[0], lB = l4[1];
+    const double mv[6] = {m01.x, m01.y, m23.x, m23.y, m45.x, m45.y};
+    const double xv[6] = {x01.x, x01.y, x23.x, x23.y, x45.x, x45.y};
+    const float lv[6] = {lA.x, lA.y, lA.z, lA.w, lB.x, lB.y};
+    bool any = false;
+#pragma unroll
+    for (int e = 0; e < 6; e++) any = any || mv[e] != 0.0 || xv[e] != 0.0 || lv[e] != 0.f;
+    if (!any) continue;
+    const double2 z2 = make_double2(0.0, 0.0);
+    m2[0] = m2[1] = m2[2] = z2;
+    x2[0] = x2[1] = x2[2] = z2;
+    l4[0] = l4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!have_geo) {
+      const float4 a = __ldg(A.tetrec + 8 * t + 1), b = __ldg(A.tetrec + 8 * t + 2), c = __ldg(A.tetrec + 8 * t + 3);
+      const float4 p = __ldg(A.tetdf + 4 * t), q = __ldg(A.tetdf + 4 * t + 1), r = __ldg(A.tetdf + 4 * t + 2);
+      const float gh[9] = {a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z};
+      const float gl[9] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w, r.x};
+#pragma unroll
+      for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) G[k + 1][j] = fast_two_sum(gh[3 * k + j], gl[3 * k + j]);
+#pragma unroll
+      for (int j = 0; j < 3; j++) G[0][j] = df_neg(df_add(df_add(G[1][j], G[2][j]), G[3][j]));
+      have_geo = true;
+    }
+    const DF S[3] = {f64_to_df(mv[0]), f64_to_df(mv[1]), f64_to_df(mv[2])};
+    const DF M[3] = {f64_to_df(mv[3]), f64_to_df(mv[4]), f64_to_df(mv[5])};
+    const DF qw = DF{A.qwh[s], A.qwl[s]};
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+      const int i = le0(e), j = le1(e);
+      DF C[3];
+      df_cross(G[i], G[j], C);
+      DF g = df_dot3(C, M);
+      if (i == 0) g = df_add(g, df_dot3(G[j], S));
+      g = df_add(g, df_add(f64_to_df(xv[e]), DF{lv[e], 0.f}));
+      acc[e] = df_add(acc[e], df_mul(g, qw));
+    }
+  }
+  float4* o = A.out + 3 * t;
+  o[0] = make_float4(acc[0].h, acc[0].l, acc[1].h, acc[1].l);
+  o[1] = make_float4(acc[2].h, acc[2].l, acc[3].h, acc[3].l);
+  o[2] = make_float4(acc[4].h, acc[4].l, acc[5].h, acc[5].l);
+}
+
 struct FinalizeArgs {
   int64_t ne;
   int64_t nt;
-  const int32_t* estart;         // mixed form: edge -> (tet, local edge) slots
+  const int32_t* estart;         // mixed forms: edge -> (tet, local edge) slots
   const int32_t* eslot;
-  int32_t mixed;
+  int32_t mode;                  // 0 FP64 accumulator, 1 contract form (per-tet pairs), 2 24-bit form
   int32_t ns;
-  double qwscale[kMaxSpecies];   // q w 2^-48 per species (mixed form)
+  double qwscale[kMaxSpecies];   // q w 2^-48 per species (24-bit form)
   double* dG;
-  const unsigned long long* dGq;  // mixed form: deposit slots [ns][nt][8]
+  const unsigned long long* dGq;  // 24-bit form: deposit slots [ns][nt][8]
+  const float* tetout;           // contract form: [nt][12] (h, l) pairs of the 6 local edges
   double* Gcum;
   double* dG_out;
   double* Gcum_out;
@@ -1374,17 +1920,18 @@ struct FinalizeArgs {
   double c, s;                   // cos, sin of omega0 t_next
 };
 
-// Deposit finalize, one thread per edge.  Mixed form: the edge pulls its
-// exact int64 sums from the deposit slots of its tets (adjacency built once
-// on the host; integer sums, so the result does not depend on the order) and
-// scales them by q w 2^-48; the slots are cleared afterwards by one
-// coalesced memset.  FP64 form: the edge's FP64 accumulator.  Then G_cum +=
-// dG and the requested outputs (dG, G_cum, the envelope-frame G~).
+// Deposit finalize, one thread per edge.  The mixed forms pull the edge's
+// values from its tets (adjacency built once on the host, a fixed order):
+// the 24-bit form its exact int64 sums from the integer slots, scaled by
+// q w 2^-48 (the slots are cleared afterwards by one coalesced memset); the
+// contract form its tets' double-float values from k_tet_finalize.  FP64
+// form: the edge's FP64 accumulator.  Then G_cum += dG and the requested
+// outputs (dG, G_cum, the envelope-frame G~).
 __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= A.ne) return;
   double d;
-  if (A.mixed) {
+  if (A.mode == 2) {
     d = 0.0;
     const int32_t j0 = A.estart[e], j1 = A.estart[e + 1];
     for (int s = 0; s < A.ns; s++) {
@@ -1396,6 +1943,15 @@ __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
       }
       d += A.qwscale[s] * (double)q;
     }
+  } else if (A.mode == 1) {
+    DF acc = DF{0.f, 0.f};
+    const int32_t j0 = A.estart[e], j1 = A.estart[e + 1];
+    for (int32_t j = j0; j < j1; j++) {
+      const int32_t k = A.eslot[j];
+      const float2 v = reinterpret_cast<const float2*>(A.tetout)[(int64_t)(k / 6) * 6 + k % 6];
+      acc = df_add(acc, DF{v.x, v.y});
+    }
+    d = df_to_f64(acc);
   } else {
     d = A.dG[e];
     A.dG[e] = 0.0;
@@ -1416,7 +1972,7 @@ struct ChargeArgs {
   const int32_t* tet;
   Species sp;
   int64_t nt;
-  int32_t mixed;
+  int32_t q24;                // 24-bit form: the integer barycentrics its deposit uses
   const double* geom64;
   const float4* tetrec;
   const int4* tn;
@@ -1434,7 +1990,7 @@ __global__ void __launch_bounds__(kThreads) k_nodal_charge(ChargeArgs A) {
   const double qw = A.sp.qw[s];
   const double r[3] = {A.x[p], A.y[p], A.z[p]};
   double lam[4];
-  if (A.mixed) {
+  if (A.q24) {
     int32_t Q[4];
     bary_q_at(A.tetrec, T, r, Q);
     for (int i = 0; i < 4; i++) lam[i] = (double)Q[i] * (1.0 / (double)kQOne);
@@ -1683,12 +2239,12 @@ __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, in
     beta = (R)F[9];
   } else {
     const float4* Rr = A.tetrec + 8 * (int64_t)T;
-    const Geo32 G = Geo32{__ldg(Rr), __ldg(Rr + 1), __ldg(Rr + 2), __ldg(Rr + 3)};
+    const Geo32 G = ld_geo(A.tetrec, T);
     const float4 f0 = __ldg(Rr + 4), f1 = __ldg(Rr + 5), f2 = __ldg(Rr + 6);
-    const FF rs[3] = {split_f64(A.x[p]), split_f64(A.y[p]), split_f64(A.z[p])};
-    float dx, dy, dz;
-    dpos32(G, rs, dx, dy, dz);
-    d = {(R)dx, (R)dy, (R)dz};
+    FF dd[3];
+    float d32[3];
+    dpos(G, A.x[p], A.y[p], A.z[p], dd, d32);   // the forward step's sequence
+    d = {(R)d32[0], (R)d32[1], (R)d32[2]};
     E0 = {(R)f0.x, (R)f0.y, (R)f0.z};
     W = {(R)f0.w, (R)f1.x, (R)f1.y};
     B0 = {(R)f1.z, (R)f1.w, (R)f2.x};
@@ -2006,8 +2562,13 @@ struct fempic_env {
   int4* tf = nullptr;
   void* field = nullptr;
   double* dG = nullptr;
-  unsigned long long* dGq = nullptr;   // mixed form [dGq_species][nt][8]
+  unsigned long long* dGq = nullptr;   // 24-bit form [dGq_species][nt][8]
   int32_t dGq_species = 0;
+  float4* tetdf = nullptr;             // contract form: low parts of grad lambda_1..3, [nt][4]
+  double* mom = nullptr;               // contract form: moment slots [dGq_species][nt][8]
+  double* xhi = nullptr;               // contract form: crossing deposits [dGq_species][nt][8]
+  float* xlo = nullptr;                // their low parts [dGq_species][nt][8]
+  float4* tetout = nullptr;            // contract form: per-tet edge values of a step [nt][3]
   double* Gcum = nullptr;
   unsigned long long* stats = nullptr;
   int64_t* gstart = nullptr;
@@ -2025,7 +2586,7 @@ struct fempic_env {
   int32_t* xcount = nullptr;        // [xtiles]
   int64_t xtiles = 0;
   int num_sms = 1;
-  int tma_blocks_per_sm = 0;        // resident CTAs of the staged kernel (persistent grid)
+  int tma_blocks_per_sm[2] = {0, 0}; // resident CTAs of the staged kernels (contract, 24-bit)
   int64_t steps = 0;
   // per-kernel event timing (measurement support)
   struct Rec {
@@ -2039,6 +2600,9 @@ struct fempic_env {
   int32_t* sort_sums = nullptr;     // [sort_cap / 2048 + 1]
   int64_t sort_cap = 0;
   bool profiling = false;
+  int32_t stall_cta = -1;           // fempic_debug_stall (test support)
+  unsigned long long stall_ns = 0;
+  unsigned long long seen_frozen = 0, seen_timeouts = 0;   // fempic_error_count baselines
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
@@ -2080,7 +2644,8 @@ struct LaunchTimer {
 static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
-  void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq,
+  void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq, e->tetdf, e->mom,
+                  e->xhi, e->xlo, e->tetout,
                   e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->tadj, e->estart, e->eslot, e->fslot, e->xrec, e->xrec64, e->xcount,
                   nullptr};
   for (void* q : ptrs)
@@ -2095,22 +2660,49 @@ extern "C" void fempic_env_destroy(fempic_env* env) { free_env(env); }
 static int upload(fempic_env* e) {
   const HostMesh& m = e->h;
   const int64_t nt = m.nt;
-  std::vector<float4> geo(8 * nt);
+  std::vector<float4> geo(8 * nt), gdf(4 * nt);
   std::vector<int4> tn(nt), nb(nt), te(2 * nt), tf(nt);
+  double max_coord = 0.0;
+  for (int64_t i = 0; i < m.nn * 3; i++) max_coord = std::max(max_coord, std::fabs(m.xyz[i]));
   for (int64_t t = 0; t < nt; t++) {
     const double* G = &m.geom[12 * t];
-    // mixed-form record: x0 as an FP32 pair (x0 = hi + lo) and FP32 gradients
-    float xh[3], xl[3], g[9];
-    for (int a = 0; a < 3; a++) {
-      xh[a] = (float)G[a];
-      xl[a] = (float)(G[a] - (double)xh[a]);
+    // mixed-form record: x0 exactly (3 x f64), FP32 gradients, the error
+    // bound kappa of the FP32 inside test; the low FP32 parts of the
+    // gradients go to tetdf (contract form)
+    float g[9], glo[9];
+    for (int i = 0; i < 9; i++) {
+      g[i] = (float)G[3 + i];
+      glo[i] = (float)(G[3 + i] - (double)g[i]);
     }
-    for (int i = 0; i < 9; i++) g[i] = (float)G[3 + i];
-    geo[8 * t] = make_float4(xh[0], xh[1], xh[2], xl[0]);
-    geo[8 * t + 1] = make_float4(xl[1], xl[2], g[0], g[1]);
-    geo[8 * t + 2] = make_float4(g[2], g[3], g[4], g[5]);
-    geo[8 * t + 3] = make_float4(g[6], g[7], g[8], 0.f);
+    // kappa bounds |FP32 lambda(b) - lambda(b)| for a segment start in the
+    // tet: FP32 roundings of d, d + D, the gradients and the three-term
+    // sums (each 2^-24 relative), amplified by |grad lambda_k|_1 and the
+    // coordinate extent of the tet, plus the FP64 rounding of b.
+    double gsum = 0.0, ext = 0.0;
+    for (int k = 0; k < 4; k++) {
+      double s1 = 0.0;
+      for (int j = 0; j < 3; j++) {
+        const double gk = k == 0 ? -(G[3 + j] + G[6 + j] + G[9 + j]) : G[3 * k + j];
+        s1 += std::fabs(gk);
+      }
+      gsum = std::max(gsum, s1);
+    }
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++)
+        for (int a = 0; a < 3; a++)
+          ext = std::max(ext, std::fabs(m.xyz[3 * (int64_t)m.tn[4 * t + i] + a] - m.xyz[3 * (int64_t)m.tn[4 * t + j] + a]));
+    float kappa = (float)(0x1p-16 * (1.0 + 4.0 * gsum * ext) + gsum * max_coord * 0x1p-50);
+    if (!(gsum * ext < 0x1p16)) kappa = INFINITY;   // a sliver: every particle takes the crossing pass
+    float head[16];
+    std::memcpy(head, G, 24);   // x0 as 6 words, bits unchanged
+    std::memcpy(head + 6, g, sizeof(g));
+    head[15] = kappa;
+    std::memcpy(&geo[8 * t], head, sizeof(head));
     for (int k = 4; k < 7; k++) geo[8 * t + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    gdf[4 * t] = make_float4(glo[0], glo[1], glo[2], glo[3]);
+    gdf[4 * t + 1] = make_float4(glo[4], glo[5], glo[6], glo[7]);
+    gdf[4 * t + 2] = make_float4(glo[8], 0.f, 0.f, 0.f);
+    gdf[4 * t + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
     {
       // face maps of the mixed crossing walk, 16 bits per local face k with a
       // neighbour: bits 0-1 the neighbour's local node that is not in this
@@ -2153,6 +2745,10 @@ static int upload(fempic_env* e) {
   FEMPIC_CUDA(dalloc(&e->tf, nt));
   FEMPIC_CUDA(cudaMemcpy(e->geom64, m.geom.data(), 12 * nt * sizeof(double), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->tetrec, geo.data(), 8 * nt * sizeof(float4), cudaMemcpyHostToDevice));
+  if (e->opt.precision == FEMPIC_MIXED) {
+    FEMPIC_CUDA(dalloc(&e->tetdf, 4 * nt));
+    FEMPIC_CUDA(cudaMemcpy(e->tetdf, gdf.data(), 4 * nt * sizeof(float4), cudaMemcpyHostToDevice));
+  }
   FEMPIC_CUDA(cudaMemcpy(e->tn, tn.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->nb, nb.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   FEMPIC_CUDA(cudaMemcpy(e->te, te.data(), 2 * nt * sizeof(int4), cudaMemcpyHostToDevice));
@@ -2200,7 +2796,8 @@ extern "C" int fempic_env_create(const fempic_mesh_desc* mesh, const fempic_opti
   g_last_error.clear();
   if (!mesh || !opts || !out) return fail(FEMPIC_EINVAL, "env_create: NULL argument");
   *out = nullptr;
-  if ((opts->precision != FEMPIC_FP64 && opts->precision != FEMPIC_MIXED) || opts->max_crossings < 0 ||
+  if ((opts->precision != FEMPIC_FP64 && opts->precision != FEMPIC_MIXED && opts->precision != FEMPIC_MIXED_Q24) ||
+      opts->max_crossings < 0 ||
       opts->max_crossings > kMaxCrossingsLimit ||
       (opts->wall_mode != FEMPIC_WALL_REFLECT && opts->wall_mode != FEMPIC_WALL_ABSORB) || opts->reserved != 0)
     return fail(FEMPIC_EINVAL, "env_create: bad options");
@@ -2323,7 +2920,7 @@ static int ensure_xqueue(fempic_env* env, int64_t n, cudaStream_t st) {
     env->xcount = nullptr;
     env->xtiles = 0;
   }
-  if (env->opt.precision == FEMPIC_MIXED)
+  if (env->opt.precision != FEMPIC_FP64)
     FEMPIC_CUDA(dalloc(&env->xrec, tiles * kThreads));
   else
     FEMPIC_CUDA(dalloc(&env->xrec64, tiles * kThreads));
@@ -2333,18 +2930,41 @@ static int ensure_xqueue(fempic_env* env, int64_t n, cudaStream_t st) {
 }
 
 static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
-  if (env->dGq && env->dGq_species >= ns) return FEMPIC_OK;
-  // The integer accumulators hold one step only; a larger species count
-  // reallocates them, so a step must be finalized (fempic_deposit) before the
-  // species table grows.
-  unsigned long long* nq = nullptr;
-  FEMPIC_CUDA(dalloc(&nq, (size_t)ns * env->h.nt * 8));
-  FEMPIC_CUDA(cudaMemsetAsync(nq, 0, (size_t)ns * env->h.nt * 8 * sizeof(unsigned long long), st));
-  if (env->dGq) {
-    FEMPIC_CUDA(cudaStreamSynchronize(st));
-    cudaFree(env->dGq);
+  const bool q24 = env->opt.precision == FEMPIC_MIXED_Q24;
+  if ((q24 ? env->dGq != nullptr : env->mom != nullptr) && env->dGq_species >= ns) return FEMPIC_OK;
+  // The slots hold one step only; a larger species count reallocates them,
+  // so a step must be finalized (fempic_deposit) before the species table
+  // grows.
+  const size_t nslot = (size_t)ns * env->h.nt * 8;
+  if (env->dGq || env->mom) FEMPIC_CUDA(cudaStreamSynchronize(st));
+  if (q24) {
+    unsigned long long* nq = nullptr;
+    FEMPIC_CUDA(dalloc(&nq, nslot));
+    FEMPIC_CUDA(cudaMemsetAsync(nq, 0, nslot * sizeof(unsigned long long), st));
+    if (env->dGq) cudaFree(env->dGq);
+    env->dGq = nq;
+  } else {
+    double *nm = nullptr, *nh = nullptr;
+    float* nl = nullptr;
+    FEMPIC_CUDA(dalloc(&nm, nslot));
+    FEMPIC_CUDA(dalloc(&nh, nslot));
+    FEMPIC_CUDA(dalloc(&nl, nslot));
+    FEMPIC_CUDA(cudaMemsetAsync(nm, 0, nslot * sizeof(double), st));
+    FEMPIC_CUDA(cudaMemsetAsync(nh, 0, nslot * sizeof(double), st));
+    FEMPIC_CUDA(cudaMemsetAsync(nl, 0, nslot * sizeof(float), st));
+    if (env->mom) {
+      cudaFree(env->mom);
+      cudaFree(env->xhi);
+      cudaFree(env->xlo);
+    }
+    env->mom = nm;
+    env->xhi = nh;
+    env->xlo = nl;
+    if (!env->tetout) {
+      FEMPIC_CUDA(dalloc(&env->tetout, 3 * env->h.nt));
+      FEMPIC_CUDA(cudaMemsetAsync(env->tetout, 0, 3 * env->h.nt * sizeof(float4), st));
+    }
   }
-  env->dGq = nq;
   env->dGq_species = ns;
   return FEMPIC_OK;
 }
@@ -2358,8 +2978,9 @@ struct HostLevels {
   double amp;
 };
 
-static int push_step_impl(fempic_env* env, const fempic_particles* p, const HostLevels& H, double omega0,
-                          double t, double dt, void* stream) {
+// Every argument check of a push step, on the host, before any device work.
+static int validate_step(const fempic_particles* p, const HostLevels& H, double omega0, double t, double dt,
+                         Species* sp) {
   int rc = check_particles(p, true);
   if (rc) return rc;
   for (int k = 0; k < H.nl; k++)
@@ -2368,11 +2989,17 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
     return fail(FEMPIC_EINVAL, "push_step: non-finite or non-positive scalar");
   for (int k = 0; k < H.nl; k++)
     if (!std::isfinite(H.w[k])) return fail(FEMPIC_EINVAL, "push_step: non-finite level weight");
+  return fill_species(p, dt, sp);
+}
+
+static int push_step_impl(fempic_env* env, const fempic_particles* p, const HostLevels& H, double omega0,
+                          double t, double dt, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   PushArgs A{};
-  rc = fill_species(p, dt, &A.sp);
+  int rc = validate_step(p, H, omega0, t, dt, &A.sp);
   if (rc) return rc;
-  const bool mixed = env->opt.precision == FEMPIC_MIXED;
+  const bool mixed = env->opt.precision != FEMPIC_FP64;
+  const bool q24 = env->opt.precision == FEMPIC_MIXED_Q24;
   if (mixed) {
     rc = ensure_mixed_accumulators(env, p->n_species, st);
     if (rc) return rc;
@@ -2444,12 +3071,19 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
   A.field = env->field;
   A.dG = env->deposit_on ? env->dG : nullptr;
   A.dGq = env->deposit_on ? env->dGq : nullptr;
+  A.mom = env->deposit_on ? env->mom : nullptr;
+  A.xhi = env->deposit_on ? env->xhi : nullptr;
+  A.xlo = env->xlo;
+  A.tetdf = env->tetdf;
   A.stats = env->stats;
   rc = ensure_xqueue(env, p->n, st);
   if (rc) return rc;
   A.xrec = env->xrec;
   A.xrec64 = env->xrec64;
   A.xcount = env->xcount;
+  A.wait_ns = env->stall_cta >= 0 ? env->stall_ns : kWaitLimitNs;
+  A.stall_cta = env->stall_cta;
+  env->stall_cta = -1;   // one launch only
   {
     LaunchTimer lt(env, st, FEMPIC_K_PUSH);
     if (mixed) {
@@ -2459,25 +3093,38 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
                               (uintptr_t)p->vy | (uintptr_t)p->vz | (uintptr_t)p->tet;
       const int64_t ntiles = (FEMPIC_USE_TMA && !(align & 15u)) ? p->n / kTile : 0;
       if (ntiles > 0) {
-        if (env->tma_blocks_per_sm == 0) {
+        int& bps = env->tma_blocks_per_sm[q24 ? 1 : 0];
+        if (bps == 0) {
           int nb = 0;
-          FEMPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_mixed_tma, kThreads, 0));
-          env->tma_blocks_per_sm = nb > 0 ? nb : 1;
+          if (q24)
+            FEMPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_mixed_tma<true>, kThreads, 0));
+          else
+            FEMPIC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_mixed_tma<false>, kThreads, 0));
+          bps = nb > 0 ? nb : 1;
         }
-        const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)env->num_sms * env->tma_blocks_per_sm);
-        k_push_mixed_tma<<<grid, kThreads, 0, st>>>(A, ntiles);
+        const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)env->num_sms * bps);
+        if (q24)
+          k_push_mixed_tma<true><<<grid, kThreads, 0, st>>>(A, ntiles);
+        else
+          k_push_mixed_tma<false><<<grid, kThreads, 0, st>>>(A, ntiles);
         lt.kernels++;
       }
       const int64_t rest = p->n - ntiles * kTile;
       if (rest > 0) {
-        k_push_mixed<<<blocks_for(rest), kThreads, 0, st>>>(A, ntiles * kTile);
+        if (q24)
+          k_push_mixed<true><<<blocks_for(rest), kThreads, 0, st>>>(A, ntiles * kTile);
+        else
+          k_push_mixed<false><<<blocks_for(rest), kThreads, 0, st>>>(A, ntiles * kTile);
         lt.kernels++;
       }
       const int64_t all_tiles = (p->n + kTile - 1) / kTile;
       const unsigned cross_blocks = (unsigned)std::min<int64_t>(
           (all_tiles + 7) / 8, (int64_t)env->num_sms * kCrossWarpsPerSm / (kThreads / 32));
       LaunchTimer lc(env, st, FEMPIC_K_CROSS);   // nested: also inside the push bracket
-      k_cross_mixed<<<cross_blocks, kThreads, 0, st>>>(A, all_tiles);
+      if (q24)
+        k_cross_q24<<<cross_blocks, kThreads, 0, st>>>(A, all_tiles);
+      else
+        k_cross_df<<<cross_blocks, kThreads, 0, st>>>(A, all_tiles);
       lc.kernels = 1;
     } else {
       k_push_fp64<<<blocks_for(p->n), kThreads, 0, st>>>(A);
@@ -2520,6 +3167,23 @@ extern "C" int fempic_push_step3(fempic_env* env, const fempic_particles* p, con
   return push_step_impl(env, p, H, omega0, t, dt, stream);
 }
 
+namespace fempic {
+int env_precision(const fempic_env* env) { return env->opt.precision; }
+
+int validate_push_step(const fempic_particles* p, const fempic_envelope* envl, double omega0, double t,
+                       double dt) {
+  if (!envl) return fail(FEMPIC_EINVAL, "push_step: NULL envelope");
+  HostLevels H{};
+  H.nl = 1;
+  H.e[0] = envl->e_tilde;
+  H.b[0] = envl->b_tilde;
+  H.w[0] = 1.0;
+  H.amp = envl->amp;
+  Species sp{};
+  return validate_step(p, H, omega0, t, dt, &sp);
+}
+}  // namespace fempic
+
 extern "C" int fempic_lagrange3(const double* tau, double t, double* w_out) {
   if (!tau || !w_out) return fail(FEMPIC_EINVAL, "lagrange3: NULL argument");
   if (!std::isfinite(t) || !std::isfinite(tau[0]) || !std::isfinite(tau[1]) || !std::isfinite(tau[2]) ||
@@ -2538,31 +3202,56 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
                               void* G_env_out, void* stream) {
   if (!env) return fail(FEMPIC_EINVAL, "deposit: NULL env");
   if (!std::isfinite(omega0) || !std::isfinite(t_next)) return fail(FEMPIC_EINVAL, "deposit: non-finite scalar");
-  const bool mixed = env->opt.precision == FEMPIC_MIXED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prec = env->opt.precision;
   FinalizeArgs A{};
   A.ne = env->h.ne;
-  A.mixed = mixed;
-  A.ns = mixed ? (env->dGq ? env->ns_last : 0) : 0;
+  A.nt = env->h.nt;
+  A.mode = prec == FEMPIC_FP64 ? 0 : (prec == FEMPIC_MIXED ? 1 : 2);
+  A.ns = env->ns_last;
   for (int s = 0; s < kMaxSpecies; s++) A.qwscale[s] = env->qw_last[s] * 0x1p-48;
   A.dG = env->dG;
+  A.dGq = env->dGq;
+  A.tetout = reinterpret_cast<const float*>(env->tetout);
   A.Gcum = env->Gcum;
   A.dG_out = dG_out;
   A.Gcum_out = G_cum_out;
   A.Genv_out = static_cast<double2*>(G_env_out);
+  A.estart = env->estart;
+  A.eslot = env->eslot;
   const double phi = omega0 * t_next;
   A.c = std::cos(phi);
   A.s = std::sin(phi);
+  if (A.mode == 2 && !env->dGq) A.ns = 0;
+  if (A.mode == 1 && !env->mom) {
+    int rc = ensure_mixed_accumulators(env, 1, st);   // no step yet: the pull reads zeros
+    if (rc) return rc;
+    A.tetout = reinterpret_cast<const float*>(env->tetout);
+    A.ns = 0;
+  }
   {
-    LaunchTimer lt(env, (cudaStream_t)stream, FEMPIC_K_FINALIZE);
-    A.nt = env->h.nt;
-    A.estart = env->estart;
-    A.eslot = env->eslot;
-    A.dGq = env->dGq;
-    k_deposit_finalize<<<blocks_for(A.ne), kThreads, 0, (cudaStream_t)stream>>>(A);
+    LaunchTimer lt(env, st, FEMPIC_K_FINALIZE);
+    if (A.mode == 1) {
+      TetFinalizeArgs T{};
+      T.nt = env->h.nt;
+      T.ns = A.ns;
+      T.tetrec = env->tetrec;
+      T.tetdf = env->tetdf;
+      T.mom = env->mom;
+      T.xhi = env->xhi;
+      T.xlo = env->xlo;
+      for (int s = 0; s < kMaxSpecies; s++) {
+        T.qwh[s] = (float)env->qw_last[s];
+        T.qwl[s] = (float)(env->qw_last[s] - (double)T.qwh[s]);
+      }
+      T.out = env->tetout;
+      k_tet_finalize<<<blocks_for(T.nt), kThreads, 0, st>>>(T);
+      lt.kernels++;
+    }
+    k_deposit_finalize<<<blocks_for(A.ne), kThreads, 0, st>>>(A);
     lt.kernels++;
-    if (mixed && env->dGq && A.ns > 0)
-      FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)A.ns * env->h.nt * 8 * sizeof(unsigned long long),
-                                  (cudaStream_t)stream));
+    if (A.mode == 2 && A.ns > 0)
+      FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)A.ns * env->h.nt * 8 * sizeof(unsigned long long), st));
   }
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
@@ -2579,9 +3268,12 @@ extern "C" int fempic_reset_deposit(fempic_env* env, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   FEMPIC_CUDA(cudaMemsetAsync(env->Gcum, 0, env->h.ne * sizeof(double), st));
   if (env->dG) FEMPIC_CUDA(cudaMemsetAsync(env->dG, 0, env->h.ne * sizeof(double), st));
-  if (env->dGq) {
-    FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)env->dGq_species * env->h.nt * 8 * sizeof(unsigned long long),
-                                st));
+  const size_t nslot = (size_t)env->dGq_species * env->h.nt * 8;
+  if (env->dGq) FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, nslot * sizeof(unsigned long long), st));
+  if (env->mom) {
+    FEMPIC_CUDA(cudaMemsetAsync(env->mom, 0, nslot * sizeof(double), st));
+    FEMPIC_CUDA(cudaMemsetAsync(env->xhi, 0, nslot * sizeof(double), st));
+    FEMPIC_CUDA(cudaMemsetAsync(env->xlo, 0, nslot * sizeof(float), st));
   }
   return FEMPIC_OK;
 }
@@ -2602,7 +3294,7 @@ extern "C" int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, d
   A.z = p->z;
   A.tet = p->tet;
   A.nt = env->h.nt;
-  A.mixed = env->opt.precision == FEMPIC_MIXED;
+  A.q24 = env->opt.precision == FEMPIC_MIXED_Q24;
   A.geom64 = env->geom64;
   A.tetrec = env->tetrec;
   A.tn = env->tn;
@@ -2626,6 +3318,32 @@ extern "C" int fempic_stats(fempic_env* env, int64_t* out4, void* stream) {
   out4[1] = (int64_t)h[1];
   out4[2] = env->steps;
   out4[3] = (int64_t)h[2];
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_error_count(fempic_env* env, int64_t* n_bad, void* stream) {
+  if (!env || !n_bad) return fail(FEMPIC_EINVAL, "error_count: NULL argument");
+  unsigned long long h[3] = {0, 0, 0};
+  cudaStream_t st = (cudaStream_t)stream;
+  FEMPIC_CUDA(cudaMemcpyAsync(h, env->stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  FEMPIC_CUDA(cudaStreamSynchronize(st));
+  *n_bad = (int64_t)(h[1] - env->seen_frozen);
+  const unsigned long long gave_up = h[2] - env->seen_timeouts;
+  env->seen_frozen = h[1];
+  env->seen_timeouts = h[2];
+  if (gave_up)
+    return fail(FEMPIC_EINCOMPLETE, "error_count: " + std::to_string(gave_up) +
+                                        " staged push CTA(s) gave up waiting for a bulk copy; the particles of "
+                                        "their remaining tiles were not advanced and their deposit is missing");
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_debug_stall(fempic_env* env, int32_t cta, int64_t limit_ns) {
+  if (!env) return fail(FEMPIC_EINVAL, "debug_stall: NULL env");
+  if (cta < 0 || limit_ns < 1000 || limit_ns > (int64_t)kWaitLimitNs)
+    return fail(FEMPIC_EINVAL, "debug_stall: cta >= 0 and 1 us <= limit_ns <= 1 s");
+  env->stall_cta = cta;
+  env->stall_ns = (unsigned long long)limit_ns;
   return FEMPIC_OK;
 }
 
@@ -2900,7 +3618,7 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
   AdjArgs A{};
   rc = fill_species(before, dt, &A.sp);
   if (rc) return rc;
-  const bool mixed = env->opt.precision == FEMPIC_MIXED;
+  const bool mixed = env->opt.precision != FEMPIC_FP64;
   const int64_t nt = env->h.nt;
   if (!env->tetgrad) {
     FEMPIC_CUDA(dalloc(&env->tetgrad, 10 * nt));
@@ -3013,7 +3731,7 @@ extern "C" int fempic_kinetic_energy(fempic_env* env, const fempic_particles* p,
     A.vby = seed->vy;
     A.vbz = seed->vz;
   }
-  if (env->opt.precision == FEMPIC_MIXED)
+  if (env->opt.precision != FEMPIC_FP64)
     k_kinetic_energy<float><<<blocks_for(p->n), kThreads, 0, st>>>(A);
   else
     k_kinetic_energy<double><<<blocks_for(p->n), kThreads, 0, st>>>(A);

@@ -46,4 +46,12 @@ inline int grid_cell(double x, double lo, double ginv, int gd) {
   return (int)f;
 }
 
+// Precision form of an env (FEMPIC_FP64 or FEMPIC_MIXED).
+int env_precision(const fempic_env* env);
+
+// Every host-side argument check of fempic_push_step, without device work:
+// FEMPIC_OK or the code and message fempic_push_step would return.
+int validate_push_step(const fempic_particles* p, const fempic_envelope* envl, double omega0, double t,
+                       double dt);
+
 }  // namespace fempic

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import capi
-from .capi import FEMPIC_FP64, FEMPIC_MIXED  # noqa: F401
+from .capi import FEMPIC_FP64, FEMPIC_MIXED, FEMPIC_MIXED_Q24  # noqa: F401
 
 
 def _stream(stream) -> int:
@@ -225,6 +225,12 @@ class FempicEnv:
         out = np.zeros(4, np.int64)
         capi.fempic_stats(self.h, out.ctypes.data, _stream(stream))
         return dict(crossings=int(out[0]), frozen=int(out[1]), steps=int(out[2]), wait_timeouts=int(out[3]))
+
+    def error_count(self, stream=None) -> tuple:
+        """Synchronize and report the steps since the last call: (ok, frozen)
+        where ok is False when a step left particles unadvanced."""
+        rc, n = capi.fempic_error_count(self.h, _stream(stream))
+        return rc == capi.FEMPIC_OK, n
 
     def profile(self, enable: bool):
         """Start (clearing earlier records) or stop per-kernel event timing."""

@@ -178,3 +178,41 @@ def test_downshift_rejects_bad_arguments():
     ds.step(st, e, b, 1.0, wl.omega0, 0.0, wl.dt)
     torch.cuda.synchronize()
     assert (st.status.cpu().numpy() == 0).all()
+
+
+def test_downshift_c_entry_checks_everything_before_any_launch():
+    """Through the C entry point itself (no Python-side checks): a mixed-form
+    env is rejected (its f32 velocities and complex64 DoFs would be read as
+    f64 and complex128), and a bad species table (NULL weights) is rejected
+    before the first launch, so the particles and history are untouched."""
+    import ctypes as C
+
+    from paper_2208_12795_gb300 import capi
+    from paper_2208_12795_gb300.env import Downshift, FempicEnv, ParticleState, _ptr
+    wl = I.workload_small()
+    lib = capi.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    env = FempicEnv.from_mesh(wl.mesh, precision=FP64)
+    st = ParticleState.from_host(wl.particles.subset(500), FP64)
+    env.locate(st)
+    ds = Downshift(env, st.n)
+    ds.planes.fill_(0.25)
+    e = torch.from_numpy(wl.e_tilde).to(torch.complex128).cuda()
+    b = torch.from_numpy(wl.b_tilde).to(torch.complex128).cuda()
+    envl = capi.fempic_envelope(_ptr(e), _ptr(b), 1.0)
+    hist = capi.fempic_downshift_history(st.n, _ptr(ds.planes))
+    before = st.to_numpy()
+    mixed = FempicEnv.from_mesh(wl.mesh, precision=1)
+    rc = lib.fempic_push_step_downshift(mixed.h, ds.h, C.byref(st.cstruct()), C.byref(hist), C.byref(envl),
+                                        wl.omega0, 0.0, wl.dt, 1, stream)
+    assert rc == capi.FEMPIC_EINVAL and "FP64 form" in capi.fempic_downshift_last_error()
+    p = st.cstruct()
+    p.w = None
+    rc = lib.fempic_push_step_downshift(env.h, ds.h, C.byref(p), C.byref(hist), C.byref(envl), wl.omega0, 0.0,
+                                        wl.dt, 1, stream)
+    assert rc == capi.FEMPIC_EINVAL
+    torch.cuda.synchronize()
+    after = st.to_numpy()
+    for k in ("x", "y", "z", "vx", "vy", "vz", "tet", "status"):
+        assert np.array_equal(before[k], after[k]), k
+    assert bool((ds.planes == 0.25).all())

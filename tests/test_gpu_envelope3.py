@@ -80,6 +80,7 @@ def test_push_step3_matches_oracle(prec):
         assert np.array_equal(g["n_cross"], ost.n_cross)
     else:
         assert same >= 0.99 and np.median(er) <= 1e-7 and np.median(ev) <= 2e-6 and eG <= 1e-5
+        assert er.max() <= 1e-6 and ev.max() <= 1e-5
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])

@@ -12,13 +12,14 @@ import math
 import numpy as np
 import pytest
 
-from oracle.oracle import OracleMesh, OracleState, push_step as oracle_push, run as oracle_run
+from oracle.oracle import (OracleMesh, OracleState, envelope_frame, push_step as oracle_push,
+                           run as oracle_run)
 from paper_2208_12795_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FP64, MIXED = 0, 1
+FP64, MIXED, Q24 = 0, 1, 2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -210,20 +211,70 @@ def test_bad_dof_dtype_rejected():
         env.push_step(st, e, b, 1.0, wl.omega0, 0.0, wl.dt)
 
 
+# ------------------------------------------------- envelope-frame deposit
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (MIXED, 1e-5), (Q24, 1e-4)])
+def test_envelope_frame_deposit_matches_oracle(prec, tol):
+    """fempic_deposit's outputs after every step: dG_out, G_cum_out and the
+    envelope-frame current G~ = e^{-j omega0 t_next} G_cum that the field
+    solve consumes (Sec. III-A forcing term, Sec. III-D G_integral).  G~ is
+    the oracle's envelope-frame map of the GPU's own G_cum to rounding (so
+    its phase is taken at t_next, not t), and the oracle's G~ within the
+    form's tolerance of its maximum."""
+    FempicEnv, ParticleState = _env_mod()
+    wl = I.workload_small()
+    steps = 12
+    env = FempicEnv.from_mesh(wl.mesh, precision=prec)
+    st = ParticleState.from_host(wl.particles, prec)
+    env.locate(st)
+    e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+    b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+    om = OracleMesh(wl.mesh.nodes, wl.mesh.tets)
+    tet, _ = om.locate(wl.particles.x, wl.particles.y, wl.particles.z)
+    ost = OracleState(wl.particles, tet)
+    oG = np.zeros(om.n_edges)
+    dG = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+    Gc = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+    Ge = torch.zeros(env.n_edges, dtype=torch.complex128, device="cuda")
+    G_sum = np.zeros(env.n_edges)
+    for n in range(steps):
+        t, t1 = n * wl.dt, (n + 1) * wl.dt
+        env.push_step(st, e, b, wl.amp(t), wl.omega0, t, wl.dt)
+        env.deposit(wl.omega0, t1, dG_out=dG, G_cum_out=Gc, G_env_out=Ge)
+        oracle_push(om, ost, wl.e_tilde, wl.b_tilde, wl.amp(t), wl.omega0, t, wl.dt, oG)
+        g_cum, g_env, d = Gc.cpu().numpy(), Ge.cpu().numpy(), dG.cpu().numpy()
+        G_sum += d
+        scale = np.abs(g_cum).max()
+        assert np.abs(G_sum - g_cum).max() <= 1e-14 * scale
+        own = envelope_frame(g_cum, wl.omega0, t1)
+        assert np.abs(g_env - own).max() <= 1e-15 * scale
+        ref = envelope_frame(oG, wl.omega0, t1)
+        err = np.abs(g_env - ref).max() / np.abs(ref).max()
+        assert err <= tol, (n, err)
+        # the phase of the step's own start time would not match
+        assert np.abs(g_env - envelope_frame(g_cum, wl.omega0, t)).max() > 1e-3 * scale
+    print(f"\n[envelope frame prec={prec}] after {steps} steps: rel err {err:.2e}")
+
+
 # ---------------------------------------------------------- mixed form
-# Stated error of the mixed form against the FP64 oracle (per workload):
+# Stated error of the mixed forms against the FP64 oracle (per workload):
 # median / max relative error of positions and velocities, max |dG| / max |G|.
+# The FP32 push sets the position and velocity errors of both forms; the
+# deposit error of the contract form follows the trajectories' (the path
+# integral itself is FP64-accurate), the 24-bit form adds its 2^-24 of a tet.
 MIXED_TOL = {
-    "cube4_2k_te101": dict(r_med=1e-7, r_max=1e-6, v_med=2e-6, v_max=1e-5, G=1e-5),
-    "cube4j_hot": dict(r_med=1e-5, r_max=1e-4, v_med=1e-5, v_max=1e-4, G=1e-4),
+    (MIXED, "cube4_2k_te101"): dict(r_med=1e-7, r_max=1e-6, v_med=2e-6, v_max=1e-5, G=1e-5, tet=0.99),
+    (MIXED, "cube4j_hot"): dict(r_med=1e-5, r_max=1e-4, v_med=1e-5, v_max=1e-4, G=1e-4, tet=0.99),
+    (Q24, "cube4_2k_te101"): dict(r_med=1e-7, r_max=1e-6, v_med=2e-6, v_max=1e-5, G=1e-4, tet=0.99),
+    (Q24, "cube4j_hot"): dict(r_med=1e-5, r_max=1e-4, v_med=1e-5, v_max=1e-4, G=1e-4, tet=0.99),
 }
 
 
+@pytest.mark.parametrize("prec", [MIXED, Q24])
 @pytest.mark.parametrize("maker", [I.workload_small, I.workload_hot_small])
-def test_mixed_error_vs_oracle_and_exact_conservation(maker):
+def test_mixed_error_vs_oracle_and_conservation(maker, prec):
     wl = maker()
     steps = min(wl.steps, 100)
-    env, st, G, rho0, rho1, _ = gpu_run(wl, MIXED, steps)
+    env, st, G, rho0, rho1, _ = gpu_run(wl, prec, steps)
     om, ost, oG, _ = oracle_run_wl(wl, steps)
     g = st.to_numpy()
     same_tet = (g["tet"] == ost.tet).mean()
@@ -231,30 +282,34 @@ def test_mixed_error_vs_oracle_and_exact_conservation(maker):
     ev = rel_vec_err((g["vx"], g["vy"], g["vz"]), (ost.vx, ost.vy, ost.vz), 1e-30)
     eG = np.abs(G - oG).max() / np.abs(oG).max()
     res = conservation_residual(env, G, rho0, rho1)
-    print(f"\n[mixed {wl.name}] tet agree {same_tet:.5f}  r err max {er.max():.2e} med {np.median(er):.2e}  "
+    print(f"\n[prec={prec} {wl.name}] tet agree {same_tet:.5f}  r err max {er.max():.2e} med {np.median(er):.2e}  "
           f"v err max {ev.max():.2e} med {np.median(ev):.2e}  G err {eG:.2e}  conservation {res:.2e}")
-    tol = MIXED_TOL[wl.name]
+    tol = MIXED_TOL[(prec, wl.name)]
     assert (g["status"] == 0).all()
     assert res <= 1e-13
-    assert same_tet >= 0.99
+    assert same_tet >= tol["tet"]
     assert np.median(er) <= tol["r_med"] and er.max() <= tol["r_max"]
     assert np.median(ev) <= tol["v_med"] and ev.max() <= tol["v_max"]
     assert eG <= tol["G"]
 
 
-def test_mixed_one_step_deposit_close_to_oracle():
-    """One step from identical FP64 inputs: the mixed deposit equals the exact
-    path integral to the resolution of its 24-bit barycentrics."""
+@pytest.mark.parametrize("prec,tol", [(MIXED, 2.0 ** -24), (Q24, 64 * 2.0 ** -24)])
+def test_mixed_one_step_deposit_close_to_oracle(prec, tol):
+    """One step from identical FP64 inputs: each mixed form's deposit is the
+    exact path integral of its own (FP32-pushed) trajectory; the difference
+    from the oracle's is the trajectory's FP32 error (contract form) plus the
+    24-bit barycentrics' resolution (24-bit form), in units of q w."""
     wl = I.workload_small()
-    env, st, G, _, _, _ = gpu_run(wl, MIXED, 1)
+    env, st, G, _, _, _ = gpu_run(wl, prec, 1)
     om, ost, oG, _ = oracle_run_wl(wl, 1)
     scale = abs(wl.particles.q[0] * wl.particles.w[0])
-    # each particle-segment contributes |error| <~ 4 * 2^-24 (q w)
-    assert np.abs(G - oG).max() <= 64 * 2.0 ** -24 * scale
+    err = np.abs(G - oG).max() / scale
+    print(f"\n[one-step deposit prec={prec}] max |dG - dG_oracle| = {err:.2e} q w")
+    assert err <= tol
 
 
 # ------------------------------------------------ full-size sampled parity
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, Q24])
 def test_full_size_cavity48_sampled(prec):
     """10M electrons on the 48^3 x 6 cube, one step in the benchmark's launch
     configuration; 20k sampled particles checked against the oracle one by
@@ -325,16 +380,18 @@ def _unaligned_copy(t):
     return v
 
 
-def test_mixed_staged_path_equals_plain_path():
+@pytest.mark.parametrize("prec", [MIXED, Q24])
+def test_mixed_staged_path_equals_plain_path(prec):
     """The bulk-copy staged common-path kernel (16-byte aligned particle
     arrays) and the plain kernel (unaligned arrays) give bit-identical
-    particles and, the deposit being integer, bit-identical dG."""
+    particles; dG is bit-identical in the 24-bit form (integer sums) and
+    equal to FP64 rounding in the contract form (FP64 atomics)."""
     FempicEnv, ParticleState = _env_mod()
     wl = I.te101_cavity(12, 2_000_000, 5.0, 1e4, 5, 7, dt=2e-9)   # ~13 tiles per staged CTA
     res = []
     for aligned in (True, False):
-        env = FempicEnv.from_mesh(wl.mesh, precision=MIXED)
-        st = ParticleState.from_host(wl.particles, MIXED)
+        env = FempicEnv.from_mesh(wl.mesh, precision=prec)
+        st = ParticleState.from_host(wl.particles, prec)
         if not aligned:
             for k in ("x", "y", "z", "vx", "vy", "vz", "tet", "status", "n_cross"):
                 setattr(st, k, _unaligned_copy(getattr(st, k)))
@@ -351,7 +408,10 @@ def test_mixed_staged_path_equals_plain_path():
     (a, Ga, sa), (b_, Gb, sb) = res
     for k in a:
         assert np.array_equal(a[k], b_[k]), k
-    assert np.array_equal(Ga, Gb)
+    if prec == Q24:
+        assert np.array_equal(Ga, Gb)
+    else:
+        assert np.abs(Ga - Gb).max() <= 1e-13 * np.abs(Ga).max()
     assert sa["crossings"] == sb["crossings"] > 0 and sa["wait_timeouts"] == sb["wait_timeouts"] == 0
 
 
@@ -384,7 +444,7 @@ def _sampled_parity(wl, prec, n_sample, seed):
     return same, er, ev, res, g, ost
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, Q24])
 def test_full_size_jittered64_beam_plasma_sampled(prec):
     """64^3 x 6 jittered cube, 5M 10 keV beam electrons (several face crossings
     per step) + 45M cosine-profile plasma electrons, random windowed DoFs."""
@@ -398,10 +458,11 @@ def test_full_size_jittered64_beam_plasma_sampled(prec):
         assert np.array_equal(g["n_cross"], ost.n_cross)
     else:
         assert same >= 0.999 and np.median(er) <= 1e-7 and np.median(ev) <= 1e-5
+        assert er.max() <= 1e-6 and ev.max() <= 1e-4
     assert res <= 1e-13
 
 
-@pytest.mark.parametrize("prec", [FP64, MIXED])
+@pytest.mark.parametrize("prec", [FP64, MIXED, Q24])
 def test_large96_two_species_slice_sampled(prec):
     """96^3 x 6 cube (5.3M tets) with the two-species load (electrons and
     1836 m_e ions at 2 eV) and random windowed DoFs, on a 4M-particle slice."""
@@ -421,4 +482,5 @@ def test_large96_two_species_slice_sampled(prec):
         assert same == 1.0 and er.max() <= 1e-12 and ev.max() <= 1e-12
     else:
         assert same >= 0.999 and np.median(er) <= 1e-7 and np.median(ev) <= 1e-5
+        assert er.max() <= 1e-6 and ev.max() <= 1e-4
     assert res <= 1e-13

@@ -92,3 +92,34 @@ def test_sort_noalloc_rejects_more_keys_than_its_scratch():
     assert rc == capi.FEMPIC_EINVAL
     assert "exceeds the fixed scratch" in capi.fempic_last_error()
     env.close()
+
+
+def test_sort_noalloc_takes_no_device_memory_after_the_first_call():
+    """After a warm-up call (which looks up the scratch area's address and
+    loads the kernels), further calls, on a larger key count than before,
+    leave the device's free memory exactly unchanged."""
+    capi, FempicEnv, ParticleState = _loaded()
+    rng = np.random.default_rng(99)
+    stream = torch.cuda.current_stream().cuda_stream
+    small = FempicEnv.from_mesh(I.kuhn_cube_mesh(5), precision=1)
+    big = FempicEnv.from_mesh(I.kuhn_cube_mesh(40), precision=1)        # 384,000 tets
+    ps = I.uniform_maxwellian(5000, 1.0, rng)
+    pb = I.concat_species([I.uniform_maxwellian(300_000, 1.0, rng),
+                           I.uniform_maxwellian(200_000, 2.0, rng, q=I.E_CHARGE, m=1836 * I.M_ELECTRON)])
+    ss, sb = _state(ParticleState, small, ps, 1, rng), _state(ParticleState, big, pb, 1, rng)
+    outs, outb = ss.empty_like(), sb.empty_like()
+    capi.fempic_sort_noalloc(small.h, ss.cstruct(), outs.cstruct(), stream)     # warm-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        capi.fempic_sort_noalloc(big.h, sb.cstruct(), outb.cstruct(), stream)
+        capi.fempic_sort_noalloc(small.h, ss.cstruct(), outs.cstruct(), stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert 2 * (big.n_tets + 1) > 100 * (small.n_tets + 1)              # far more keys than the warm-up
+    ref = sb.empty_like()
+    capi.fempic_sort(big.h, sb.cstruct(), ref.cstruct(), stream)
+    torch.cuda.synchronize()
+    _check_same(ref, outb, pb)
+    big.close()
+    small.close()
