@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--particles", type=int, default=10_000_000)
     ap.add_argument("--sort-every", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true", help="skip the side-by-side FP64 form")
+    ap.add_argument("--no-q24", action="store_true", help="skip the 24-bit mixed variant")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-particles", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=30)
@@ -261,7 +262,7 @@ def run_ours(args):
         return ParticleState(*arrs, sb, q, m, w, track_crossings=False)
 
     def timed_form(form):
-        prec = 1 if form == "mixed" else 0
+        prec = {"mixed": 1, "mixed_q24": 2, "fp64": 0}[form]
         env = FempicEnv.from_mesh(mesh, precision=prec)
         st = particle_state(prec)
         env.locate(st)
@@ -315,6 +316,11 @@ def run_ours(args):
     out = {}
     mixed = timed_form("mixed")
     out["mixed"] = mixed
+    if not args.no_q24:
+        q = timed_form("mixed_q24")
+        out["mixed_q24"] = q
+        q["env"].close()
+        del q["st"], q["scratch"]
     if not args.no_fp64:
         f64 = timed_form("fp64")
         out["fp64"] = f64
@@ -615,7 +621,8 @@ def report(args, world, n_p, out, cpu, adj=None):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64 mixed (FP32 gather/carrier/Boris; FP64 positions; int64 exact deposit)",
+        "dtype": "f32+f64 mixed (FP32 gather/carrier/Boris; FP64 positions; FP64-accurate exit parameter, "
+                 "crossing barycentrics and deposit; FP64 edge accumulation)",
         "data": DATA_DESC[args.workload],
         "config": {
             "workload": WORKLOAD_DESC[args.workload],
@@ -659,6 +666,16 @@ def report(args, world, n_p, out, cpu, adj=None):
         rec["fp64_form"] = {"value": total / (f["ms"] / 1e3), "ms_per_step": f["ms"] / K,
                             "push_avg_launch_ms": tf * 1e3, "hbm_frac": bf / tf / 1e9 / peak,
                             "clocks": f["clocks"]}
+    if "mixed_q24" in out:
+        q = out["mixed_q24"]
+        qp = q["prof"]["push"]
+        tq = qp["ms"] / max(qp["launches"], 1) / 1e3
+        rec["mixed_q24"] = {"value": total / (q["ms"] / 1e3), "ms_per_step": q["ms"] / K,
+                            "push_avg_launch_ms": tq * 1e3, "hbm_frac_push": b_alg / tq / 1e9 / peak,
+                            "hbm_frac_step": b_alg / (q["ms"] / K / 1e3) / 1e9 / peak,
+                            "kernel_ms": {k: v["ms"] for k, v in q["prof"].items() if v["launches"]},
+                            "what": "FEMPIC_MIXED_Q24: tracking and deposit on 24-bit integer barycentrics "
+                                    "(exit parameter FP32, deposit exact in int64 at 2^-24 of a tet)"}
     if m.get("levels3") is not None:
         rec["levels3"] = m["levels3"]
     if "downshift" in out:

@@ -115,10 +115,9 @@ struct PushArgs {
   double* dG;                   // FP64 form accumulator [Ne]
   unsigned long long* dGq;      // 24-bit form: per (species, tet) slots of the 6 local edges,
                                 // [ns][nt][8] int64 in units of 2^-48 (q w)
-  double* mom;                  // contract form: per (species, tet) moment slots [ns][nt][8]:
+  double* mom;                  // contract form: per (species, tet) moment slots [ns][nt][6]:
                                 // sum of D (3), sum of u x D (3), FP64
-  double* xhi;                  // contract form: crossing-pass edge deposits [ns][nt][8], FP64 part
-  float* xlo;                   // and their low FP32 parts [ns][nt][8]
+  float* momlo;                 // low FP32 parts of the crossing pass's moments [ns][nt][8]
   const float4* tetdf;          // contract form: low FP32 parts of grad lambda_1..3, [nt][4] float4
   unsigned long long* stats;    // [0] crossings, [1] frozen, [2] staging wait timeouts
   CrossRec* xrec;               // mixed form: crossing records, 256-slot region per tile
@@ -899,19 +898,25 @@ __device__ __forceinline__ DF f64_to_df(double r) {
 // like the 24-bit form's integers, and the run head adds the sums, as FP64,
 // to the tet's moment slot with FP64 atomics.
 
-// x / 2^(emax - 177) as an integer (rounded), emax the biased exponent of
-// the warp's largest |x|: |result| < 2^51, so 32 lanes sum below 2^56.
-__device__ __forceinline__ long long fx_scaled(float x, unsigned emax) {
+// x / 2^(emax - 177) as an integer, rounded half away from zero, with emax
+// the biased exponent of the warp's largest |x| (bias = 27 - emax): |result|
+// < 2^51, so 32 lanes sum below 2^56.  32-bit operations only: the 24-bit
+// significand is shifted left into a word pair, or rounded right.
+__device__ __forceinline__ long long fx_scaled(float x, int bias) {
   const unsigned u = __float_as_uint(x);
   const int ex = (int)((u >> 23) & 0xffu);
-  if (ex == 0) return 0;   // zero or below 2^-126
-  const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
-  const int sh = ex - (int)emax + 27;
-  long long v = 0;
-  if (sh >= 0)
-    v = m << sh;
-  else if (sh > -25)
-    v = (m + (1ll << (-sh - 1))) >> (-sh);
+  const unsigned m = (u & 0x7fffffu) | 0x800000u;
+  const int sh = ex + bias;   // <= 27
+  unsigned lo, hi = 0u;
+  if (sh >= 0) {
+    lo = m << sh;
+    hi = __funnelshift_l(m, 0u, (unsigned)sh);
+  } else {
+    const unsigned r = (unsigned)min(-sh, 31);
+    lo = (m + (1u << (r - 1u))) >> r;
+  }
+  if (ex == 0) lo = hi = 0u;   // zero or below 2^-126
+  const long long v = (long long)(((unsigned long long)hi << 32) | lo);
   return (u >> 31) ? -v : v;
 }
 
@@ -1120,10 +1125,11 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
       }
       eD = __reduce_max_sync(full, uD) >> 23;
       eM = __reduce_max_sync(full, uM) >> 23;
+      const int bD = 27 - (int)eD, bM = 27 - (int)eM;
 #pragma unroll
       for (int k = 0; k < 3; k++) {
-        o.gh[k] = fx_scaled(o.mv[k], eD);
-        o.gh[3 + k] = fx_scaled(o.mv[3 + k], eM) + fx_scaled(o.mv[6 + k], eM);
+        o.gh[k] = fx_scaled(o.mv[k], bD);
+        o.gh[3 + k] = fx_scaled(o.mv[3 + k], bM) + fx_scaled(o.mv[6 + k], bM);
       }
     }
     const int32_t prev = __shfl_up_sync(full, o.key, 1);
@@ -1131,8 +1137,10 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
     const unsigned heads = __ballot_sync(full, head);
     const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
     const int run_end = above ? (__ffs(above) - 2) : 31;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
+    // as many shuffle rounds as the warp's longest run needs
+    const unsigned longest = __reduce_max_sync(full, head ? (unsigned)(run_end - lane + 1) : 0u);
+#pragma unroll 1
+    for (int off = 1; off < (int)longest; off <<= 1) {
 #pragma unroll
       for (int e = 0; e < 6; e++) {
         const long long v = __shfl_down_sync(full, o.gh[e], off);
@@ -1146,7 +1154,7 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
         for (int e = 0; e < 6; e++)
           if (o.gh[e]) atomicAdd(base + e, (unsigned long long)o.gh[e]);
       } else {
-        double* base = A.mom + ((int64_t)o.shome * A.nt + o.Thome) * 8;
+        double* base = A.mom + ((int64_t)o.shome * A.nt + o.Thome) * 6;
 #pragma unroll
         for (int e = 0; e < 6; e++)
           if (o.gh[e]) atomicAdd(base + e, i64_to_f64(o.gh[e], (int)(e < 3 ? eD : eM) - 177));
@@ -1576,8 +1584,9 @@ __global__ void __launch_bounds__(kThreads) k_cross_q24(PushArgs A, int64_t ntil
 struct CrossStateDF {
   double a0[3], b[3];   // the current straight run goes from a0 to b ...
   DF S;                 // ... and the current piece starts at a0 + S (b - a0)
+  FF w[3];              // b - a0 as FP32 pairs (before a reflection: exactly dt v)
   DF la[4];             // barycentrics of the piece start in T
-  float vn[3];
+  unsigned flips;       // bit k: velocity component k mirrored an odd number of times
   int32_t T, p;
   int entry, nc, s;
   uint8_t st;
@@ -1587,8 +1596,8 @@ struct CrossStateDF {
 // lambda(r) in tet T in double-float: d = r - x0 exact in FP64 and split into
 // FP32 pairs, lambda_k = (G_k,hi + G_k,lo) . d for k = 1..3 from exact
 // products of the high parts, lambda_0 = 1 - lambda_1 - lambda_2 - lambda_3.
-__device__ __forceinline__ void lambda_df(const Geo32& G, const float glo[9], const double r[3], DF lam[4]) {
-  FF dd[3];
+__device__ __forceinline__ void lambda_df(const Geo32& G, const float glo[9], const double r[3], DF lam[4],
+                                          FF dd[3]) {
   float d32[3];
   dpos(G, r[0], r[1], r[2], dd, d32);
 #pragma unroll
@@ -1613,20 +1622,39 @@ __device__ __forceinline__ void ld_glo(const float4* __restrict__ tetdf, int64_t
   glo[8] = c.x;
 }
 
-// Edge-form deposit of the piece la -> lb in tet T (species s).
-__device__ __forceinline__ void deposit_df(const PushArgs& A, int32_t T, int s, const DF la[4], const DF lb[4]) {
-  if (!A.xhi) return;   // deposits off
-  const int64_t slot = ((int64_t)s * A.nt + T) * 8;
-  float lo[6];
+// Moment-form deposit of the piece of the run a0 -> b between path fractions
+// S and S + dS, inside tet T (species s): its displacement dS w and its
+// moment about x0, (a0 + S w - x0) x (dS w) = dS ((a0 - x0) x w) (w x w = 0),
+// the quantities the common path deposits for a whole segment.  a0 - x0 is
+// (b - x0) - w, from the pair the barycentrics of b were formed with.  The
+// high FP32 parts go to the FP64 moment slot, the low parts to its FP32
+// companion.
+__device__ __forceinline__ void deposit_piece_df(const PushArgs& A, int s, int32_t T, const FF w[3],
+                                                 const FF db[3], DF dS) {
+  if (!A.mom) return;   // deposits off
+  DF u[3];
 #pragma unroll
-  for (int e = 0; e < 6; e++) {
-    const int i = le0(e), j = le1(e);
-    const DF g = df_sub(df_mul(la[i], lb[j]), df_mul(la[j], lb[i]));
-    atomicAdd(A.xhi + slot + e, f32_to_f64(g.h));
-    lo[e] = g.l;
+  for (int k = 0; k < 3; k++) u[k] = df_sub(DF{db[k].hi, db[k].lo}, DF{w[k].hi, w[k].lo});
+  float lo[6];
+  double* ms = A.mom + ((int64_t)s * A.nt + T) * 6;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const int i = (k + 1) % 3, j = (k + 2) % 3;   // (u x w)_k = u_i w_j - u_j w_i
+    const DF p1 = two_prod(u[i].h, w[j].hi), p2 = two_prod(u[j].h, w[i].hi);
+    const DF sd = two_sum(p1.h, -p2.h);
+    float e = __fadd_rn(sd.l, __fsub_rn(p1.l, p2.l));
+    e = __fmaf_rn(u[i].h, w[j].lo, __fmaf_rn(u[i].l, w[j].hi, e));
+    e = __fmaf_rn(-u[j].h, w[i].lo, __fmaf_rn(-u[j].l, w[i].hi, e));
+    const DF m = df_mul(dS, fast_two_sum(sd.h, e));
+    const DF d = df_mul(dS, DF{w[k].hi, w[k].lo});
+    atomicAdd(ms + k, f32_to_f64(d.h));
+    atomicAdd(ms + 3 + k, f32_to_f64(m.h));
+    lo[k] = d.l;
+    lo[3 + k] = m.l;
   }
-  atomicAdd(reinterpret_cast<float4*>(A.xlo + slot), make_float4(lo[0], lo[1], lo[2], lo[3]));
-  atomicAdd(reinterpret_cast<float2*>(A.xlo + slot + 4), make_float2(lo[4], lo[5]));
+  float* ls = A.momlo + ((int64_t)s * A.nt + T) * 8;
+  atomicAdd(reinterpret_cast<float4*>(ls), make_float4(lo[0], lo[1], lo[2], lo[3]));
+  atomicAdd(reinterpret_cast<float2*>(ls + 4), make_float2(lo[4], lo[5]));
 }
 
 __device__ __forceinline__ void cross_begin_df(const PushArgs& A, const CrossRec& r, CrossStateDF& c) {
@@ -1637,9 +1665,10 @@ __device__ __forceinline__ void cross_begin_df(const PushArgs& A, const CrossRec
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     c.a0[k] = r.a[k];
-    c.vn[k] = r.v[k];
     c.b[k] = advance(r.a[k], dt32, r.v[k]);
+    c.w[k] = FF{__fmul_rn(dt32, r.v[k]), 0.f};
   }
+  c.flips = 0u;
   c.S = DF{0.f, 0.f};
   c.entry = -1;
   c.nc = 0;
@@ -1659,12 +1688,13 @@ __device__ __forceinline__ void cross_point_df(const CrossStateDF& c, double r[3
 // Returns true when the particle's step is complete.
 __device__ __forceinline__ bool cross_advance_df(const PushArgs& A, CrossStateDF& c, bool fresh) {
   DF lb[4];
+  FF db[3];   // b - x0 of this tet
   {
     const Geo32 G = ld_geo(A.tetrec, c.T);
     float glo[9];
     ld_glo(A.tetdf, c.T, glo);
-    if (fresh) lambda_df(G, glo, c.a0, c.la);
-    lambda_df(G, glo, c.b, lb);
+    if (fresh) lambda_df(G, glo, c.a0, c.la, db);
+    lambda_df(G, glo, c.b, lb, db);
   }
   int kx = -1;
   DF smin = DF{INFINITY, 0.f};
@@ -1679,17 +1709,19 @@ __device__ __forceinline__ bool cross_advance_df(const PushArgs& A, CrossStateDF
       kx = k;
     }
   }
+  const DF rest = df_sub(DF{1.0f, 0.0f}, c.S);   // fraction of the run still ahead
   if (kx < 0) {
-    deposit_df(A, c.T, c.s, c.la, lb);
+    deposit_piece_df(A, c.s, c.T, c.w, db, rest);
     return true;
   }
   DF lp[4];
 #pragma unroll
   for (int i = 0; i < 4; i++)
     lp[i] = (i == kx) ? DF{0.f, 0.f} : df_add(c.la[i], df_mul(smin, df_sub(lb[i], c.la[i])));
-  deposit_df(A, c.T, c.s, c.la, lp);
+  const DF dS = df_mul(smin, rest);
+  deposit_piece_df(A, c.s, c.T, c.w, db, dS);
   c.nc++;
-  c.S = df_add(c.S, df_mul(smin, df_sub(DF{1.0f, 0.0f}, c.S)));
+  c.S = df_add(c.S, dS);
   if (c.nc > A.max_cross) {
     c.st = FEMPIC_P_CAP;
     c.moved = false;
@@ -1718,19 +1750,21 @@ __device__ __forceinline__ bool cross_advance_df(const PushArgs& A, CrossStateDF
     c.entry = ent;
   } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
     // the wall point in FP64 starts the mirrored rest of the step
-    double w[3];
-    cross_point_df(c, w);
+    double wp[3];
+    cross_point_df(c, wp);
 #pragma unroll
-    for (int k = 0; k < 3; k++) c.a0[k] = w[k];
+    for (int k = 0; k < 3; k++) c.a0[k] = wp[k];
     c.S = DF{0.f, 0.f};
     const int code = -1 - nbt, ax = code >> 1, side = code & 1;
 #pragma unroll
-    for (int k = 0; k < 3; k++)
+    for (int k = 0; k < 3; k++) {
       if (k == ax) {
         const double L = side ? A.hi[k] : A.lo[k];
         c.b[k] = 2.0 * L - c.b[k];
-        c.vn[k] = -c.vn[k];
+        c.flips ^= 1u << k;
       }
+      c.w[k] = split_f64(__dsub_rn(c.b[k], c.a0[k]));
+    }
     c.reflected = true;
 #pragma unroll
     for (int j = 0; j < 4; j++) c.la[j] = lp[j];
@@ -1757,11 +1791,11 @@ __device__ __forceinline__ void cross_finish_df(const PushArgs& A, const CrossSt
     A.y[p] = c.b[1];
     A.z[p] = c.b[2];
   }
-  if (c.reflected) {
-    static_cast<float*>(A.vx)[p] = c.vn[0];
-    static_cast<float*>(A.vy)[p] = c.vn[1];
-    static_cast<float*>(A.vz)[p] = c.vn[2];
-  }
+  // the common path stored the new velocity; mirror the reflected components
+  float* vv[3] = {static_cast<float*>(A.vx), static_cast<float*>(A.vy), static_cast<float*>(A.vz)};
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+    if (c.flips & (1u << k)) vv[k][p] = -vv[k][p];
   int32_t T = c.T;
   if (c.st != FEMPIC_P_OK) {
     A.status[p] = c.st;
@@ -1830,8 +1864,7 @@ struct TetFinalizeArgs {
   const float4* tetrec;
   const float4* tetdf;
   double* mom;
-  double* xhi;
-  float* xlo;
+  float* momlo;
   float qwh[kMaxSpecies], qwl[kMaxSpecies];   // q w per species as FP32 pairs
   float4* out;                                // [nt][3]: (h, l) of local edges 0..5
 };
@@ -1845,61 +1878,61 @@ __device__ __forceinline__ void df_cross(const DF a[3], const DF b[3], DF c[3]) 
 __global__ void __launch_bounds__(kThreads) k_tet_finalize(TetFinalizeArgs A) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= A.nt) return;
-  DF acc[6];
-#pragma unroll
-  for (int e = 0; e < 6; e++) acc[e] = DF{0.f, 0.f};
-  bool have_geo = false;
-  DF G[4][3];
+  // the slots' sums, as FP32 pairs, scaled by q w and summed over species
+  // (the conversion below is linear in them)
+  DF S[3] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}}, M[3] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+  bool any = false;
   for (int s = 0; s < A.ns; s++) {
-    const int64_t slot = ((int64_t)s * A.nt + t) * 8;
-    double2* m2 = reinterpret_cast<double2*>(A.mom + slot);
-    double2* x2 = reinterpret_cast<double2*>(A.xhi + slot);
-    const double2 m01 = m2[0], m23 = m2[1], m45 = m2[2];
-    const double2 x01 = x2[0], x23 = x2[1], x45 = x2[2];
-    float4* l4 = reinterpret_cast<float4*>(A.xlo + slot);
-    const float4 lA = l4[0], lB = l4[1];
-    const double mv[6] = {m01.x, m01.y, m23.x, m23.y, m45.x, m45.y};
-    const double xv[6] = {x01.x, x01.y, x23.x, x23.y, x45.x, x45.y};
-    const float lv[6] = {lA.x, lA.y, lA.z, lA.w, lB.x, lB.y};
-    bool any = false;
+    double2* m2 = reinterpret_cast<double2*>(A.mom + ((int64_t)s * A.nt + t) * 6);
+    float4* l4 = reinterpret_cast<float4*>(A.momlo + ((int64_t)s * A.nt + t) * 8);
+    const double2 a = m2[0], b = m2[1], c = m2[2];
+    const float4 la = l4[0], lb = l4[1];
+    const double mv[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
+    const float lv[6] = {la.x, la.y, la.z, la.w, lb.x, lb.y};
+    bool here = false;
 #pragma unroll
-    for (int e = 0; e < 6; e++) any = any || mv[e] != 0.0 || xv[e] != 0.0 || lv[e] != 0.f;
-    if (!any) continue;
+    for (int e = 0; e < 6; e++) here = here || mv[e] != 0.0 || lv[e] != 0.f;
+    if (!here) continue;
+    any = true;
     const double2 z2 = make_double2(0.0, 0.0);
     m2[0] = m2[1] = m2[2] = z2;
-    x2[0] = x2[1] = x2[2] = z2;
     l4[0] = l4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!have_geo) {
-      const float4 a = __ldg(A.tetrec + 8 * t + 1), b = __ldg(A.tetrec + 8 * t + 2), c = __ldg(A.tetrec + 8 * t + 3);
-      const float4 p = __ldg(A.tetdf + 4 * t), q = __ldg(A.tetdf + 4 * t + 1), r = __ldg(A.tetdf + 4 * t + 2);
-      const float gh[9] = {a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z};
-      const float gl[9] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w, r.x};
-#pragma unroll
-      for (int k = 0; k < 3; k++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) G[k + 1][j] = fast_two_sum(gh[3 * k + j], gl[3 * k + j]);
-#pragma unroll
-      for (int j = 0; j < 3; j++) G[0][j] = df_neg(df_add(df_add(G[1][j], G[2][j]), G[3][j]));
-      have_geo = true;
-    }
-    const DF S[3] = {f64_to_df(mv[0]), f64_to_df(mv[1]), f64_to_df(mv[2])};
-    const DF M[3] = {f64_to_df(mv[3]), f64_to_df(mv[4]), f64_to_df(mv[5])};
     const DF qw = DF{A.qwh[s], A.qwl[s]};
 #pragma unroll
-    for (int e = 0; e < 6; e++) {
-      const int i = le0(e), j = le1(e);
-      DF C[3];
-      df_cross(G[i], G[j], C);
-      DF g = df_dot3(C, M);
-      if (i == 0) g = df_add(g, df_dot3(G[j], S));
-      g = df_add(g, df_add(f64_to_df(xv[e]), DF{lv[e], 0.f}));
-      acc[e] = df_add(acc[e], df_mul(g, qw));
+    for (int k = 0; k < 3; k++) {
+      S[k] = df_add(S[k], df_mul(qw, df_add(f64_to_df(mv[k]), DF{lv[k], 0.f})));
+      M[k] = df_add(M[k], df_mul(qw, df_add(f64_to_df(mv[3 + k]), DF{lv[3 + k], 0.f})));
     }
   }
   float4* o = A.out + 3 * t;
-  o[0] = make_float4(acc[0].h, acc[0].l, acc[1].h, acc[1].l);
-  o[1] = make_float4(acc[2].h, acc[2].l, acc[3].h, acc[3].l);
-  o[2] = make_float4(acc[4].h, acc[4].l, acc[5].h, acc[5].l);
+  if (!any) {
+    o[0] = o[1] = o[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  // gradients G_1..3 as FP32 pairs, G_0 = -(G_1 + G_2 + G_3)
+  const float4 a = __ldg(A.tetrec + 8 * t + 1), b = __ldg(A.tetrec + 8 * t + 2), c = __ldg(A.tetrec + 8 * t + 3);
+  const float4 p = __ldg(A.tetdf + 4 * t), q = __ldg(A.tetdf + 4 * t + 1), r = __ldg(A.tetdf + 4 * t + 2);
+  const float gh[9] = {a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z};
+  const float gl[9] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w, r.x};
+  DF G[4][3];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) G[k + 1][j] = fast_two_sum(gh[3 * k + j], gl[3 * k + j]);
+#pragma unroll
+  for (int j = 0; j < 3; j++) G[0][j] = df_neg(df_add(df_add(G[1][j], G[2][j]), G[3][j]));
+  DF g[6];
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const int i = le0(e), j = le1(e);
+    DF C[3];
+    df_cross(G[i], G[j], C);
+    g[e] = df_dot3(C, M);
+    if (i == 0) g[e] = df_add(g[e], df_dot3(G[j], S));
+  }
+  o[0] = make_float4(g[0].h, g[0].l, g[1].h, g[1].l);
+  o[1] = make_float4(g[2].h, g[2].l, g[3].h, g[3].l);
+  o[2] = make_float4(g[4].h, g[4].l, g[5].h, g[5].l);
 }
 
 struct FinalizeArgs {
@@ -2565,9 +2598,8 @@ struct fempic_env {
   unsigned long long* dGq = nullptr;   // 24-bit form [dGq_species][nt][8]
   int32_t dGq_species = 0;
   float4* tetdf = nullptr;             // contract form: low parts of grad lambda_1..3, [nt][4]
-  double* mom = nullptr;               // contract form: moment slots [dGq_species][nt][8]
-  double* xhi = nullptr;               // contract form: crossing deposits [dGq_species][nt][8]
-  float* xlo = nullptr;                // their low parts [dGq_species][nt][8]
+  double* mom = nullptr;               // contract form: moment slots [dGq_species][nt][6]
+  float* momlo = nullptr;              // their low FP32 parts [dGq_species][nt][8]
   float4* tetout = nullptr;            // contract form: per-tet edge values of a step [nt][3]
   double* Gcum = nullptr;
   unsigned long long* stats = nullptr;
@@ -2645,7 +2677,7 @@ static void free_env(fempic_env* e) {
   if (!e) return;
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq, e->tetdf, e->mom,
-                  e->xhi, e->xlo, e->tetout,
+                  e->momlo, e->tetout,
                   e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->tadj, e->estart, e->eslot, e->fslot, e->xrec, e->xrec64, e->xcount,
                   nullptr};
   for (void* q : ptrs)
@@ -2944,22 +2976,19 @@ static int ensure_mixed_accumulators(fempic_env* env, int ns, cudaStream_t st) {
     if (env->dGq) cudaFree(env->dGq);
     env->dGq = nq;
   } else {
-    double *nm = nullptr, *nh = nullptr;
+    const size_t nmom = (size_t)ns * env->h.nt * 6;
+    double* nm = nullptr;
     float* nl = nullptr;
-    FEMPIC_CUDA(dalloc(&nm, nslot));
-    FEMPIC_CUDA(dalloc(&nh, nslot));
+    FEMPIC_CUDA(dalloc(&nm, nmom));
     FEMPIC_CUDA(dalloc(&nl, nslot));
-    FEMPIC_CUDA(cudaMemsetAsync(nm, 0, nslot * sizeof(double), st));
-    FEMPIC_CUDA(cudaMemsetAsync(nh, 0, nslot * sizeof(double), st));
+    FEMPIC_CUDA(cudaMemsetAsync(nm, 0, nmom * sizeof(double), st));
     FEMPIC_CUDA(cudaMemsetAsync(nl, 0, nslot * sizeof(float), st));
     if (env->mom) {
       cudaFree(env->mom);
-      cudaFree(env->xhi);
-      cudaFree(env->xlo);
+      cudaFree(env->momlo);
     }
     env->mom = nm;
-    env->xhi = nh;
-    env->xlo = nl;
+    env->momlo = nl;
     if (!env->tetout) {
       FEMPIC_CUDA(dalloc(&env->tetout, 3 * env->h.nt));
       FEMPIC_CUDA(cudaMemsetAsync(env->tetout, 0, 3 * env->h.nt * sizeof(float4), st));
@@ -3072,8 +3101,7 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
   A.dG = env->deposit_on ? env->dG : nullptr;
   A.dGq = env->deposit_on ? env->dGq : nullptr;
   A.mom = env->deposit_on ? env->mom : nullptr;
-  A.xhi = env->deposit_on ? env->xhi : nullptr;
-  A.xlo = env->xlo;
+  A.momlo = env->momlo;
   A.tetdf = env->tetdf;
   A.stats = env->stats;
   rc = ensure_xqueue(env, p->n, st);
@@ -3238,8 +3266,7 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
       T.tetrec = env->tetrec;
       T.tetdf = env->tetdf;
       T.mom = env->mom;
-      T.xhi = env->xhi;
-      T.xlo = env->xlo;
+      T.momlo = env->momlo;
       for (int s = 0; s < kMaxSpecies; s++) {
         T.qwh[s] = (float)env->qw_last[s];
         T.qwl[s] = (float)(env->qw_last[s] - (double)T.qwh[s]);
@@ -3271,9 +3298,8 @@ extern "C" int fempic_reset_deposit(fempic_env* env, void* stream) {
   const size_t nslot = (size_t)env->dGq_species * env->h.nt * 8;
   if (env->dGq) FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, nslot * sizeof(unsigned long long), st));
   if (env->mom) {
-    FEMPIC_CUDA(cudaMemsetAsync(env->mom, 0, nslot * sizeof(double), st));
-    FEMPIC_CUDA(cudaMemsetAsync(env->xhi, 0, nslot * sizeof(double), st));
-    FEMPIC_CUDA(cudaMemsetAsync(env->xlo, 0, nslot * sizeof(float), st));
+    FEMPIC_CUDA(cudaMemsetAsync(env->mom, 0, (size_t)env->dGq_species * env->h.nt * 6 * sizeof(double), st));
+    FEMPIC_CUDA(cudaMemsetAsync(env->momlo, 0, nslot * sizeof(float), st));
   }
   return FEMPIC_OK;
 }
