@@ -49,6 +49,7 @@ WORKLOAD_DESC = {
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal, for context next to the measured copy peak
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "push_mixed_cube48_10M.txt")
+FP64_SUMMARY = os.path.join(ROOT, "profiles", "fp64_ops_cube48_4M.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2208_12795_gb300", "csrc", f)
                   for f in ("fempic_env.cu", "fempic_internal.h")]
 
@@ -70,6 +71,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient-window measurement")
     ap.add_argument("--no-levels3", action="store_true", help="skip the three-level envelope measurement")
     ap.add_argument("--no-downshift", action="store_true", help="skip the downshifted-integrator measurement")
+    ap.add_argument("--no-errors", action="store_true", help="skip the per-quantity error report against the oracle")
+    ap.add_argument("--no-large", action="store_true", help="skip the 50M jittered and 400M two-species legs")
+    ap.add_argument("--large-steps", type=int, default=5)
     ap.add_argument("--workload", choices=("cube48", "jittered64", "large96"), default="cube48",
                     help="cube48: 48^3x6 cube, 10M e- (headline); jittered64: 64^3x6 jittered cube, 50M "
                          "(10 keV beam + cosine plasma), random DoFs; large96: 96^3x6 cube, 400M e- + ions")
@@ -111,13 +115,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profile_value(key):
-    """A per-particle figure from the committed ncu summary; None when absent
+def _profile_value(key, path=PROFILE_SUMMARY):
+    """A per-particle figure from a committed ncu summary; None when absent
     or when the kernel source changed since the capture."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    if not os.path.exists(path):
         return None
     kv = {}
-    for line in open(PROFILE_SUMMARY):
+    for line in open(path):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
@@ -151,6 +155,146 @@ def issue_roofline(n_p, t_launch_s, sm_mhz):
             "unit": "warp instructions/s", "frac": achieved / peak, "warp_instructions_per_launch": ipp * n_p,
             "avg_launch_ms": t_launch_s * 1e3,
             "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz (median SM clock sampled in the timed region)"}
+
+
+def fp64_roofline(n_p, t_launch_s, rate):
+    """FP64-pipe roofline of the FP64 form's push group (k_push_fp64 +
+    k_cross_fp64): FP64 lane operations per launch (ncu count per particle,
+    scaled to n_p) over the launch time, against the FP64 FMA rate measured
+    in this run."""
+    opp = _profile_value("fp64_lane_ops_per_particle", FP64_SUMMARY)
+    if opp is None or t_launch_s <= 0 or not rate:
+        return None
+    achieved = opp * n_p / t_launch_s
+    return {"kernel": "k_push_fp64 + k_cross_fp64", "bound": "fp64", "achieved": achieved, "peak": rate,
+            "unit": "FP64 lane-ops/s", "frac": achieved / rate, "fp64_lane_ops_per_particle": opp,
+            "peak_source": "fempic_measure_fp64_rate: independent FMA chains on every SM, this run"}
+
+
+def large_leg(kind, steps, warmup, sort_every):
+    """Forward step of the 64^3 jittered beam + plasma load (50M) or of the
+    96^3 two-species load (400M), contract mixed form, particles drawn on the
+    device; timed with CUDA events like the headline."""
+    import torch
+    from paper_2208_12795_gb300 import inputs as I
+    from paper_2208_12795_gb300.env import FempicEnv, ParticleState
+    if kind == "jittered64":
+        wl = I.workload_jittered64(n_particles=2)
+        cols, table = I.device_beam_plasma(50_000_000, I.SEED_BASE + 30)
+    else:
+        wl = I.workload_large96(n_particles=2)
+        cols, table = I.device_two_species(400_000_000, I.SEED_BASE + 50, vdtype=torch.float32)
+    n = int(cols[0].numel())
+    vel = [c.to(torch.float32) for c in cols[3:]]
+    st = ParticleState(cols[0], cols[1], cols[2], vel[0], vel[1], vel[2], *table, track_crossings=False)
+    del cols
+    env = FempicEnv.from_mesh(wl.mesh, precision=1)
+    env.locate(st)
+    scratch = st.empty_like()
+    env.sort(st, scratch)
+    e = torch.from_numpy(wl.e_tilde).to(torch.complex64).cuda()
+    b = torch.from_numpy(wl.b_tilde).to(torch.complex64).cuda()
+
+    def step(k):
+        t = k * wl.dt
+        env.push_step(st, e, b, wl.amp(t), wl.omega0, t, wl.dt)
+        env.deposit(wl.omega0, t + wl.dt)
+        if sort_every > 0 and (k + 1) % sort_every == 0:
+            env.sort(st, scratch)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    st0 = env.stats()
+    env.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for k in range(warmup, warmup + steps):
+        step(k)
+    ev1.record()
+    torch.cuda.synchronize()
+    env.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    prof = env.profile_read()
+    st1 = env.stats()
+    counts = (env.n_nodes, env.n_edges, env.n_faces, env.n_tets)
+    b_alg = bytes_alg_per_step(n, counts, "mixed")
+    peak = measured_peaks()[0]
+    push = prof["push"]
+    t_push = push["ms"] / max(push["launches"], 1) / 1e3
+    out = {"workload": WORKLOAD_DESC[kind] + " (particles drawn on the device)", "form": "mixed",
+           "value": n * steps / (ms / 1e3), "unit": "particle-steps/s", "steps": steps, "warmup": warmup,
+           "ms_per_step": ms / steps, "algorithmic_bytes_per_step": b_alg,
+           "hbm_frac_step": b_alg / (ms / steps / 1e3) / 1e9 / peak,
+           "hbm_frac_push": b_alg / t_push / 1e9 / peak,
+           "crossings_per_particle_step": (st1["crossings"] - st0["crossings"]) / (n * steps),
+           "kernel_ms_per_step": {k: v["ms"] / steps for k, v in prof.items() if v["launches"]},
+           "sort_every": sort_every}
+    env.close()
+    del st, scratch
+    torch.cuda.empty_cache()
+    return out
+
+
+def config2_errors(wl, n_sub, steps):
+    """Per-quantity error of the GPU forms against the FP64 oracle on the 48^3
+    cube workload: the first n_sub particles for `steps` steps, same seeded
+    inputs on both sides."""
+    import torch
+    from oracle.oracle import OracleMesh, OracleState, push_step as oracle_push
+    from paper_2208_12795_gb300.env import FempicEnv, ParticleState
+    P = wl.particles.subset(n_sub)
+    om = OracleMesh(wl.mesh.nodes, wl.mesh.tets)
+    tet0, _ = om.locate(P.x, P.y, P.z)
+    ost = OracleState(P, tet0)
+    oG = np.zeros(om.n_edges)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        oracle_push(om, ost, wl.e_tilde, wl.b_tilde, wl.amp(k * wl.dt), wl.omega0, k * wl.dt, wl.dt, oG)
+    t_or = time.perf_counter() - t0
+    en = None
+    res = {"workload": f"cube48 TE101 10 kV/m, first {n_sub} of the 10M electrons, {steps} steps "
+                       f"(dt 0.5 ns, ramp sigma 20 ns)",
+           "note": "positions in m (absolute), velocities relative; G_cum relative to max |G_cum|; a particle "
+                   "whose FP32 trajectory passes within rounding of a face can take the other tet and then "
+                   "sample other fields, which sets the max of the mixed forms",
+           "oracle_s": t_or, "oracle_crossings_per_particle": float(ost.n_cross.mean())}
+    for name, prec in (("fp64", 0), ("mixed", 1), ("mixed_q24", 2)):
+        env = FempicEnv.from_mesh(wl.mesh, precision=prec)
+        st = ParticleState.from_host(P, prec)
+        env.locate(st)
+        e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+        b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+        G = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+        rho0 = env.nodal_charge(st)
+        for k in range(steps):
+            t = k * wl.dt
+            env.push_step(st, e, b, wl.amp(t), wl.omega0, t, wl.dt)
+            env.deposit(wl.omega0, t + wl.dt, G_cum_out=G)
+        rho1 = env.nodal_charge(st).cpu().numpy()
+        rho0 = rho0.cpu().numpy()
+        g = st.to_numpy()
+        Gg = G.cpu().numpy()
+        if en is None:
+            en = env.query()["edge_nodes"]
+        div = np.zeros(env.n_nodes)
+        np.add.at(div, en[:, 1], Gg)
+        np.subtract.at(div, en[:, 0], Gg)
+        er = np.sqrt((g["x"] - ost.x) ** 2 + (g["y"] - ost.y) ** 2 + (g["z"] - ost.z) ** 2)
+        vr = np.sqrt(ost.vx ** 2 + ost.vy ** 2 + ost.vz ** 2)
+        ev = np.sqrt((g["vx"] - ost.vx) ** 2 + (g["vy"] - ost.vy) ** 2 + (g["vz"] - ost.vz) ** 2) / vr
+        gerr = np.abs(Gg - oG) / np.abs(oG).max()
+        res[name] = {"r_err_max_m": float(er.max()), "r_err_p999_m": float(np.quantile(er, 0.999)),
+                     "r_err_p99_m": float(np.quantile(er, 0.99)), "r_err_median_m": float(np.median(er)),
+                     "v_rel_err_max": float(ev.max()), "v_rel_err_p999": float(np.quantile(ev, 0.999)),
+                     "v_rel_err_p99": float(np.quantile(ev, 0.99)), "v_rel_err_median": float(np.median(ev)),
+                     "tet_agreement": float((g["tet"] == ost.tet).mean()),
+                     "particles_on_another_tet": int((g["tet"] != ost.tet).sum()),
+                     "crossing_count_agreement": float((g["n_cross"] == ost.n_cross).mean()),
+                     "G_cum_err_rel_max": float(gerr.max()), "G_cum_err_rel_p99": float(np.quantile(gerr, 0.99)),
+                     "conservation_residual_rel": float(np.abs(div - (rho1 - rho0)).max() / np.abs(rho1).max())}
+        env.close()
+    return res
 
 
 class ClockSampler:
@@ -471,6 +615,12 @@ def run_ours(args):
         del st_d, ds
 
     adj = None if (args.no_adjoint or args.workload != "cube48") else adjoint_window(rank)
+    if args.workload == "cube48" and not args.no_errors:
+        out["errors"] = config2_errors(wl, 100_000, 100)
+    if args.workload == "cube48" and not args.no_large and world == 1:
+        out["large"] = {k: large_leg(k, args.large_steps, 2, args.sort_every) for k in ("jittered64", "large96")}
+    from paper_2208_12795_gb300 import capi as _capi
+    out["fp64_rate"] = _capi.fempic_measure_fp64_rate(torch.cuda.current_stream().cuda_stream)
     if rank == 0:
         cpu = None if (args.no_cpu or world > 1) else cpu_baseline(wl, args.cpu_particles, args.cpu_steps)
         if cpu is not None and args.workload == "cube48" and not args.no_cpu_parallel:
@@ -493,6 +643,7 @@ def adjoint_window(rank):
     res = {}
     for form, prec in (("mixed", 1), ("fp64", 0)):
         env = FempicEnv.from_mesh(wl.mesh, precision=prec)
+        counts = (env.n_nodes, env.n_edges, env.n_faces, env.n_tets)
         st0 = ParticleState.from_host(wl.particles, prec, track_crossings=False)
         env.locate(st0)
         sc = st0.empty_like()
@@ -524,7 +675,7 @@ def adjoint_window(rank):
         env.close()
     return {"workload": "cube48_4M_adjoint: 48^3x6 cube, 4M electrons at 5 eV, TE101 10 kV/m, K=50, "
                         "checkpoint every 10; loss = kinetic energy after K steps",
-            "unit": "particle-steps/s", **res}
+            "unit": "particle-steps/s", "particles": wl.particles.n, "counts": counts, **res}
 
 
 def cpu_baseline(wl, n_sample, steps):
@@ -634,7 +785,7 @@ def report(args, world, n_p, out, cpu, adj=None):
             "parallelism": f"particle replicas x{world}, dG summed over ranks" if world > 1 else "1 GPU",
         },
         "roofline": {
-            "kernel": "push step group: k_push_mixed_tma (+ k_push_mixed ragged tail) + k_cross_mixed",
+            "kernel": "push step group: k_push_mixed_tma (+ k_push_mixed ragged tail) + k_cross_df",
             "bound": "hbm",
             "achieved": achieved,
             "peak": peak,
@@ -645,6 +796,9 @@ def report(args, world, n_p, out, cpu, adj=None):
             "algorithmic_bytes_per_launch": b_alg,
             "avg_launch_ms": t_push * 1e3,
             "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+            "frac_step": b_alg / (m["ms"] / K / 1e3) / 1e9 / peak,
+            "frac_step_note": "whole step (field, push group, finalize, sort amortised) on the same "
+                              "algorithmic bytes",
         },
         "e2e": {"value": total / m["e2e_s"], "unit": "particle-steps/s",
                 "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"]},
@@ -665,6 +819,7 @@ def report(args, world, n_p, out, cpu, adj=None):
         bf = bytes_alg_per_step(n_p, f["counts"], "fp64")
         rec["fp64_form"] = {"value": total / (f["ms"] / 1e3), "ms_per_step": f["ms"] / K,
                             "push_avg_launch_ms": tf * 1e3, "hbm_frac": bf / tf / 1e9 / peak,
+                            "roofline_fp64": fp64_roofline(n_p, tf, out.get("fp64_rate")),
                             "clocks": f["clocks"]}
     if "mixed_q24" in out:
         q = out["mixed_q24"]
@@ -681,7 +836,29 @@ def report(args, world, n_p, out, cpu, adj=None):
     if "downshift" in out:
         rec["downshift"] = out["downshift"]
     if adj is not None:
+        # HBM fractions of the gradient window: forward steps on the forward
+        # algorithmic bytes, reverse steps on 232 B per particle-step (forward
+        # recompute, stash and reload of the segment's states, adjoint state
+        # read and written) plus the DoF-gradient terms
+        nn, ne, nf, nt = adj.get("counts", (0, 0, 0, 0))
+        n_adj = adj.get("particles", 0)
+        for form in ("mixed", "fp64"):
+            r = adj.get(form)
+            if not r or not n_adj:
+                continue
+            fb = bytes_alg_per_step(n_adj, (nn, ne, nf, nt), form) / n_adj
+            rb = (232 if form == "mixed" else 2 * 2 * 52 + 2 * 48) + (8 * (ne + nf)) / n_adj
+            r["bytes_per_particle_step_forward"] = fb
+            r["bytes_per_particle_step_reverse"] = rb
+            r["hbm_frac_forward"] = r["forward_particle_steps_per_s"] * fb / 1e9 / peak
+            r["hbm_frac_reverse"] = r["reverse_particle_steps_per_s"] * rb / 1e9 / peak
         rec["adjoint"] = adj
+    if "errors" in out:
+        rec["mixed_error_vs_oracle"] = out["errors"]
+    if "large" in out:
+        rec["large_forward"] = out["large"]
+    if out.get("fp64_rate"):
+        rec["fp64_rate_lane_ops_per_s"] = out["fp64_rate"]
     if cpu is not None:
         rec["cpu_baseline"] = cpu
     print(json.dumps(rec), flush=True)

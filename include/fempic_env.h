@@ -358,6 +358,15 @@ int fempic_profile_enable(fempic_env* env, int32_t enable);
  * Synchronizes on the recorded events.  Errors: EINVAL, ECUDA. */
 int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* calls_out, int64_t* kernels_out);
 
+/* Measurement support (no counterpart in the paper): the FP64 fused
+ * multiply-add rate of the current device in lane operations per second,
+ * from one timed launch of independent FMA chains on every SM (after one
+ * untimed launch), written to *lane_ops_per_s (host).  It is the ceiling of
+ * the FP64 form, whose step is FP64-pipe bound on GB300.  Allocates 8 bytes
+ * of device memory for the duration of the call; synchronizes `stream`.
+ * Errors: EINVAL, ECUDA. */
+int fempic_measure_fp64_rate(double* lane_ops_per_s, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* fempic_last_error(void);
 

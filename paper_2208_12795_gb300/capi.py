@@ -31,7 +31,8 @@ EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_pus
            "fempic_lagrange3",
            "fempic_deposit", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
            "fempic_error_count", "fempic_debug_stall", "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
-           "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read", "fempic_last_error", "fempic_env_destroy")
+           "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read",
+           "fempic_measure_fp64_rate", "fempic_last_error", "fempic_env_destroy")
 # Every function declared in include/fempic_downshift.h.
 DS_EXPORTS = ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift",
               "fempic_downshift_last_error", "fempic_downshift_destroy")
@@ -124,6 +125,7 @@ def load(path: str = LIB_PATH):
                                                  C.c_void_p]
         lib.fempic_profile_enable.argtypes = [C.c_void_p, C.c_int32]
         lib.fempic_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_measure_fp64_rate.argtypes = [C.c_void_p, C.c_void_p]
         lib.fempic_downshift_create.argtypes = [P(fempic_mesh_desc), P(C.c_void_p)]
         lib.fempic_downshift_weights.argtypes = [C.c_double, C.c_double, C.c_double, C.c_void_p]
         lib.fempic_push_step_downshift.argtypes = [C.c_void_p, C.c_void_p, P(fempic_particles),
@@ -258,6 +260,12 @@ def fempic_profile_enable(env, enable: bool):
 
 def fempic_profile_read(env, ms_out, calls_out, kernels_out):
     check(load().fempic_profile_read(env, ms_out, calls_out, kernels_out), "fempic_profile_read")
+
+
+def fempic_measure_fp64_rate(stream=0) -> float:
+    r = C.c_double(0.0)
+    check(load().fempic_measure_fp64_rate(C.byref(r), stream), "fempic_measure_fp64_rate")
+    return r.value
 
 
 def fempic_last_error() -> str:

@@ -3373,6 +3373,56 @@ extern "C" int fempic_debug_stall(fempic_env* env, int32_t cta, int64_t limit_ns
   return FEMPIC_OK;
 }
 
+// ------------------------------------------------ measurement support
+// FP64 FMA issue-rate probe: every thread runs `iters` rounds of 8
+// independent FMA chains (no dependence between the chains, so the rate is
+// the FP64 pipe's, not its latency); the result is stored only under a
+// condition that never holds, which keeps the work from being removed.
+__global__ void __launch_bounds__(kThreads) k_fp64_probe(int iters, double* out) {
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) a[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) a[j] = fma(a[j], 0.9999999, 1e-7);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; j++) sum += a[j];
+  if (sum == -1.0) out[0] = sum;
+}
+
+extern "C" int fempic_measure_fp64_rate(double* lane_ops_per_s, void* stream) {
+  if (!lane_ops_per_s) return fail(FEMPIC_EINVAL, "measure_fp64_rate: NULL output");
+  int dev = 0, sms = 1;
+  FEMPIC_CUDA(cudaGetDevice(&dev));
+  FEMPIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  double* sink = nullptr;
+  FEMPIC_CUDA(cudaMalloc(&sink, sizeof(double)));
+  cudaEvent_t a = nullptr, b = nullptr;
+  int rc = FEMPIC_OK;
+  const unsigned grid = (unsigned)sms * 8u;
+  const int iters = 2048;
+  float ms = 0.f;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    rc = fail(FEMPIC_ECUDA, "measure_fp64_rate: event creation");
+  } else {
+    k_fp64_probe<<<grid, kThreads, 0, st>>>(iters, sink);   // warm-up
+    cudaEventRecord(a, st);
+    k_fp64_probe<<<grid, kThreads, 0, st>>>(iters, sink);
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess || !(ms > 0.f))
+      rc = fail(FEMPIC_ECUDA, "measure_fp64_rate: timing");
+    else
+      *lane_ops_per_s = (double)grid * kThreads * iters * 8.0 / (ms * 1e-3);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(sink);
+  return rc;
+}
+
 extern "C" int fempic_profile_enable(fempic_env* env, int32_t enable) {
   if (!env) return fail(FEMPIC_EINVAL, "profile_enable: NULL env");
   if (enable) {

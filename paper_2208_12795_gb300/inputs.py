@@ -434,3 +434,76 @@ def workload_large96(n_particles: int = 400_000_000) -> Workload:
     ion = uniform_maxwellian(n_particles - half, 2.0, rng, q=E_CHARGE, m=1836.0 * M_ELECTRON)
     return Workload("cube96_400M_two_species", mesh, concat_species([el, ion]), e_t, b_t,
                     te101_omega0(), 0.5e-9, 20, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Device-side draws of the two largest loads (benchmark legs): the same
+# distributions as electron_beam / cosine_plasma / uniform_maxwellian, drawn
+# with a seeded torch generator on the device so that 50M-400M particles
+# take seconds instead of minutes of host time.  The random numbers differ
+# from the host generators'; the parity tests use the host generators.
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def device_beam_plasma(n_particles: int, seed: int, device="cuda"):
+    """10% 10 keV electron beam along z (Gaussian transverse profile of radius
+    0.1 about (0.5, 0.5), resampled into the cube; 0.5% energy spread) + 90%
+    plasma electrons at 5 eV with density 1 + 0.5 cos(2 pi x).  Returns
+    (x, y, z, vx, vy, vz) float64 device tensors and the species table."""
+    torch = _torch()
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = dict(dtype=torch.float64, device=device)
+    nb = n_particles // 10
+    npl = n_particles - nb
+    # beam: transverse Gaussian, out-of-cube draws redrawn
+    xy = torch.empty((nb, 2), **f64)
+    todo = torch.arange(nb, device=device)
+    while todo.numel():
+        cand = 0.5 + 0.1 * torch.randn((todo.numel(), 2), generator=g, **f64)
+        ok = ((cand > 0.0) & (cand < 1.0)).all(1)
+        xy[todo[ok]] = cand[ok]
+        todo = todo[~ok]
+    zb = torch.rand(nb, generator=g, **f64)
+    en = 1e4 * (1.0 + 0.005 * torch.randn(nb, generator=g, **f64))
+    vzb = torch.sqrt(2.0 * en.clamp(min=0.0) * E_CHARGE / M_ELECTRON)
+    # plasma: x by rejection against 1 + 0.5 cos(2 pi x)
+    xp = torch.empty(npl, **f64)
+    todo = torch.arange(npl, device=device)
+    while todo.numel():
+        cand = torch.rand(todo.numel(), generator=g, **f64)
+        acc = torch.rand(todo.numel(), generator=g, **f64) * 1.5 < 1.0 + 0.5 * torch.cos(2 * math.pi * cand)
+        xp[todo[acc]] = cand[acc]
+        todo = todo[~acc]
+    yzp = torch.rand((npl, 2), generator=g, **f64)
+    vp = torch.randn((npl, 3), generator=g, **f64) * thermal_sigma(5.0, M_ELECTRON)
+    zeros = torch.zeros(nb, **f64)
+    cols = (torch.cat([xy[:, 0], xp]), torch.cat([xy[:, 1], yzp[:, 0]]), torch.cat([zb, yzp[:, 1]]),
+            torch.cat([zeros, vp[:, 0]]), torch.cat([zeros, vp[:, 1]]), torch.cat([vzb, vp[:, 2]]))
+    table = (np.array([0, nb, n_particles], np.int64), np.array([-E_CHARGE, -E_CHARGE]),
+             np.array([M_ELECTRON, M_ELECTRON]), np.array([1e3, 1e3]))
+    return cols, table
+
+
+def device_two_species(n_particles: int, seed: int, device="cuda", vdtype=None):
+    """Uniform electrons then heavy ions (m = 1836 m_e, q = +e), both at 2 eV,
+    half each (the species table of large96_species).  Velocities in vdtype
+    (float64 by default) to keep the device footprint of 400M particles low."""
+    torch = _torch()
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    vdtype = vdtype or torch.float64
+    sb, q, m, w, temp = large96_species(n_particles)
+    pos = [torch.rand(n_particles, generator=g, dtype=torch.float64, device=device) for _ in range(3)]
+    vel = [torch.empty(n_particles, dtype=vdtype, device=device) for _ in range(3)]
+    chunk = 50_000_000
+    for s in range(2):
+        sig = thermal_sigma(temp, m[s])
+        for c0 in range(int(sb[s]), int(sb[s + 1]), chunk):
+            c1 = min(int(sb[s + 1]), c0 + chunk)
+            for k in range(3):
+                vel[k][c0:c1] = (torch.randn(c1 - c0, generator=g, dtype=torch.float64, device=device) * sig).to(vdtype)
+    return tuple(pos) + tuple(vel), (sb, q, m, w)

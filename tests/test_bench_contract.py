@@ -89,3 +89,31 @@ def test_algorithmic_bytes_per_step_match_the_stated_formula():
     assert b == 10_000_000 * 2 * 40 + 72 * nt + 24 * nn + (8 + 8) * ne + 8 * nf
     assert b / 10_000_000 == pytest.approx(87.4, abs=0.05)
     assert bench.bytes_alg_per_step(10_000_000, counts, "fp64") / 10_000_000 == pytest.approx(113.1, abs=0.05)
+
+
+def test_step_fraction_variant_and_reports_are_carried(monkeypatch):
+    """roofline.frac_step (whole step on the algorithmic bytes), the 24-bit
+    variant's object, the per-quantity error report, the large-load legs,
+    the adjoint window's HBM fractions and the FP64 rate are in the line."""
+    monkeypatch.setattr(bench, "issue_roofline", lambda *a: None)
+    args = argparse.Namespace(steps=100, warmup=10, workload="cube48", sort_every=4)
+    out = _fake_out(100)
+    out["mixed_q24"] = dict(out["mixed"], ms=0.72 * 100)
+    out["errors"] = {"mixed": {"tet_agreement": 1.0}}
+    out["large"] = {"jittered64": {"value": 7e9}, "large96": {"value": 1.4e10}}
+    out["fp64_rate"] = 5.3e11
+    adj = {"particles": 4_000_000, "counts": (117649, 795024, 1340928, 663552),
+           "mixed": {"forward_particle_steps_per_s": 1.5e10, "reverse_particle_steps_per_s": 6e9}}
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.report(args, 1, 10_000_000, out, None, adj)
+    d = json.loads(buf.getvalue().strip())
+    b_alg = bench.bytes_alg_per_step(10_000_000, out["mixed"]["counts"], "mixed")
+    assert d["roofline"]["frac_step"] == pytest.approx(b_alg / 0.67e-3 / 1e9 / d["roofline"]["peak"])
+    assert d["mixed_q24"]["ms_per_step"] == pytest.approx(0.72)
+    assert d["mixed_error_vs_oracle"] == out["errors"] and d["large_forward"] == out["large"]
+    assert d["fp64_rate_lane_ops_per_s"] == 5.3e11
+    a = d["adjoint"]["mixed"]
+    assert a["hbm_frac_reverse"] == pytest.approx(6e9 * a["bytes_per_particle_step_reverse"] / 1e9 /
+                                                  d["roofline"]["peak"])
+    assert a["bytes_per_particle_step_reverse"] > 232
