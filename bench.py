@@ -9,13 +9,15 @@ FP64 form is measured side by side.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun each rank runs its own 10M-particle replica (weak scaling)
-and the per-step edge deposit dG is summed over ranks.  Rank 0 prints one
-JSON line.
+Under torchrun each rank advances its own 10M particles: a z-slab, i.e. a
+contiguous tet range, of a uniform load of N x 10M (weak scaling).  Each
+step's edge deposit dG is finalized per rank, all-reduced, and added to every
+rank's G_cum.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -365,7 +367,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
 
-    from paper_2208_12795_gb300 import build, inputs as I
+    from paper_2208_12795_gb300 import build, inputs as I, shard
     from paper_2208_12795_gb300.env import Downshift, FempicEnv, ParticleState
 
     if rank == 0 or world == 1:
@@ -376,6 +378,8 @@ def run_ours(args):
     big_host = None
     if args.workload == "cube48":
         wl = I.te101_cavity(48, n_p, 5.0, 1e4, 100, 2 + 100 * rank, name="cube48_10M_te101")
+        if world > 1:   # this rank's z-slab (a contiguous tet range) of the world x n_p global load
+            wl = dataclasses.replace(wl, particles=shard.slab_load(wl.particles, rank, world))
     elif args.workload == "jittered64":
         n_p = args.particles if args.particles != 10_000_000 else 50_000_000
         wl = I.workload_jittered64(n_p)
@@ -414,15 +418,16 @@ def run_ours(args):
         env.sort(st, scratch)                 # initial tet-sorted layout (untimed)
         e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
         b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
-        dG = torch.zeros(env.n_edges, dtype=torch.float64, device="cuda")
+        sharded = shard.ShardedDeposit(env) if world > 1 else None
         counts = (env.n_nodes, env.n_edges, env.n_faces, env.n_tets)
 
         def step(n):
             t = n * wl.dt
             env.push_step(st, e, b, wl.amp(t), wl.omega0, t, wl.dt)
-            env.deposit(wl.omega0, t + wl.dt, dG_out=dG if world > 1 else None)
-            if world > 1:
-                dist.all_reduce(dG)
+            if sharded is not None:   # local dG, all-reduced, added to every rank's G_cum
+                sharded(wl.omega0, t + wl.dt)
+            else:
+                env.deposit(wl.omega0, t + wl.dt)
             if args.sort_every > 0 and (n + 1) % args.sort_every == 0:
                 env.sort(st, scratch)
 
@@ -491,9 +496,12 @@ def run_ours(args):
         e_dev.copy_(e_host, non_blocking=True)
         b_dev.copy_(b_host, non_blocking=True)
         env.push_step(st, e_dev, b_dev, wl.amp(t), wl.omega0, t, wl.dt)
-        env.deposit(wl.omega0, t + wl.dt, dG_out=dG_dev)
         if world > 1:
+            env.deposit_local(dG_dev)
             dist.all_reduce(dG_dev)
+            env.accumulate(wl.omega0, t + wl.dt, dG_dev)
+        else:
+            env.deposit(wl.omega0, t + wl.dt, dG_out=dG_dev)
         dG_host.copy_(dG_dev, non_blocking=True)
         if args.sort_every > 0 and (n + 1) % args.sort_every == 0:
             env.sort(st, mixed["scratch"])
@@ -523,9 +531,12 @@ def run_ours(args):
         def step3(n):
             t = n * wl.dt
             env.push_step3(st, e_lv, b_lv, capi.fempic_lagrange3(tau, t), wl.amp(t), wl.omega0, t, wl.dt)
-            env.deposit(wl.omega0, t + wl.dt, dG_out=dG_dev if world > 1 else None)
             if world > 1:
+                env.deposit_local(dG_dev)
                 dist.all_reduce(dG_dev)
+                env.accumulate(wl.omega0, t + wl.dt, dG_dev)
+            else:
+                env.deposit(wl.omega0, t + wl.dt)
             if args.sort_every > 0 and (n + 1) % args.sort_every == 0:
                 env.sort(st, mixed["scratch"])
 
@@ -573,9 +584,12 @@ def run_ours(args):
         def step_ds(n):
             t = n * wl.dt
             ds.step(st_d, e_d, b_d, wl.amp(t), wl.omega0, t, wl.dt)
-            env_d.deposit(wl.omega0, t + wl.dt, dG_out=dG_d if world > 1 else None)
             if world > 1:
+                env_d.deposit_local(dG_d)
                 dist.all_reduce(dG_d)
+                env_d.accumulate(wl.omega0, t + wl.dt, dG_d)
+            else:
+                env_d.deposit(wl.omega0, t + wl.dt)
 
         for n in range(max(3, args.warmup)):
             step_ds(n)
@@ -782,7 +796,7 @@ def report(args, world, n_p, out, cpu, adj=None):
             "n_tets": m["counts"][3],
             "sort_every": args.sort_every,
             "l2": f"inputs larger than L2 (particle SoA {n_p * 41 / 1e6:.0f} MB per GPU per step)",
-            "parallelism": f"particle replicas x{world}, dG summed over ranks" if world > 1 else "1 GPU",
+            "parallelism": f"particles sharded by tet range over {world} GPUs, dG all-reduced" if world > 1 else "1 GPU",
         },
         "roofline": {
             "kernel": "push step group: k_push_mixed_tma (+ k_push_mixed ragged tail) + k_cross_df",

@@ -206,6 +206,24 @@ int fempic_lagrange3(const double* tau, double t, double* w_out);
 int fempic_deposit(fempic_env* env, double omega0, double t_next, double* dG_out, double* G_cum_out,
                    void* G_env_out, void* stream);
 
+/* The two halves of fempic_deposit for a run whose particles are sharded
+ * over several processes (each GPU holds the whole mesh and DoFs and a range
+ * of the particles; the only coupling is the sum of the edge deposit, Sec.
+ * III-D eq. G_integral, over the shards):
+ *   fempic_deposit_local  finalizes this process's step deposit into dG_out
+ *                         (device f64 [Ne]) and clears the accumulator,
+ *                         leaving G_cum unchanged;
+ *   fempic_accumulate     adds a step deposit dG (device f64 [Ne], the
+ *                         all-reduced sum of every shard's dG_out) to G_cum
+ *                         and writes, when non-NULL, G_cum_out and
+ *                         G_env_out = e^{-j omega0 t_next} G_cum as
+ *                         fempic_deposit does.
+ * fempic_deposit on one process equals fempic_deposit_local followed by
+ * fempic_accumulate of that dG_out.  Stream-ordered.  Errors: EINVAL, ECUDA. */
+int fempic_deposit_local(fempic_env* env, double* dG_out, void* stream);
+int fempic_accumulate(fempic_env* env, double omega0, double t_next, const double* dG, double* G_cum_out,
+                      void* G_env_out, void* stream);
+
 /* Switch the deposit (f) of later push steps on (enable != 0, the default)
  * or off.  Off, a step still gathers, pushes and tracks every particle
  * exactly as with the deposit on, but adds nothing to dG: for callers that

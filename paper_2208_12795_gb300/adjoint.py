@@ -137,9 +137,12 @@ def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule
     return st, ckpts
 
 
-def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState):
+def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState, group=None):
     """Propagate `adj` (adjoint of the final state) back to the initial state;
-    returns the complex128 gradients of the edge and face DoFs."""
+    returns the complex128 gradients of the edge and face DoFs.  With a
+    process group (particles sharded over its ranks, the loss the sum of the
+    ranks' losses), the DoF gradients are summed over the ranks; the
+    particles' gradients stay with their rank."""
     eg = torch.zeros(env.n_edges, dtype=torch.complex128, device=e.device)
     bg = torch.zeros(env.n_faces, dtype=torch.complex128, device=b.device)
     stream = _stream(None)
@@ -165,17 +168,25 @@ def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState)
                 spare = AdjointState(adj.n, adj.vx.dtype, device=adj.rx.device)
             capi.fempic_adjoint_unpermute(env.h, adj.cstruct(), spare.cstruct(), _ptr(ckpts[s].perm), stream)
             adj.swap(spare)
+    if group is not None:
+        from .shard import allreduce_
+        allreduce_(torch.view_as_real(eg), group)
+        allreduce_(torch.view_as_real(bg), group)
     return eg, bg
 
 
-def kinetic_energy_and_grad(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule):
+def kinetic_energy_and_grad(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule, group=None):
     """(L, dL/de, dL/db, adjoint of the initial state) for L = kinetic energy
-    after sch.steps steps from st0 (st0 is not modified)."""
+    after sch.steps steps from st0 (st0 is not modified).  With a process
+    group, L and the DoF gradients are those of the whole sharded load."""
     final, ckpts = forward_checkpointed(env, st0, e, b, sch)
     vdt = torch.float64 if env.precision == FEMPIC_FP64 else torch.float32
     adj = AdjointState(st0.n, vdt, device=st0.x.device)
     L = kinetic_energy(env, final, seed=adj)
-    eg, bg = reverse_sweep(env, ckpts, e, b, sch, adj)
+    if group is not None:
+        from .shard import allreduce_
+        allreduce_(L.view(1), group)
+    eg, bg = reverse_sweep(env, ckpts, e, b, sch, adj, group=group)
     return L, eg, bg, adj
 
 

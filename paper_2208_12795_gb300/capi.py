@@ -29,7 +29,7 @@ FEMPIC_WALL_ABSORB = 1
 # Every function declared in include/fempic_env.h.
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step", "fempic_push_step3",
            "fempic_lagrange3",
-           "fempic_deposit", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
+           "fempic_deposit", "fempic_deposit_local", "fempic_accumulate", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
            "fempic_error_count", "fempic_debug_stall", "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
            "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read",
            "fempic_measure_fp64_rate", "fempic_last_error", "fempic_env_destroy")
@@ -107,6 +107,9 @@ def load(path: str = LIB_PATH):
         lib.fempic_deposit.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]
         lib.fempic_reset_deposit.argtypes = [C.c_void_p, C.c_void_p]
+        lib.fempic_deposit_local.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.fempic_accumulate.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]
         lib.fempic_set_deposit.argtypes = [C.c_void_p, C.c_int32]
         lib.fempic_nodal_charge.argtypes = [C.c_void_p, P(fempic_particles), C.c_void_p, C.c_void_p]
         lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -196,6 +199,15 @@ def fempic_set_deposit(env, enable: bool):
 def fempic_deposit(env, omega0, t_next, dG_out=0, G_cum_out=0, G_env_out=0, stream=0):
     check(load().fempic_deposit(env, float(omega0), float(t_next), dG_out, G_cum_out, G_env_out, stream),
           "fempic_deposit")
+
+
+def fempic_deposit_local(env, dG_out, stream=0):
+    check(load().fempic_deposit_local(env, dG_out, stream), "fempic_deposit_local")
+
+
+def fempic_accumulate(env, omega0, t_next, dG, G_cum_out=0, G_env_out=0, stream=0):
+    check(load().fempic_accumulate(env, float(omega0), float(t_next), dG, G_cum_out, G_env_out, stream),
+          "fempic_accumulate")
 
 
 def fempic_reset_deposit(env, stream=0):

@@ -1951,6 +1951,7 @@ struct FinalizeArgs {
   double* Gcum_out;
   double2* Genv_out;
   double c, s;                   // cos, sin of omega0 t_next
+  int32_t local;                 // 1: write dG_out only, leave G_cum (fempic_deposit_local)
 };
 
 // Deposit finalize, one thread per edge.  The mixed forms pull the edge's
@@ -1989,11 +1990,28 @@ __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
     d = A.dG[e];
     A.dG[e] = 0.0;
   }
+  if (A.local) {
+    A.dG_out[e] = d;
+    return;
+  }
   const double g = A.Gcum[e] + d;
   A.Gcum[e] = g;
   if (A.dG_out) A.dG_out[e] = d;
   if (A.Gcum_out) A.Gcum_out[e] = g;
   if (A.Genv_out) A.Genv_out[e] = make_double2(A.c * g, -(A.s * g));
+}
+
+// G_cum += dG for a step deposit reduced outside the library (a sharded run
+// all-reduces each rank's dG), then the requested outputs.
+__global__ void __launch_bounds__(kThreads) k_accumulate(int64_t ne, const double* __restrict__ dG,
+                                                         double* __restrict__ Gcum, double* Gcum_out,
+                                                         double2* Genv_out, double c, double s) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const double g = Gcum[e] + dG[e];
+  Gcum[e] = g;
+  if (Gcum_out) Gcum_out[e] = g;
+  if (Genv_out) Genv_out[e] = make_double2(c * g, -(s * g));
 }
 
 // ------------------------------------------------------------ nodal charge
@@ -3226,10 +3244,8 @@ extern "C" int fempic_lagrange3(const double* tau, double t, double* w_out) {
   return FEMPIC_OK;
 }
 
-extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, double* dG_out, double* G_cum_out,
-                              void* G_env_out, void* stream) {
-  if (!env) return fail(FEMPIC_EINVAL, "deposit: NULL env");
-  if (!std::isfinite(omega0) || !std::isfinite(t_next)) return fail(FEMPIC_EINVAL, "deposit: non-finite scalar");
+static int deposit_impl(fempic_env* env, double omega0, double t_next, double* dG_out, double* G_cum_out,
+                        void* G_env_out, bool local, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int prec = env->opt.precision;
   FinalizeArgs A{};
@@ -3247,6 +3263,7 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
   A.Genv_out = static_cast<double2*>(G_env_out);
   A.estart = env->estart;
   A.eslot = env->eslot;
+  A.local = local ? 1 : 0;
   const double phi = omega0 * t_next;
   A.c = std::cos(phi);
   A.s = std::sin(phi);
@@ -3279,6 +3296,33 @@ extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, dou
     lt.kernels++;
     if (A.mode == 2 && A.ns > 0)
       FEMPIC_CUDA(cudaMemsetAsync(env->dGq, 0, (size_t)A.ns * env->h.nt * 8 * sizeof(unsigned long long), st));
+  }
+  FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_deposit(fempic_env* env, double omega0, double t_next, double* dG_out, double* G_cum_out,
+                              void* G_env_out, void* stream) {
+  if (!env) return fail(FEMPIC_EINVAL, "deposit: NULL env");
+  if (!std::isfinite(omega0) || !std::isfinite(t_next)) return fail(FEMPIC_EINVAL, "deposit: non-finite scalar");
+  return deposit_impl(env, omega0, t_next, dG_out, G_cum_out, G_env_out, false, stream);
+}
+
+extern "C" int fempic_deposit_local(fempic_env* env, double* dG_out, void* stream) {
+  if (!env || !dG_out) return fail(FEMPIC_EINVAL, "deposit_local: NULL env or dG_out");
+  return deposit_impl(env, 0.0, 0.0, dG_out, nullptr, nullptr, true, stream);
+}
+
+extern "C" int fempic_accumulate(fempic_env* env, double omega0, double t_next, const double* dG, double* G_cum_out,
+                                 void* G_env_out, void* stream) {
+  if (!env || !dG) return fail(FEMPIC_EINVAL, "accumulate: NULL env or dG");
+  if (!std::isfinite(omega0) || !std::isfinite(t_next)) return fail(FEMPIC_EINVAL, "accumulate: non-finite scalar");
+  const double phi = omega0 * t_next;
+  {
+    LaunchTimer lt(env, (cudaStream_t)stream, FEMPIC_K_FINALIZE);
+    k_accumulate<<<blocks_for(env->h.ne), kThreads, 0, (cudaStream_t)stream>>>(
+        env->h.ne, dG, env->Gcum, G_cum_out, static_cast<double2*>(G_env_out), std::cos(phi), std::sin(phi));
+    lt.kernels = 1;
   }
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;

@@ -192,6 +192,14 @@ class FempicEnv:
         capi.fempic_deposit(self.h, omega0, t_next, _ptr(dG_out), _ptr(G_cum_out), _ptr(G_env_out),
                             _stream(stream))
 
+    def deposit_local(self, dG_out, stream=None):
+        """This process's step deposit into dG_out (G_cum unchanged)."""
+        capi.fempic_deposit_local(self.h, _ptr(dG_out), _stream(stream))
+
+    def accumulate(self, omega0: float, t_next: float, dG, G_cum_out=None, G_env_out=None, stream=None):
+        """G_cum += dG (a step deposit summed over every shard), then the outputs."""
+        capi.fempic_accumulate(self.h, omega0, t_next, _ptr(dG), _ptr(G_cum_out), _ptr(G_env_out), _stream(stream))
+
     @property
     def deposit_on(self) -> bool:
         return getattr(self, "_deposit_on", True)
