@@ -207,12 +207,12 @@ def push_step_downshift(mesh: OracleMesh, st: OracleState, hist: History, e_dof,
     st.vz[:] = u[:, 2]
     zero_e = np.zeros(mesh.n_edges, np.complex128)
     zero_b = np.zeros(mesh.n_faces, np.complex128)
+    mirror = np.zeros(n, np.uint8)
     push_step(mesh, st, zero_e, zero_b, 0.0, omega0, t, dt, dG, max_crossings=max_crossings,
-              wall_mode=wall_mode)
-    u_after = np.stack([st.vx, st.vy, st.vz], 1)
-    # D6: an axis was mirrored (an odd number of times) iff the tracked
-    # velocity came back negated; a zero component cannot reach a wall
-    flip = (u != 0.0) & (u_after == -u)
+              wall_mode=wall_mode, mirror=mirror)
+    # D6: the axes the walk mirrored an odd number of times, as recorded by
+    # the walk itself where it reflects
+    flip = ((mirror[:, None] >> np.arange(3)[None, :]) & 1).astype(bool)
     sign = np.where(flip, -1.0, 1.0)
     # history shift (active particles only), then the mirror of every velocity
     new_hv = hist.v.copy()

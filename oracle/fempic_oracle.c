@@ -475,7 +475,7 @@ static int finite3(const double *a) { return isfinite(a[0]) && isfinite(a[1]) &&
 
 static void step_one(const omesh *m, oparts *P, int64_t p, double kq, double qw, double cre, double cim,
                      const double *e_dof, const double *b_dof, double dt, int32_t max_cross,
-                     int32_t wall_mode, double *dG) {
+                     int32_t wall_mode, double *dG, uint8_t *mirror) {
   int32_t T = P->tet[p];
   if (T < 0) return;
   if (T >= m->nt) { P->tet[p] = -1; P->status[p] = OR_LOST; return; }
@@ -507,6 +507,7 @@ static void step_one(const omesh *m, oparts *P, int64_t p, double kq, double qw,
   or_bary(m, T, a, la);
   int entry = -1;
   int32_t ncross = 0;
+  int mir = 0;   /* bit ax: mirrored in axis ax an odd number of times */
   for (;;) {
     or_bary(m, T, b, lb);
     int kx = -1;
@@ -548,6 +549,7 @@ static void step_one(const omesh *m, oparts *P, int64_t p, double kq, double qw,
       double L = side ? m->hi[ax] : m->lo[ax];
       b[ax] = 2.0 * L - b[ax];
       vn[ax] = -vn[ax];
+      mir ^= 1 << ax;
       for (int i = 0; i < 4; i++) la[i] = lp[i];
       entry = kx;
     } else {
@@ -560,16 +562,20 @@ static void step_one(const omesh *m, oparts *P, int64_t p, double kq, double qw,
   P->vx[p] = vn[0]; P->vy[p] = vn[1]; P->vz[p] = vn[2];
   P->tet[p] = T;
   if (P->n_cross) P->n_cross[p] += ncross;
+  if (mirror) mirror[p] = (uint8_t)mir;
 }
 
 /* One particle step for all particles, serially in index order.
  * Species s covers particles [species_begin[s], species_begin[s+1]).
- * dG (length ne) is accumulated into (not cleared). */
+ * dG (length ne) is accumulated into (not cleared).  mirror (length n, may be
+ * NULL) receives per particle the axes whose velocity component the walls
+ * mirrored an odd number of times during the step (bit ax), recorded where
+ * the walk reflects; particles not stepped keep their entry. */
 int or_push_step(const void *h, int64_t n, double *x, double *y, double *z, double *vx, double *vy,
                  double *vz, int32_t *tet, uint8_t *status, int32_t *n_cross, int32_t n_species,
                  const int64_t *species_begin, const double *q, const double *mass, const double *w,
                  const double *e_dof, const double *b_dof, double amp, double omega0, double t,
-                 double dt, int32_t max_cross, int32_t wall_mode, double *dG) {
+                 double dt, int32_t max_cross, int32_t wall_mode, double *dG, uint8_t *mirror) {
   const omesh *m = (const omesh *)h;
   oparts P = {x, y, z, vx, vy, vz, tet, status, n_cross};
   double phi = omega0 * t;
@@ -579,7 +585,7 @@ int or_push_step(const void *h, int64_t n, double *x, double *y, double *z, doub
     double qw = q[s] * w[s];
     int64_t p1 = species_begin[s + 1] < n ? species_begin[s + 1] : n;
     for (int64_t p = species_begin[s]; p < p1; p++)
-      step_one(m, &P, p, kq, qw, cre, cim, e_dof, b_dof, dt, max_cross, wall_mode, dG);
+      step_one(m, &P, p, kq, qw, cre, cim, e_dof, b_dof, dt, max_cross, wall_mode, dG, mirror);
   }
   return 0;
 }

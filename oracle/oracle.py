@@ -58,7 +58,7 @@ def _load():
         lib.or_push_step.argtypes = ([C.c_void_p, C.c_int64] + [_d] * 6 +
                                      [_i32, _u8, C.c_void_p, C.c_int32, _i64, _d, _d, _d, _d, _d,
                                       C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
-                                      C.c_int32, _d])
+                                      C.c_int32, _d, C.c_void_p])
         lib.or_push_step_jvp.restype = C.c_int
         lib.or_push_step_jvp.argtypes = ([C.c_void_p, C.c_int64] + [_d] * 6 +
                                          [_i32, _u8, C.c_void_p, C.c_int32, _i64, _d, _d, _d, _d, _d,
@@ -196,15 +196,21 @@ class OracleState:
 
 
 def push_step(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, t, dt, dG,
-              max_crossings=4096, wall_mode=0):
-    """One oracle particle step; accumulates into dG (float64 [Ne])."""
+              max_crossings=4096, wall_mode=0, mirror=None):
+    """One oracle particle step; accumulates into dG (float64 [Ne]).  mirror
+    (uint8 [n] or None) receives each particle's mirrored axes (bit ax: the
+    walls mirrored that velocity component an odd number of times)."""
     e = _f64(np.ascontiguousarray(e_dof, np.complex128).view(np.float64))
     b = _f64(np.ascontiguousarray(b_dof, np.complex128).view(np.float64))
     assert dG.dtype == np.float64 and dG.flags.c_contiguous and dG.shape[0] == mesh.n_edges
+    mp = None
+    if mirror is not None:
+        assert mirror.dtype == np.uint8 and mirror.flags.c_contiguous and mirror.shape[0] == st.n
+        mp = mirror.ctypes.data_as(C.c_void_p)
     mesh.lib.or_push_step(mesh.h, st.n, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.tet, st.status,
                           st.n_cross.ctypes.data_as(C.c_void_p), len(st.q), st.species_begin, st.q,
                           st.m, st.w, e, b, float(amp), float(omega0), float(t), float(dt),
-                          int(max_crossings), int(wall_mode), dG)
+                          int(max_crossings), int(wall_mode), dG, mp)
 
 
 def push_step_jvp(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, t, dt, dG, tr, tv, de, db,
@@ -290,8 +296,27 @@ def envelope3(levels, weights):
     return out
 
 
+def envelope3_literal(levels, weights, tau, omega0, t):
+    """The fine-step field formula with the carrier of each level's own time
+    inside the interpolation (Sec. III-D as printed): the field at t is
+    Re{sum_k N_k(t) level_k e^{j omega0 tau_k}}.  Returned as the envelope
+    that the carrier at t turns into that field, sum_k N_k(t) level_k
+    e^{j omega0 (tau_k - t)}, so that push_step takes it unchanged."""
+    out = np.zeros_like(np.asarray(levels[0], dtype=np.complex128))
+    for lv, wk, tk in zip(levels, weights, tau):
+        out = out + (wk * np.exp(1j * omega0 * (tk - t))) * np.asarray(lv, dtype=np.complex128)
+    return out
+
+
 def push_step3(mesh: OracleMesh, st: OracleState, e_levels, b_levels, weights, amp, omega0, t, dt, dG,
-               max_crossings=4096, wall_mode=0):
-    """One oracle step with the envelope interpolated from three levels."""
-    push_step(mesh, st, envelope3(e_levels, weights), envelope3(b_levels, weights), amp, omega0, t, dt, dG,
-              max_crossings=max_crossings, wall_mode=wall_mode)
+               max_crossings=4096, wall_mode=0, tau=None, literal_phase=False):
+    """One oracle step with the envelope interpolated from three levels.
+    Default: the reading taken (carrier at the fine-step time t).  With
+    literal_phase, the printed formula's per-level carrier e^{j omega0 tau_k}
+    (tau: the three level times)."""
+    if literal_phase:
+        e_env = envelope3_literal(e_levels, weights, tau, omega0, t)
+        b_env = envelope3_literal(b_levels, weights, tau, omega0, t)
+    else:
+        e_env, b_env = envelope3(e_levels, weights), envelope3(b_levels, weights)
+    push_step(mesh, st, e_env, b_env, amp, omega0, t, dt, dG, max_crossings=max_crossings, wall_mode=wall_mode)

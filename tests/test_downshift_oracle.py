@@ -288,3 +288,43 @@ def test_mesh_step_conserves_charge_and_mirrors_the_history(cube4j):
         np.testing.assert_allclose([sq.x[0], sq.y[0], sq.z[0]], want, rtol=1e-13, atol=1e-15)
     assert sq.vx[0] == -v0[0] and np.all(hq.v[:, 0, 0] == -v0[0])
     assert AB4.sum() == pytest.approx(1.0, abs=1e-15)
+
+
+def test_walk_records_its_wall_mirrors():
+    """The oracle's walk records, where it reflects, which velocity
+    components it mirrored an odd number of times (the downshifted rule
+    mirrors its history with that record, D6): a corner hit mirrors two
+    axes, a step long enough to bounce off both x walls mirrors none, and
+    on a hot load the record equals what the velocity signs show."""
+    from oracle.oracle import OracleMesh, OracleState, push_step
+    from paper_2208_12795_gb300 import inputs as I
+    m = I.kuhn_cube_mesh(4)
+    om = OracleMesh(m.nodes, m.tets)
+    dt = 1e-9
+    x = np.array([0.9, 0.9, 0.5, 0.3])
+    y = np.array([0.9, 0.5, 0.5, 0.3])
+    z = np.array([0.5, 0.5, 0.5, 0.3])
+    vx = np.array([0.3, 1.5, 0.0, 0.2]) / dt      # corner; two x walls; at rest in x; no wall
+    vy = np.array([0.3, 0.0, 0.0, 0.1]) / dt
+    vz = np.zeros(4)
+    P = I.Particles(x, y, z, vx, vy, vz, np.array([0, 4], np.int64), np.array([-I.E_CHARGE]),
+                    np.array([I.M_ELECTRON]), np.array([1.0]))
+    tet, _ = om.locate(x, y, z)
+    st = OracleState(P, tet)
+    mirror = np.full(4, 255, np.uint8)
+    e0 = np.zeros(om.n_edges, np.complex128)
+    b0 = np.zeros(om.n_faces, np.complex128)
+    push_step(om, st, e0, b0, 0.0, 1.0, 0.0, dt, np.zeros(om.n_edges), mirror=mirror)
+    assert list(mirror) == [0b011, 0b000, 0b000, 0b000]
+    assert st.vx[0] < 0 and st.vy[0] < 0 and st.vx[1] == vx[1]             # two x mirrors cancel
+    assert abs(st.x[1] - 0.4) < 1e-12 and abs(st.x[0] - 0.8) < 1e-12 and abs(st.y[0] - 0.8) < 1e-12
+    wl = I.workload_hot_small(jitter=0.2)
+    om2 = OracleMesh(wl.mesh.nodes, wl.mesh.tets)
+    st = OracleState(wl.particles, om2.locate(wl.particles.x, wl.particles.y, wl.particles.z)[0])
+    v0 = np.stack([st.vx, st.vy, st.vz], 1).copy()
+    mirror = np.zeros(st.n, np.uint8)
+    push_step(om2, st, np.zeros(om2.n_edges, np.complex128), np.zeros(om2.n_faces, np.complex128), 0.0, 1.0,
+              0.0, wl.dt, np.zeros(om2.n_edges), mirror=mirror)
+    v1 = np.stack([st.vx, st.vy, st.vz], 1)
+    bits = ((mirror[:, None] >> np.arange(3)[None, :]) & 1).astype(bool)
+    assert bits.any() and np.array_equal(bits, (v0 != 0) & (v1 == -v0))

@@ -59,3 +59,55 @@ def test_library_weights_match_the_oracle_on_the_host():
         assert np.allclose(lw, ow, rtol=1e-15, atol=1e-16)
     with pytest.raises(capi.FempicError):
         capi.fempic_lagrange3((0.0, 1.0, 1.0), 0.5)
+
+
+# ------------------------------------------- printed per-level carrier phase
+def _fields(omega0, dtau, env, t):
+    """The field Re{e^{j omega0 t} sum_k N_k(t) env(tau_k)} of the reading
+    taken, the printed formula's Re{sum_k N_k(t) env(tau_k) e^{j omega0 tau_k}},
+    and the field Re{env(t) e^{j omega0 t}} the levels sample."""
+    from oracle.oracle import envelope3_literal
+    tau = (-dtau, 0.0, dtau)
+    lv = [np.array([env(tk)]) for tk in tau]
+    w = lagrange3_weights(tau, t)
+    carrier = np.exp(1j * omega0 * t)
+    taken = (carrier * envelope3(lv, w))[0].real
+    literal = (carrier * envelope3_literal(lv, w, tau, omega0, t))[0].real
+    return taken, literal, (env(t) * carrier).real
+
+
+def test_literal_phase_agrees_when_the_field_step_resolves_the_carrier():
+    """With a field step much shorter than a carrier period the per-level
+    carrier is itself interpolated to third order: the printed formula and
+    the reading taken differ by O((omega0 dtau)^3), falling 8x per halving,
+    and agree exactly at the level times."""
+    omega0 = 2 * np.pi * 1e9
+    env = lambda s: (1.0 + 0.3j) + (0.2 - 0.1j) * s / 1e-6     # a slow envelope (quadratic is exact)
+    diffs = []
+    for dtau in (2e-12, 1e-12, 5e-13):
+        ts = np.linspace(-dtau, dtau, 41)
+        d = max(abs(_fields(omega0, dtau, env, t)[0] - _fields(omega0, dtau, env, t)[1]) for t in ts)
+        diffs.append(d)
+        assert d <= 2 * (omega0 * dtau) ** 3
+        for tk in (-dtau, 0.0, dtau):
+            a, b, _ = _fields(omega0, dtau, env, tk)
+            assert abs(a - b) <= 1e-15
+    assert 6.0 < diffs[0] / diffs[1] < 10.0 and 6.0 < diffs[1] / diffs[2] < 10.0
+
+
+def test_literal_phase_aliases_when_a_field_step_spans_the_carrier():
+    """With a field step of half a carrier period (the regime the method is
+    for: many fine steps, and carrier periods, per field step) the samples
+    e^{j omega0 tau_k} alternate in sign and their quadratic interpolant is
+    not the carrier: the printed formula's field misses the sampled field by
+    O(1), while the reading taken reproduces it exactly (the envelope is
+    linear in t)."""
+    omega0 = 2 * np.pi * 1e9
+    dtau = np.pi / omega0
+    env = lambda s: (1.0 + 0.3j) + (0.2 - 0.1j) * s / 1e-6
+    worst_taken, worst_literal = 0.0, 0.0
+    for t in np.linspace(-dtau, dtau, 81):
+        taken, literal, true = _fields(omega0, dtau, env, t)
+        worst_taken = max(worst_taken, abs(taken - true))
+        worst_literal = max(worst_literal, abs(literal - true))
+    assert worst_taken <= 1e-12 and worst_literal > 0.5
