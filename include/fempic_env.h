@@ -272,6 +272,20 @@ int fempic_error_count(fempic_env* env, int64_t* n_bad, void* stream);
  * Host only.  Errors: EINVAL. */
 int fempic_debug_stall(fempic_env* env, int32_t cta, int64_t limit_ns);
 
+/* Deposited-current term of the loss for the adjoint steps (the paper has no
+ * adjoint; this differentiates the per-segment deposit g_ij of Sec. II eq.
+ * g_def as the push step applies it): u (device f64 [Ne], read now, not
+ * kept) weights each edge's deposit, and every later
+ * fempic_push_step_adjoint adds the gradient of sum_e u_e dG_e over its
+ * step, dG the step's edge deposit for the species' q w.  The gradient
+ * follows the step's FP64 face walk (the mixed forms' walk agrees with it
+ * except where a path grazes an edge or vertex within the FP32 filter's
+ * margin).  Per tet the kernel stores alpha = sum_j u_{0j} grad l_j and
+ * beta = sum_{i<j} u_{ij} grad l_i x grad l_j (48 B, allocated on first
+ * use).  u == NULL turns the term off.  Stream-ordered.  Errors: EINVAL,
+ * ECUDA. */
+int fempic_adjoint_current_weights(fempic_env* env, const double* u, void* stream);
+
 /* Reverse mode of one fempic_push_step (gradients of a loss of the particle
  * state after some steps, with respect to the envelope DoFs and the initial
  * phase space; the paper has no adjoint, this differentiates its particle
@@ -282,7 +296,10 @@ int fempic_debug_stall(fempic_env* env, int32_t cta, int64_t limit_ns);
  * non-OK status a freeze).  On entry adj holds the adjoint of `after`; on
  * exit the adjoint of `before`.  The derivative is that of the piecewise
  * smooth map for the tet sequence the forward step took.  Particles frozen
- * during the step get a zero adjoint.  e_grad (complex128 [Ne]) and b_grad
+ * during the step get a zero adjoint (plus, with current weights set, the
+ * gradient of the charge they moved before freezing).  When
+ * fempic_adjoint_current_weights has set weights u, the loss also holds
+ * sum_e u_e dG_e of this step's deposit, and its gradient is added.  e_grad (complex128 [Ne]) and b_grad
  * (complex128 [Nf]) accumulate dL/dRe + j dL/dIm of the DoFs (added to, in
  * FP64).  The mixed form differentiates its FP32 push in FP32 and keeps the
  * position adjoint and the DoF gradients in FP64.  Stream-ordered; the

@@ -714,9 +714,29 @@ static void tangent_fields(const omesh *m, int32_t T, const double *r, const dou
 
 static double dot3(const double *a, const double *b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
 
+/* Tangent of one piece's deposit: with lambda_i = lambda_i(start), mu_i =
+ * lambda_i(end) and their tangents dl_i = gl_i . d(start), dm_i = gl_i .
+ * d(end) in this tet, d g_ij = q w (dl_i mu_j + lambda_i dm_j - dl_j mu_i -
+ * lambda_j dm_i). */
+static void deposit_segment_tangent(const omesh *m, int32_t t, const double *la, const double *lb,
+                                    const double *dpa, const double *dpb, double qw, double *dGt) {
+  if (!dGt) return;
+  const double *g = m->gl + 12 * (int64_t)t;
+  double dl[4], dm[4];
+  for (int k = 0; k < 4; k++) {
+    dl[k] = (g[3 * k] * dpa[0] + g[3 * k + 1] * dpa[1]) + g[3 * k + 2] * dpa[2];
+    dm[k] = (g[3 * k] * dpb[0] + g[3 * k + 1] * dpb[1]) + g[3 * k + 2] * dpb[2];
+  }
+  for (int e = 0; e < 6; e++) {
+    int i = LE[e][0], j = LE[e][1];
+    double v = ((dl[i] * lb[j] + la[i] * dm[j]) - dl[j] * lb[i]) - la[j] * dm[i];
+    dGt[m->te[6 * (int64_t)t + e]] += qw * v;
+  }
+}
+
 static void step_one_jvp(const omesh *m, oparts *P, int64_t p, double kq, double qw, double cre, double cim,
                          const double *e_dof, const double *b_dof, double dt, int32_t max_cross, int32_t wall_mode,
-                         double *dG, double *TR, double *TV, const double *de, const double *dbf) {
+                         double *dG, double *TR, double *TV, const double *de, const double *dbf, double *dGt) {
   int32_t T = P->tet[p];
   if (T < 0) return;
   if (T >= m->nt) { P->tet[p] = -1; P->status[p] = OR_LOST; return; }
@@ -769,6 +789,7 @@ static void step_one_jvp(const omesh *m, oparts *P, int64_t p, double kq, double
     }
     if (kx < 0) {
       deposit_segment(m, T, la, lb, qw, dG);
+      deposit_segment_tangent(m, T, la, lb, da, db, qw, dGt);
       for (int c = 0; c < 3; c++) { a[c] = b[c]; da[c] = db[c]; }
       break;
     }
@@ -786,6 +807,7 @@ static void step_one_jvp(const omesh *m, oparts *P, int64_t p, double kq, double
     }
     for (int i = 0; i < 4; i++) lp[i] = (i == kx) ? 0.0 : la[i] + smin * (lb[i] - la[i]);
     deposit_segment(m, T, la, lp, qw, dG);
+    deposit_segment_tangent(m, T, la, lp, da, dpp, qw, dGt);
     ncross++;
     for (int c = 0; c < 3; c++) { a[c] = pp[c]; da[c] = dpp[c]; }
     if (ncross > max_cross) { P->status[p] = OR_CAP; T = -2 - T; break; }
@@ -826,13 +848,15 @@ static void step_one_jvp(const omesh *m, oparts *P, int64_t p, double kq, double
 }
 
 /* One step of values and tangents.  tr, tv: [n][3] tangents of position and
- * velocity, updated in place; de, db: tangent DoFs (complex interleaved). */
+ * velocity, updated in place; de, db: tangent DoFs (complex interleaved);
+ * dGt (length ne, may be NULL): the tangent of the step's deposit is added
+ * to it. */
 int or_push_step_jvp(const void *h, int64_t n, double *x, double *y, double *z, double *vx, double *vy,
                      double *vz, int32_t *tet, uint8_t *status, int32_t *n_cross, int32_t n_species,
                      const int64_t *species_begin, const double *q, const double *mass, const double *w,
                      const double *e_dof, const double *b_dof, double amp, double omega0, double t,
                      double dt, int32_t max_cross, int32_t wall_mode, double *dG, double *tr, double *tv,
-                     const double *de, const double *db) {
+                     const double *de, const double *db, double *dGt) {
   const omesh *m = (const omesh *)h;
   oparts P = {x, y, z, vx, vy, vz, tet, status, n_cross};
   double phi = omega0 * t;
@@ -842,7 +866,7 @@ int or_push_step_jvp(const void *h, int64_t n, double *x, double *y, double *z, 
     double qw = q[s] * w[s];
     int64_t p1 = species_begin[s + 1] < n ? species_begin[s + 1] : n;
     for (int64_t p = species_begin[s]; p < p1; p++)
-      step_one_jvp(m, &P, p, kq, qw, cre, cim, e_dof, b_dof, dt, max_cross, wall_mode, dG, tr, tv, de, db);
+      step_one_jvp(m, &P, p, kq, qw, cre, cim, e_dof, b_dof, dt, max_cross, wall_mode, dG, tr, tv, de, db, dGt);
   }
   return 0;
 }

@@ -63,7 +63,7 @@ def _load():
         lib.or_push_step_jvp.argtypes = ([C.c_void_p, C.c_int64] + [_d] * 6 +
                                          [_i32, _u8, C.c_void_p, C.c_int32, _i64, _d, _d, _d, _d, _d,
                                           C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
-                                          C.c_int32, _d, _d, _d, _d, _d])
+                                          C.c_int32, _d, _d, _d, _d, _d, C.c_void_p])
         lib.or_nodal_charge.argtypes = [C.c_void_p, C.c_int64, _d, _d, _d, _i32, C.c_int32, _i64, _d,
                                         _d, _d]
         lib.or_edge_divergence.argtypes = [C.c_void_p, _d, _d]
@@ -214,11 +214,12 @@ def push_step(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, t, d
 
 
 def push_step_jvp(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, t, dt, dG, tr, tv, de, db,
-                  max_crossings=4096, wall_mode=0):
+                  max_crossings=4096, wall_mode=0, dGt=None):
     """One oracle step of values and forward-mode tangents.
 
     tr, tv: float64 [n, 3] tangents of position and velocity (updated in
-    place); de, db: complex tangent DoFs."""
+    place); de, db: complex tangent DoFs; dGt (float64 [Ne] or None): the
+    tangent of the step's edge deposit is added to it."""
     e = _f64(np.ascontiguousarray(e_dof, np.complex128).view(np.float64))
     b = _f64(np.ascontiguousarray(b_dof, np.complex128).view(np.float64))
     tde = _f64(np.ascontiguousarray(de, np.complex128).view(np.float64))
@@ -229,7 +230,7 @@ def push_step_jvp(mesh: OracleMesh, st: OracleState, e_dof, b_dof, amp, omega0, 
                               st.n_cross.ctypes.data_as(C.c_void_p), len(st.q), st.species_begin, st.q,
                               st.m, st.w, e, b, float(amp), float(omega0), float(t), float(dt),
                               int(max_crossings), int(wall_mode), dG, tr.reshape(-1), tv.reshape(-1),
-                              tde, tdb)
+                              tde, tdb, None if dGt is None else dGt.ctypes.data_as(C.c_void_p))
 
 
 def kinetic_energy_jvp(st: OracleState, tv):

@@ -1,7 +1,9 @@
-"""Gradients of the kinetic energy after K particle steps (reverse mode).
+"""Gradients of a loss of K particle steps (reverse mode): the kinetic
+energy after the steps, or a weighted sum of the edge current they deposit.
 
 Every derivative is computed by the library's kernels
-(`fempic_push_step_adjoint`, `fempic_kinetic_energy`); this module only
+(`fempic_push_step_adjoint`, `fempic_kinetic_energy`,
+`fempic_adjoint_current_weights`); this module only
 schedules them: a forward pass that keeps a checkpoint of the particle state
 every `every` steps, then a reverse sweep that, segment by segment from the
 last, recomputes the segment's states from its checkpoint and runs the adjoint
@@ -12,9 +14,11 @@ Each checkpoint is taken after sorting the state by (species, tet)
 (`fempic_sort_perm`), so the steps of every segment run on tet-ordered
 particles; the reverse sweep carries the adjoint back across each of those
 sorts with `fempic_adjoint_unpermute`.  The gradient is returned in the
-particle order of the initial state.  The window's steps run with the
-deposit off (`fempic_set_deposit`): the loss does not depend on the
-deposited charge, and the env's accumulated deposit is left untouched.
+particle order of the initial state.  For the kinetic energy the window's
+steps run with the deposit off (`fempic_set_deposit`): that loss does not
+depend on the deposited charge.  For the current loss the forward steps
+deposit and each step's deposit is taken out with `fempic_deposit_local`.
+Either way the env's accumulated deposit is left untouched.
 
 The derivative is that of the piecewise smooth map for the tet sequence the
 forward run took (a particle that crosses a face keeps the crossing; a
@@ -116,13 +120,31 @@ class Checkpoint:
         self.st, self.perm = st, perm
 
 
-def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule, sort: bool = True):
-    """Run sch.steps steps from a copy of st0; returns (final state,
-    checkpoints).  With `sort`, the state is sorted by tet at every
-    checkpoint (the final state is in the last checkpoint's order)."""
+class _DepositOn:
+    """The window's steps deposit (for a loss of the deposited current); each
+    step's deposit is taken out with fempic_deposit_local, so G_cum is left
+    as it was."""
+
+    def __init__(self, env: FempicEnv):
+        self.env = env
+
+    def __enter__(self):
+        self.prev = self.env.deposit_on
+        self.env.set_deposit(True)
+
+    def __exit__(self, *exc):
+        self.env.set_deposit(self.prev)
+        return False
+
+
+def _forward(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule, sort: bool, u=None):
     st = st0 if (sort and sch.steps > 0) else clone_state(st0)
     ckpts = []
-    with _DepositOff(env):
+    L = None
+    if u is not None:
+        L = torch.zeros((), dtype=torch.float64, device=st.x.device)
+        dG = torch.empty(env.n_edges, dtype=torch.float64, device=st.x.device)
+    with (_DepositOn(env) if u is not None else _DepositOff(env)):
         for k in range(sch.steps):
             if k % sch.every == 0:
                 if sort:
@@ -134,6 +156,17 @@ def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule
                 else:
                     ckpts.append(Checkpoint(clone_state(st), None))
             _step(env, st, e, b, sch, k)
+            if u is not None:
+                env.deposit_local(dG)
+                L += torch.dot(u, dG)
+    return st, ckpts, L
+
+
+def forward_checkpointed(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule, sort: bool = True):
+    """Run sch.steps steps from a copy of st0; returns (final state,
+    checkpoints).  With `sort`, the state is sorted by tet at every
+    checkpoint (the final state is in the last checkpoint's order)."""
+    st, ckpts, _ = _forward(env, st0, e, b, sch, sort)
     return st, ckpts
 
 
@@ -187,6 +220,41 @@ def kinetic_energy_and_grad(env: FempicEnv, st0: ParticleState, e, b, sch: Sched
         from .shard import allreduce_
         allreduce_(L.view(1), group)
     eg, bg = reverse_sweep(env, ckpts, e, b, sch, adj, group=group)
+    return L, eg, bg, adj
+
+
+class _CurrentWeights:
+    """Adjoint steps inside the block add the gradient of sum_e u_e dG_e."""
+
+    def __init__(self, env: FempicEnv, u):
+        self.env, self.u = env, u
+
+    def __enter__(self):
+        capi.fempic_adjoint_current_weights(self.env.h, _ptr(self.u), _stream(None))
+
+    def __exit__(self, *exc):
+        capi.fempic_adjoint_current_weights(self.env.h, None, _stream(None))
+        return False
+
+
+def current_loss_and_grad(env: FempicEnv, st0: ParticleState, e, b, sch: Schedule, u, group=None,
+                          sort: bool = True):
+    """(L, dL/de, dL/db, adjoint of the initial state) for the deposited-current
+    loss L = sum_e u_e (G_cum after sch.steps steps - G_cum before), i.e. the
+    weights u (device f64 [Ne]) applied to the edge deposit of the window's
+    steps.  The env must hold no pending step deposit (finalize it first);
+    the window's deposits are taken out step by step and G_cum is left
+    unchanged.  With a process group, L and the DoF gradients are those of
+    the whole sharded load."""
+    u = u.to(torch.float64).contiguous()
+    final, ckpts, L = _forward(env, st0, e, b, sch, sort, u=u)
+    vdt = torch.float64 if env.precision == FEMPIC_FP64 else torch.float32
+    adj = AdjointState(st0.n, vdt, device=st0.x.device)   # the final state does not enter L
+    if group is not None:
+        from .shard import allreduce_
+        allreduce_(L.view(1), group)
+    with _CurrentWeights(env, u):
+        eg, bg = reverse_sweep(env, ckpts, e, b, sch, adj, group=group)
     return L, eg, bg, adj
 
 

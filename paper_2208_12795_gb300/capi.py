@@ -30,7 +30,7 @@ FEMPIC_WALL_ABSORB = 1
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step", "fempic_push_step3",
            "fempic_lagrange3",
            "fempic_deposit", "fempic_deposit_local", "fempic_accumulate", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
-           "fempic_error_count", "fempic_debug_stall", "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
+           "fempic_error_count", "fempic_debug_stall", "fempic_adjoint_current_weights", "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
            "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read",
            "fempic_measure_fp64_rate", "fempic_last_error", "fempic_env_destroy")
 # Every function declared in include/fempic_downshift.h.
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_error_count.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_debug_stall.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
+        lib.fempic_adjoint_current_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_push_step_adjoint.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles),
                                                  P(fempic_envelope), C.c_double, C.c_double, C.c_double,
                                                  P(fempic_adjoint), C.c_void_p, C.c_void_p, C.c_void_p]
@@ -234,6 +235,10 @@ def fempic_error_count(env, stream=0) -> tuple:
 
 def fempic_debug_stall(env, cta: int, limit_ns: int):
     check(load().fempic_debug_stall(env, int(cta), int(limit_ns)), "fempic_debug_stall")
+
+
+def fempic_adjoint_current_weights(env, u, stream=0):
+    check(load().fempic_adjoint_current_weights(env, u, stream), "fempic_adjoint_current_weights")
 
 
 def fempic_push_step_adjoint(env, before: fempic_particles, after: fempic_particles, envl: fempic_envelope,

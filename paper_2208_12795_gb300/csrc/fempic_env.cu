@@ -2249,7 +2249,253 @@ struct AdjArgs {
   void* vbz;
   double* tetgrad;           // [nt][10]
   float* tetgrad32;          // mixed form: [nt][12] (10 used), per-lane vector atomics
+  // deposited-current loss (fempic_adjoint_current_weights): per-tet alpha, beta [nt][6], or NULL
+  const double* curw;
+  const int4* nb;
+  const int4* tn;
+  int32_t max_cross;
+  int32_t wall_mode;
+  double lo[3], hi[3];
 };
+
+// ------------------------------------------------ adjoint of the deposit
+// Loss L = sum_e u_e dG_e over the step's deposit.  Inside a tet the
+// deposit of a straight piece p -> q is linear in (q - p) and in the moment
+// (p - x0) x (q - p) (g_0j = G_j . D + (G_0 x G_j) . M, g_ij = (G_i x G_j) .
+// M), so its share of L is alpha . (q - p) + beta . ((p - x0) x (q - p))
+// with the per-tet vectors alpha = sum_j u_0j G_j and beta = sum_e u_e
+// (G_i x G_j) (k_current_weights).  The gradient of one particle's share
+// with respect to its start a and displacement w (the straight run a -> a +
+// w) follows the FP64 walk again: a crossing point q = a0 + S w on face f
+// moves in the face plane, dq = P (da0 + S dw) with P = I - w G_f^T / (G_f .
+// w); a wall reflection starts a new run a0' = q, w' = M (1 - S) w (M the
+// mirror), whose Jacobian is folded into the running 6 x 6 one.
+__device__ __forceinline__ void cross3d(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double dot3d(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Gradient rows of tet T (FP64): G[k] = grad lambda_k, G_0 = -(G_1 + G_2 + G_3).
+__device__ __forceinline__ void grads64(const double* geom64, int32_t T, double G[4][3]) {
+  const double* g = geom64 + 12 * (int64_t)T;
+#pragma unroll
+  for (int k = 1; k < 4; k++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) G[k][c] = g[3 * k + c];
+#pragma unroll
+  for (int c = 0; c < 3; c++) G[0][c] = -((G[1][c] + G[2][c]) + G[3][c]);
+}
+
+// d(loss)/d(a), d(loss)/d(w) of one particle-step whose run starts at a with
+// end b (= a + w as the forward step formed it), tet T0 at the start.
+// The 6 x 6 Jacobian lives in local memory (loops not unrolled): only
+// particles that reflected in this step touch it.
+__device__ __noinline__ void dep_loss_grad(const AdjArgs& A, int32_t T0, const double a[3], const double b_in[3],
+                                           double ga[3], double gw[3]) {
+  double a0[3], b[3], w[3], pnt[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    a0[c] = a[c];
+    b[c] = b_in[c];
+    w[c] = b[c] - a[c];
+    pnt[c] = a[c];
+    ga[c] = gw[c] = 0.0;
+  }
+  double J[6][6];          // d(a0, w of the current run) / d(a, w of the step), once a wall reflected it
+  bool refl = false;
+  double gprev[3] = {0.0, 0.0, 0.0}, Sprev = 0.0;
+  bool on_face = false;    // the piece start is a crossing point of this run (face gradient gprev)
+  double S = 0.0;
+  int32_t T = T0;
+  int entry = -1, nc = 0;
+  double la[4], lb[4];
+  bary64(A.geom64 + 12 * (int64_t)T, pnt, la);
+  for (;;) {
+    bary64(A.geom64 + 12 * (int64_t)T, b, lb);
+    int kx = -1;
+    double smin = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (k == entry || !negative_bits(lb[k])) continue;
+      double sk = la[k] / (la[k] - lb[k]);
+      if (sk < 0.0) sk = 0.0;
+      if (sk < smin) {
+        smin = sk;
+        kx = k;
+      }
+    }
+    double G[4][3];
+    grads64(A.geom64, T, G);
+    const double* cw = A.curw + 6 * (int64_t)T;
+    const double al[3] = {cw[0], cw[1], cw[2]}, be[3] = {cw[3], cw[4], cw[5]};
+    const double* x0 = A.geom64 + 12 * (int64_t)T;
+    double q[3], Sq = 1.0;
+    if (kx < 0) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) q[c] = b[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++) q[c] = fma(smin, b[c] - pnt[c], pnt[c]);
+      Sq = S + smin * (1.0 - S);
+    }
+    // this piece's gradients at its ends
+    double u[3], d[3], bu[3], db_[3], gp[3], gq[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      u[c] = pnt[c] - x0[c];
+      d[c] = q[c] - pnt[c];
+    }
+    cross3d(be, u, bu);
+    cross3d(d, be, db_);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      gp[c] = -al[c] - bu[c] + db_[c];
+      gq[c] = al[c] + bu[c];
+    }
+    // ... through the ends' dependence on (a0, w) of this run
+    double ca[3], cwv[3];
+    {
+      double tp[3];
+      if (on_face) {
+        const double f = dot3d(w, gp) / dot3d(gprev, w);
+#pragma unroll
+        for (int c = 0; c < 3; c++) tp[c] = gp[c] - gprev[c] * f;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; c++) tp[c] = gp[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        ca[c] = tp[c];
+        cwv[c] = on_face ? Sprev * tp[c] : 0.0;
+      }
+      if (kx < 0) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          ca[c] += gq[c];
+          cwv[c] += gq[c];
+        }
+      } else {
+        const double f = dot3d(w, gq) / dot3d(G[kx], w);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const double t = gq[c] - G[kx][c] * f;
+          ca[c] += t;
+          cwv[c] += Sq * t;
+        }
+      }
+    }
+    // ... and through the run's dependence on the step's (a, w)
+    if (refl) {
+#pragma unroll 1
+      for (int i = 0; i < 3; i++) {
+        double sa = 0.0, sw = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+          sa += J[r][i] * ca[r] + J[3 + r][i] * cwv[r];
+          sw += J[r][3 + i] * ca[r] + J[3 + r][3 + i] * cwv[r];
+        }
+        ga[i] += sa;
+        gw[i] += sw;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        ga[c] += ca[c];
+        gw[c] += cwv[c];
+      }
+    }
+    if (kx < 0) break;
+    double lp[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) lp[i] = (i == kx) ? 0.0 : fma(smin, lb[i] - la[i], la[i]);
+    nc++;
+    if (nc > A.max_cross) break;   // frozen at q: the deposit ended there
+    const int4 nbv = ldg_int4(&A.nb[T]);
+    const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+    if (nbt >= 0) {
+      const int4 o4 = ldg_int4(&A.tn[T]), n4 = ldg_int4(&A.tn[nbt]);
+      const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nn[4] = {n4.x, n4.y, n4.z, n4.w};
+      int ent = 0;
+#pragma unroll
+      for (int i2 = 0; i2 < 4; i2++) {
+        int hit = -1;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+          if (on[i] == nn[i2]) hit = i;
+        double val = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+          if (i == hit) val = lp[i];
+        la[i2] = val;
+        if (hit < 0) ent = i2;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        gprev[c] = G[kx][c];
+        pnt[c] = q[c];
+      }
+      Sprev = Sq;
+      S = Sq;
+      on_face = true;
+      T = nbt;
+      entry = ent;
+    } else if (nbt <= -1 && nbt >= -6 && A.wall_mode == FEMPIC_WALL_REFLECT) {
+      // new run a0' = q, w' = M (1 - Sq) w: its Jacobian with respect to this run
+      const int code = -1 - nbt, ax = code >> 1, side = code & 1;
+      const double gfw = dot3d(G[kx], w);
+      double Jr[6][6];
+#pragma unroll 1
+      for (int i = 0; i < 3; i++)
+#pragma unroll 1
+        for (int j = 0; j < 3; j++) {
+          const double pij = (i == j ? 1.0 : 0.0) - w[i] * G[kx][j] / gfw;   // P = I - w G_f^T / (G_f . w)
+          const double mi = (i == ax) ? -1.0 : 1.0;
+          Jr[i][j] = pij;
+          Jr[i][3 + j] = Sq * pij;
+          Jr[3 + i][j] = mi * w[i] * G[kx][j] / gfw;
+          Jr[3 + i][3 + j] = mi * ((i == j ? 1.0 - Sq : 0.0) + Sq * w[i] * G[kx][j] / gfw);
+        }
+      if (refl) {
+        double Jn[6][6];
+#pragma unroll 1
+        for (int i = 0; i < 6; i++)
+#pragma unroll 1
+          for (int j = 0; j < 6; j++) {
+            double acc = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < 6; k++) acc += Jr[i][k] * J[k][j];
+            Jn[i][j] = acc;
+          }
+#pragma unroll 1
+        for (int i = 0; i < 36; i++) J[i / 6][i % 6] = Jn[i / 6][i % 6];
+      } else {
+#pragma unroll 1
+        for (int i = 0; i < 36; i++) J[i / 6][i % 6] = Jr[i / 6][i % 6];
+        refl = true;
+      }
+      const double L = side ? A.hi[ax] : A.lo[ax];
+      b[ax] = 2.0 * L - b[ax];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        a0[c] = q[c];
+        pnt[c] = q[c];
+        w[c] = b[c] - a0[c];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; i++) la[i] = lp[i];
+      entry = kx;
+      S = 0.0;
+      on_face = false;
+    } else {
+      break;   // absorbed at q
+    }
+  }
+}
 
 template <typename R>
 struct Vec {
@@ -2270,7 +2516,7 @@ __device__ __forceinline__ double flip_sign(double x, bool neg) {
 __device__ __forceinline__ double widen(float x) { return f32_to_f64(x); }
 __device__ __forceinline__ double widen(double x) { return x; }
 
-template <typename R>
+template <typename R, bool DEP>
 __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, int32_t T, R out[10]) {
   const int s = species_of(A.sp, p);
   const R kq = (R)A.sp.kq[s];
@@ -2330,6 +2576,22 @@ __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, in
   const R dt = (R)A.dt;
   // b = r + dt vn
   Vec<R> vnb = {mx * vbx[p] + dt * (R)rbx, my * vby[p] + dt * (R)rby, mz * vbz[p] + dt * (R)rbz};
+  double dga[3] = {0.0, 0.0, 0.0};
+  if (DEP) {   // this step's share of the deposited-current loss, through a and w = dt vn
+    const double a[3] = {A.x[p], A.y[p], A.z[p]};
+    const R vf[3] = {mx * vx1[p], my * vy1[p], mz * vz1[p]};   // the forward's vn, exactly
+    double b[3], gw[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      b[c] = sizeof(R) == 8 ? fma(A.dt, (double)vf[c], a[c]) : advance(a[c], (float)A.dt, (float)vf[c]);
+    dep_loss_grad(A, T, a, b, dga, gw);
+    const double qw = A.sp.qw[s];
+    vnb.x += (R)(A.dt * qw * gw[0]);
+    vnb.y += (R)(A.dt * qw * gw[1]);
+    vnb.z += (R)(A.dt * qw * gw[2]);
+#pragma unroll
+    for (int c = 0; c < 3; c++) dga[c] *= qw;
+  }
   // vn = vpl + kq E ;  vpl = vm + vp x s
   Vec<R> Eb = {kq * vnb.x, kq * vnb.y, kq * vnb.z};
   Vec<R> vmb = vnb;
@@ -2353,9 +2615,9 @@ __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, in
   const Vec<R> Wb = vx3(Eb, d);
   const Vec<R> db1 = vx3(W, Eb);
   const R betab = vd3(Bb, d);
-  A.rbx[p] = rbx + widen(db1.x + beta * Bb.x);
-  A.rby[p] = rby + widen(db1.y + beta * Bb.y);
-  A.rbz[p] = rbz + widen(db1.z + beta * Bb.z);
+  A.rbx[p] = (rbx + dga[0]) + widen(db1.x + beta * Bb.x);
+  A.rby[p] = (rby + dga[1]) + widen(db1.y + beta * Bb.y);
+  A.rbz[p] = (rbz + dga[2]) + widen(db1.z + beta * Bb.z);
   vbx[p] = vmb.x;
   vby[p] = vmb.y;
   vbz[p] = vmb.z;
@@ -2365,7 +2627,7 @@ __device__ __forceinline__ void adjoint_particle(const AdjArgs& A, int64_t p, in
   out[9] = betab;
 }
 
-template <typename R>
+template <typename R, bool DEP>
 __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -2376,11 +2638,14 @@ __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
   if (p < A.n) {
     const int32_t T = A.tet[p];
     if (T >= 0 && T < A.nt) {
-      if (A.status1[p] != FEMPIC_P_OK) {   // frozen during the step
+      const uint8_t s1 = A.status1[p];
+      if (s1 != FEMPIC_P_OK) {   // frozen during the step: its later state does not enter the loss
         A.rbx[p] = A.rby[p] = A.rbz[p] = 0.0;
         static_cast<R*>(A.vbx)[p] = static_cast<R*>(A.vby)[p] = static_cast<R*>(A.vbz)[p] = R(0);
-      } else {
-        adjoint_particle<R>(A, p, T, g);
+      }
+      // ... but the charge it moved before it froze does
+      if (s1 == FEMPIC_P_OK || (DEP && (s1 == FEMPIC_P_CAP || s1 == FEMPIC_P_ABSORBED))) {
+        adjoint_particle<R, DEP>(A, p, T, g);
         key = T;
       }
     }
@@ -2420,6 +2685,41 @@ __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
       for (int i = 0; i < 10; i++)
         if (g[i] != R(0)) atomicAdd(tg + i, (double)g[i]);
     }
+  }
+}
+
+// Per-tet weights of the deposited-current loss L = sum_e u_e dG_e: alpha =
+// sum_j u_{0j} G_j and beta = sum_{i<j} u_{ij} (G_i x G_j), with G_0 = -(G_1 +
+// G_2 + G_3), so that a piece p -> q in the tet adds alpha . (q - p) + beta .
+// ((p - x0) x (q - p)) to L per unit charge.
+__global__ void __launch_bounds__(kThreads) k_current_weights(int64_t nt, const double* __restrict__ geom64,
+                                                               const int4* __restrict__ te,
+                                                               const double* __restrict__ u,
+                                                               double* __restrict__ curw) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double G[4][3];
+  grads64(geom64, (int32_t)t, G);
+  const int4 e0 = te[2 * t], e1 = te[2 * t + 1];
+  const int32_t eid[6] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y};
+  double al[3] = {0.0, 0.0, 0.0}, be[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int e = 0; e < 6; e++) {
+    const int i = le0(e), j = le1(e);
+    const double ue = u[eid[e]];
+    double c[3];
+    cross3d(G[i], G[j], c);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      be[k] = fma(ue, c[k], be[k]);
+      if (i == 0) al[k] = fma(ue, G[j][k], al[k]);
+    }
+  }
+  double* o = curw + 6 * t;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    o[k] = al[k];
+    o[3 + k] = be[k];
   }
 }
 
@@ -2628,6 +2928,8 @@ struct fempic_env {
   double* tetgrad = nullptr;        // adjoint of the per-tet affine field [nt][10]
   float* tetgrad32 = nullptr;       // mixed form: the same from per-lane atomics, [nt][12]
   double* tadj = nullptr;           // per-tet DoF-adjoint terms of one adjoint step [nt][10]
+  double* curw = nullptr;           // deposited-current loss weights alpha, beta per tet [nt][6]
+  bool curw_on = false;
   int32_t* estart = nullptr;        // edge -> (tet, local edge) slots, CSR [ne + 1]
   int32_t* eslot = nullptr;         // [6 nt], slot = 6 tet + local edge
   int32_t* fslot = nullptr;         // face -> (tet, local face) slots [nf][2], 4 tet + local face or -1
@@ -2696,7 +2998,7 @@ static void free_env(fempic_env* e) {
   for (cudaEvent_t ev : e->pool) cudaEventDestroy(ev);
   void* ptrs[] = {e->geom64, e->tetrec, e->tn, e->nb, e->te, e->tf, e->field, e->dG, e->dGq, e->tetdf, e->mom,
                   e->momlo, e->tetout,
-                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->tadj, e->estart, e->eslot, e->fslot, e->xrec, e->xrec64, e->xcount,
+                  e->Gcum, e->stats, e->gstart, e->gtet, e->sort_counts, e->sort_offsets, e->sort_sums, e->tetgrad, e->tetgrad32, e->tadj, e->curw, e->estart, e->eslot, e->fslot, e->xrec, e->xrec64, e->xcount,
                   nullptr};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -3798,10 +4100,26 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
     A.vbz = adj->vz;
     A.tetgrad = env->tetgrad;
     A.tetgrad32 = env->tetgrad32;
-    if (mixed)
-      k_push_adjoint<float><<<blocks_for(A.n), kThreads, 0, st>>>(A);
-    else
-      k_push_adjoint<double><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+    A.curw = env->curw_on ? env->curw : nullptr;
+    A.nb = env->nb;
+    A.tn = env->tn;
+    A.max_cross = env->opt.max_crossings;
+    A.wall_mode = env->opt.wall_mode;
+    for (int a = 0; a < 3; a++) {
+      A.lo[a] = env->h.lo[a];
+      A.hi[a] = env->h.hi[a];
+    }
+    if (mixed) {
+      if (A.curw)
+        k_push_adjoint<float, true><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+      else
+        k_push_adjoint<float, false><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+    } else {
+      if (A.curw)
+        k_push_adjoint<double, true><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+      else
+        k_push_adjoint<double, false><<<blocks_for(A.n), kThreads, 0, st>>>(A);
+    }
     lt.kernels++;
     FEMPIC_CUDA(cudaGetLastError());
   }
@@ -3818,6 +4136,21 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
                                                      static_cast<double*>(b_grad));
   lt.kernels++;
   FEMPIC_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_adjoint_current_weights(fempic_env* env, const double* u, void* stream) {
+  if (!env) return fail(FEMPIC_EINVAL, "adjoint_current_weights: NULL env");
+  if (!u) {
+    env->curw_on = false;
+    return FEMPIC_OK;
+  }
+  const int64_t nt = env->h.nt;
+  if (!env->curw) FEMPIC_CUDA(dalloc(&env->curw, 6 * nt));
+  cudaStream_t st = (cudaStream_t)stream;
+  k_current_weights<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, u, env->curw);
+  FEMPIC_CUDA(cudaGetLastError());
+  env->curw_on = true;
   return FEMPIC_OK;
 }
 

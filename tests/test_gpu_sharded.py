@@ -1,8 +1,9 @@
 """The sharded particle path (paper_2208_12795_gb300.shard) on the GPU: two
 processes on one GPU, each advancing a contiguous tet range of one tet-sorted
 load, all-reducing the step's edge deposit over gloo (host copies) and
-adding it to G_cum with fempic_accumulate; the gradient window with the DoF
-gradients summed over the ranks.  G_cum, the envelope-frame G~ and the
+adding it to G_cum with fempic_accumulate; the gradient windows (kinetic
+energy, deposited current) with the loss and the DoF gradients summed over
+the ranks.  G_cum, the envelope-frame G~ and the
 gradients equal those of one process holding the whole load, to 1e-13 of
 their maxima (summation order differs).  The processes' kernels never wait on
 each other: the only exchange is the host-side all-reduce between steps."""
@@ -59,12 +60,18 @@ def _run(env, st, wl, deposit):
     return Gc.cpu().numpy(), Ge.cpu().numpy()
 
 
-def _grad(env, st, wl, group=None):
+def _grad(env, st, wl, group=None, current=False):
+    """Kinetic-energy loss, or (current) the deposited-current loss with
+    seeded edge weights."""
     from paper_2208_12795_gb300 import adjoint as A
     e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
     b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
     sch = A.Schedule(wl.amp, wl.omega0, wl.dt, K, 3)
-    L, eg, bg, adj = A.kinetic_energy_and_grad(env, st, e, b, sch, group=group)
+    if current:
+        u = torch.from_numpy(np.random.default_rng(8).standard_normal(env.n_edges)).cuda()
+        L, eg, bg, adj = A.current_loss_and_grad(env, A.clone_state(st), e, b, sch, u, group=group)
+    else:
+        L, eg, bg, adj = A.kinetic_energy_and_grad(env, st, e, b, sch, group=group)
     return float(L.item()), eg.cpu().numpy(), bg.cpu().numpy(), adj.vx.cpu().numpy().astype(np.float64)
 
 
@@ -85,9 +92,11 @@ def _worker(rank, world, port, prec, q):
     st2, ids = _global_sorted(env, wl, prec)
     n = st2.n
     a, b = rank * n // world, (rank + 1) * n // world
-    L, eg, bg, av = _grad(env, shard.tet_range(st2, rank, world), wl, group=dist.group.WORLD)
+    mine2 = shard.tet_range(st2, rank, world)
+    cur = _grad(env, mine2, wl, group=dist.group.WORLD, current=True)
+    L, eg, bg, av = _grad(env, mine2, wl, group=dist.group.WORLD)
     torch.cuda.synchronize()
-    q.put((rank, Gc, Ge, L, eg, bg, (ids[a:b], av)))
+    q.put((rank, Gc, Ge, L, eg, bg, (ids[a:b], av), cur[:3]))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -117,8 +126,9 @@ def test_two_processes_equal_one(prec):
     st, _ = _global_sorted(env, wl, prec)
     Gc, Ge = _run(env, st, wl, lambda om, t1, gc, ge: env.deposit(om, t1, G_cum_out=gc, G_env_out=ge))
     st2, ids = _global_sorted(env, wl, prec)
+    cur = _grad(env, st2, wl, current=True)
     L, eg, bg, av = _grad(env, st2, wl)
-    (Gc0, Ge0, L0, eg0, bg0, av0), (Gc1, Ge1, L1, eg1, bg1, av1) = got[0], got[1]
+    (Gc0, Ge0, L0, eg0, bg0, av0, cur0), (Gc1, Ge1, L1, eg1, bg1, av1, cur1) = got[0], got[1]
     tol = 1e-13
     for a in (Gc0, Gc1):
         assert np.abs(a - Gc).max() <= tol * np.abs(Gc).max()
@@ -136,5 +146,10 @@ def test_two_processes_equal_one(prec):
         got_v[sid] = sv
     assert not np.isnan(got_v).any() and len(av0[0]) == n // 2 and len(av1[0]) == n - n // 2
     assert np.abs(got_v - ref).max() <= gtol * np.abs(ref).max()
+    # the deposited-current loss: L and the DoF gradients summed over the ranks
+    for c in (cur0, cur1):
+        assert abs(c[0] - cur[0]) <= 1e-12 * abs(cur[0])
+        for a, ref in ((c[1], cur[1]), (c[2], cur[2])):
+            assert np.abs(a - ref).max() <= gtol * np.abs(ref).max()
     print(f"\n[sharded x2 prec={prec}] G_cum {np.abs(Gc0 - Gc).max() / np.abs(Gc).max():.2e}  "
           f"G~ {np.abs(Ge0 - Ge).max() / np.abs(Ge).max():.2e}  e-grad {np.abs(eg0 - eg).max() / np.abs(eg).max():.2e}")

@@ -143,3 +143,54 @@ def test_jvp_values_follow_the_step_on_face_ending_segments():
     assert (s1.n_cross == 1).sum() > n // 10
     for k in ("tet", "n_cross", "status", "x", "y", "z", "vx", "vy", "vz"):
         assert np.array_equal(getattr(s1, k), getattr(s2, k)), k
+
+
+@pytest.mark.parametrize("maker,K,wall", [(lambda: I.workload_hot_small(n_particles=60), 5, 0),
+                                          (lambda: I.workload_hot_small(n_particles=60, wall_mode=1), 5, 1),
+                                          (I.workload_small, 15, 0)])
+def test_deposit_tangent_matches_central_differences(maker, K, wall):
+    """The tangent of the accumulated edge deposit G after K steps (pieces
+    split at crossings, wall reflections, absorption): every edge's value
+    against central differences of the oracle's own deposit, with the tet
+    sequence held (checked) so that G is smooth between the two runs."""
+    wl = maker()
+    om = OracleMesh(wl.mesh.nodes, wl.mesh.tets)
+    P = wl.particles
+    tet, _ = om.locate(P.x, P.y, P.z)
+    rng = np.random.default_rng(61)
+    n = P.n
+    sv = np.std(np.r_[P.vx, P.vy, P.vz])
+
+    def run(Pp, e, b, jvp=None):
+        st = OracleState(Pp, tet)
+        G = np.zeros(om.n_edges)
+        dGt = np.zeros(om.n_edges)
+        if jvp is not None:
+            tr, tv, de, db = (x.copy() for x in jvp)
+        for k in range(K):
+            t = k * wl.dt
+            if jvp is None:
+                push_step(om, st, e, b, wl.amp(t), wl.omega0, t, wl.dt, G, wall_mode=wall)
+            else:
+                push_step_jvp(om, st, e, b, wl.amp(t), wl.omega0, t, wl.dt, G, tr, tv, de, db, wall_mode=wall,
+                              dGt=dGt)
+        return st, G, dGt
+
+    for trial in range(3):
+        de = (rng.standard_normal(om.n_edges) + 1j * rng.standard_normal(om.n_edges)) * np.abs(wl.e_tilde).max()
+        db = (rng.standard_normal(om.n_faces) + 1j * rng.standard_normal(om.n_faces)) * np.abs(wl.b_tilde).max()
+        tv = rng.standard_normal((n, 3)) * sv
+        tr = rng.standard_normal((n, 3)) * 1e-3 * wl.mesh.h
+        base, G0, dGt = run(P, wl.e_tilde, wl.b_tilde, jvp=(tr, tv, de, db))
+        h = 1e-7
+        Gs = []
+        for sgn in (1, -1):
+            Pp = I.Particles(P.x + sgn * h * tr[:, 0], P.y + sgn * h * tr[:, 1], P.z + sgn * h * tr[:, 2],
+                             P.vx + sgn * h * tv[:, 0], P.vy + sgn * h * tv[:, 1], P.vz + sgn * h * tv[:, 2],
+                             P.species_begin, P.q, P.m, P.w)
+            st, G, _ = run(Pp, wl.e_tilde + sgn * h * de, wl.b_tilde + sgn * h * db)
+            assert np.array_equal(st.tet, base.tet) and np.array_equal(st.n_cross, base.n_cross)
+            Gs.append(G)
+        fd = (Gs[0] - Gs[1]) / (2 * h)
+        assert np.abs(dGt).max() > 0
+        assert np.abs(fd - dGt).max() <= 1e-5 * np.abs(dGt).max(), (np.abs(fd - dGt).max(), np.abs(dGt).max())
