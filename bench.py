@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--no-downshift", action="store_true", help="skip the downshifted-integrator measurement")
     ap.add_argument("--no-errors", action="store_true", help="skip the per-quantity error report against the oracle")
     ap.add_argument("--no-large", action="store_true", help="skip the 50M jittered and 400M two-species legs")
-    ap.add_argument("--large-steps", type=int, default=5)
+    ap.add_argument("--large-steps", type=int, default=None,
+                    help="steps of the large legs (default: the workloads' own, 50 for jittered64, 20 for large96)")
     ap.add_argument("--workload", choices=("cube48", "jittered64", "large96"), default="cube48",
                     help="cube48: 48^3x6 cube, 10M e- (headline); jittered64: 64^3x6 jittered cube, 50M "
                          "(10 keV beam + cosine plasma), random DoFs; large96: 96^3x6 cube, 400M e- + ions")
@@ -91,6 +92,28 @@ def bytes_alg_per_step(n_p, counts, form):
     s_dof = 16 if form == "fp64" else 8
     nn, ne, nf, nt = counts
     return n_p * 2 * s_p + 72 * nt + 24 * nn + (s_dof + 8) * ne + s_dof * nf
+
+
+def bytes_reverse_window(n_p, counts, form, steps, every, stash, recompute_steps):
+    """Algorithmic bytes of a window's reverse sweep: the recomputed forward
+    steps; per step in stash mode a copy of the new state (read + write), or
+    in recompute mode the two state copies that seed each step's pair; per
+    adjoint step the state before it (positions, velocities, tet), the
+    velocities and status after it, the adjoint state read and written, and
+    the per-tet and DoF gradient terms; per segment the checkpoint copy and
+    the adjoint unpermute (adjoint read + written, permutation read)."""
+    nn, ne, nf, nt = counts
+    s_state = 53 if form == "fp64" else 41
+    s_adj = 48 if form == "fp64" else 36
+    before = 52 if form == "fp64" else 40
+    after = (24 if form == "fp64" else 12) + 1
+    segs = -(-steps // every)
+    per_step_mesh = 72 * nt + 4 * 80 * nt + 32 * (ne + nf)
+    b = recompute_steps * bytes_alg_per_step(n_p, counts, form)
+    b += steps * n_p * 2 * s_state * (1 if stash else 2)
+    b += steps * (n_p * (before + after + 2 * s_adj) + per_step_mesh)
+    b += segs * n_p * (2 * s_state + 2 * s_adj + 4)
+    return b
 
 
 def bytes_alg_per_step_downshift(n_p, counts):
@@ -632,7 +655,10 @@ def run_ours(args):
     if args.workload == "cube48" and not args.no_errors:
         out["errors"] = config2_errors(wl, 100_000, 100)
     if args.workload == "cube48" and not args.no_large and world == 1:
-        out["large"] = {k: large_leg(k, args.large_steps, 2, args.sort_every) for k in ("jittered64", "large96")}
+        own = {"jittered64": 50, "large96": 20}
+        out["large"] = {k: large_leg(k, args.large_steps or own[k], 2, args.sort_every) for k in own}
+        if not args.no_adjoint:
+            out["large_adjoint"] = large_adjoint_leg(args.large_steps or own["large96"])
     from paper_2208_12795_gb300 import capi as _capi
     out["fp64_rate"] = _capi.fempic_measure_fp64_rate(torch.cuda.current_stream().cuda_stream)
     if rank == 0:
@@ -689,7 +715,81 @@ def adjoint_window(rank):
         env.close()
     return {"workload": "cube48_4M_adjoint: 48^3x6 cube, 4M electrons at 5 eV, TE101 10 kV/m, K=50, "
                         "checkpoint every 10; loss = kinetic energy after K steps",
-            "unit": "particle-steps/s", "particles": wl.particles.n, "counts": counts, **res}
+            "unit": "particle-steps/s", "particles": wl.particles.n, "counts": counts, "steps": wl.steps,
+            "every": 10, **res}
+
+
+def large_adjoint_leg(steps):
+    """Gradient window on the 96^3 two-species load (400M particles, contract
+    mixed form): kinetic energy after `steps` steps, gradients with respect
+    to the DoFs and the initial phase space.  adjoint.plan_window picks the
+    checkpoint interval and the reverse mode for 85% of the device memory
+    free once the load is resident; the plan's predicted peak is reported
+    beside the allocator's measured one."""
+    import torch
+    from paper_2208_12795_gb300 import adjoint as A, inputs as I
+    from paper_2208_12795_gb300.env import FempicEnv, ParticleState
+    wl = I.workload_large96(n_particles=2)
+    cols, table = I.device_two_species(400_000_000, I.SEED_BASE + 50, vdtype=torch.float32)
+    n = int(cols[0].numel())
+    vel = [c.to(torch.float32) for c in cols[3:]]
+    st0 = ParticleState(cols[0], cols[1], cols[2], vel[0], vel[1], vel[2], *table, track_crossings=False)
+    del cols, vel
+    env = FempicEnv.from_mesh(wl.mesh, precision=1)
+    counts = (env.n_nodes, env.n_edges, env.n_faces, env.n_tets)
+    env.locate(st0)
+    sc = st0.empty_like()
+    env.sort(st0, sc)
+    del sc
+    e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+    b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    S, Ab = A.state_nbytes(st0), n * (3 * 8 + 3 * 4)
+    plan = A.plan_window(n, steps, S, Ab, int(0.85 * free))
+    A.kinetic_energy_and_grad(env, st0, e, b, A.Schedule(wl.amp, wl.omega0, wl.dt, 2, 1))   # warm-up
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    sch = A.Schedule(wl.amp, wl.omega0, wl.dt, steps, plan.every, stash=plan.stash)
+    env.profile(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    final, ckpts = A.forward_checkpointed(env, st0, e, b, sch)
+    ev[1].record()
+    adj = A.AdjointState(n, torch.float32)
+    A.kinetic_energy(env, final, seed=adj)
+    del final
+    A.reverse_sweep(env, ckpts, e, b, sch, adj)
+    ev[2].record()
+    torch.cuda.synchronize()
+    prof = env.profile_read()
+    env.profile(False)
+    peak_meas = torch.cuda.max_memory_allocated() - base
+    t_fwd, t_rev = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+    hbm = measured_peaks()[0]
+    fb = bytes_alg_per_step(n, counts, "mixed")
+    rb = bytes_reverse_window(n, counts, "mixed", steps, plan.every, plan.stash, plan.recompute_steps)
+    out = {"workload": WORKLOAD_DESC["large96"] + f" (particles drawn on the device); loss = kinetic energy "
+                       f"after K={steps} steps",
+           "form": "mixed", "unit": "particle-steps/s", "particles": n, "steps": steps,
+           "forward_particle_steps_per_s": n * steps / t_fwd,
+           "reverse_particle_steps_per_s": n * steps / t_rev,
+           "gradient_window_s": t_fwd + t_rev,
+           "hbm_frac_forward": fb * steps / t_fwd / 1e9 / hbm,
+           "hbm_frac_reverse": rb / t_rev / 1e9 / hbm,
+           "bytes_per_particle_step_forward": fb / n,
+           "bytes_per_particle_step_reverse": rb / (n * steps),
+           "memory_plan": {"every": plan.every, "stash": plan.stash, "recompute_steps": plan.recompute_steps,
+                           "budget_gb": 0.85 * free / 1e9, "predicted_peak_gb": plan.peak_bytes / 1e9,
+                           "measured_peak_gb": peak_meas / 1e9, "state_gb": S / 1e9, "adjoint_gb": Ab / 1e9},
+           "kernel_ms": {k: v["ms"] for k, v in prof.items() if v["launches"]}}
+    env.close()
+    del st0, ckpts, adj
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(wl, n_sample, steps):
@@ -851,17 +951,16 @@ def report(args, world, n_p, out, cpu, adj=None):
         rec["downshift"] = out["downshift"]
     if adj is not None:
         # HBM fractions of the gradient window: forward steps on the forward
-        # algorithmic bytes, reverse steps on 232 B per particle-step (forward
-        # recompute, stash and reload of the segment's states, adjoint state
-        # read and written) plus the DoF-gradient terms
-        nn, ne, nf, nt = adj.get("counts", (0, 0, 0, 0))
+        # algorithmic bytes, the reverse sweep on bytes_reverse_window
+        counts = adj.get("counts", (0, 0, 0, 0))
         n_adj = adj.get("particles", 0)
         for form in ("mixed", "fp64"):
             r = adj.get(form)
             if not r or not n_adj:
                 continue
-            fb = bytes_alg_per_step(n_adj, (nn, ne, nf, nt), form) / n_adj
-            rb = (232 if form == "mixed" else 2 * 2 * 52 + 2 * 48) + (8 * (ne + nf)) / n_adj
+            K = adj["steps"]
+            fb = bytes_alg_per_step(n_adj, counts, form) / n_adj
+            rb = bytes_reverse_window(n_adj, counts, form, K, adj["every"], True, K) / (n_adj * K)
             r["bytes_per_particle_step_forward"] = fb
             r["bytes_per_particle_step_reverse"] = rb
             r["hbm_frac_forward"] = r["forward_particle_steps_per_s"] * fb / 1e9 / peak
@@ -871,6 +970,8 @@ def report(args, world, n_p, out, cpu, adj=None):
         rec["mixed_error_vs_oracle"] = out["errors"]
     if "large" in out:
         rec["large_forward"] = out["large"]
+    if "large_adjoint" in out:
+        rec["large_adjoint"] = out["large_adjoint"]
     if out.get("fp64_rate"):
         rec["fp64_rate_lane_ops_per_s"] = out["fp64_rate"]
     if cpu is not None:

@@ -8,7 +8,9 @@ schedules them: a forward pass that keeps a checkpoint of the particle state
 every `every` steps, then a reverse sweep that, segment by segment from the
 last, recomputes the segment's states from its checkpoint and runs the adjoint
 steps backwards.  Memory: one state per checkpoint plus `every` + 1 states for
-the segment being reversed.
+the segment being reversed, or 2 when the schedule does not stash (each
+step's states are then recomputed from the checkpoint); `plan_window` picks
+the interval and the mode for a memory budget.
 
 Each checkpoint is taken after sorting the state by (species, tet)
 (`fempic_sort_perm`), so the steps of every segment run on tet-ordered
@@ -71,6 +73,13 @@ def clone_state(st: ParticleState) -> ParticleState:
     return o
 
 
+def _copy_state(dst: ParticleState, src: ParticleState):
+    for k in ("x", "y", "z", "vx", "vy", "vz", "tet", "status", "n_cross"):
+        t = getattr(src, k)
+        if t is not None:
+            getattr(dst, k).copy_(t)
+
+
 def kinetic_energy(env: FempicEnv, st: ParticleState, seed: AdjointState | None = None, stream=None):
     """Total kinetic energy (device f64 scalar); fills `seed` with its adjoint."""
     ke = torch.empty((), dtype=torch.float64, device=st.x.device)
@@ -88,6 +97,50 @@ class Schedule:
     steps: int
     every: int = 10        # checkpoint interval
     t0: float = 0.0
+    stash: bool = True     # keep a segment's recomputed states (else recompute each step's from the checkpoint)
+
+
+def state_nbytes(st: ParticleState) -> int:
+    """Device bytes of one particle state."""
+    return sum(t.numel() * t.element_size() for t in (st.x, st.y, st.z, st.vx, st.vy, st.vz, st.tet, st.status,
+                                                       st.n_cross) if t is not None)
+
+
+@dataclasses.dataclass
+class WindowPlan:
+    every: int
+    stash: bool
+    peak_bytes: int        # checkpoints + working states + adjoint states (the caller's st0 not counted)
+    recompute_steps: int   # forward steps the reverse sweep re-runs
+
+
+def plan_window(n: int, steps: int, state_bytes: int, adj_bytes: int, budget_bytes: int) -> WindowPlan:
+    """Checkpoint interval and reverse mode of a gradient window that fits in
+    budget_bytes of device memory with the fewest recomputed steps (ties: the
+    smaller peak).  Peak: ceil(K/every) checkpoints (a state and its sort
+    permutation each), then in the reverse sweep either every + 1 stashed
+    states of the segment (stash) or 2 (each step's pair recomputed from the
+    checkpoint, every (every + 1) / 2 steps per segment), and the adjoint
+    state with its spare for the checkpoint unpermutes.  Raises
+    MemoryError when even the leanest plan does not fit."""
+    perm = 4 * n
+    best = None
+    for every in range(1, max(steps, 1) + 1):
+        nck = -(-steps // every)
+        segs = [min(every, steps - s * every) for s in range(nck)]
+        for stash in (True, False):
+            work = (every + 1) if stash else 2
+            peak = nck * (state_bytes + perm) + work * state_bytes + 2 * adj_bytes
+            rec = steps if stash else sum(L * (L + 1) // 2 for L in segs)
+            if peak > budget_bytes:
+                continue
+            key = (rec, peak)
+            if best is None or key < (best.recompute_steps, best.peak_bytes):
+                best = WindowPlan(every, stash, peak, rec)
+    if best is None:
+        raise MemoryError(f"no checkpoint plan of a {steps}-step window over {n} particles fits "
+                          f"{budget_bytes / 1e9:.1f} GB")
+    return best
 
 
 class _DepositOff:
@@ -183,19 +236,34 @@ def reverse_sweep(env: FempicEnv, ckpts, e, b, sch: Schedule, adj: AdjointState,
     for s in range(len(ckpts) - 1, -1, -1):
         k0 = s * sch.every
         k1 = min(sch.steps, k0 + sch.every)
-        stash = [ckpts[s].st]
-        cur = clone_state(ckpts[s].st)
-        with _DepositOff(env):
-            for k in range(k0, k1):
-                _step(env, cur, e, b, sch, k)
-                stash.append(clone_state(cur))
-        for k in range(k1 - 1, k0 - 1, -1):
-            j = k - k0
+
+        def adjoint_step(k, before, after):
             t = sch.t0 + k * sch.dt
             envl = capi.fempic_envelope(_ptr(e), _ptr(b), float(sch.amp(t)))
-            capi.fempic_push_step_adjoint(env.h, stash[j].cstruct(), stash[j + 1].cstruct(), envl, sch.omega0, t,
+            capi.fempic_push_step_adjoint(env.h, before.cstruct(), after.cstruct(), envl, sch.omega0, t,
                                           sch.dt, adj.cstruct(), _ptr(eg), _ptr(bg), stream)
-        del stash, cur
+
+        if sch.stash:
+            stash = [ckpts[s].st]
+            cur = clone_state(ckpts[s].st)
+            with _DepositOff(env):
+                for k in range(k0, k1):
+                    _step(env, cur, e, b, sch, k)
+                    stash.append(clone_state(cur))
+            for k in range(k1 - 1, k0 - 1, -1):
+                adjoint_step(k, stash[k - k0], stash[k - k0 + 1])
+            del stash, cur
+        else:   # two working states: each step's (before, after) pair recomputed from the checkpoint
+            before, after = clone_state(ckpts[s].st), clone_state(ckpts[s].st)
+            for k in range(k1 - 1, k0 - 1, -1):
+                _copy_state(before, ckpts[s].st)
+                with _DepositOff(env):
+                    for j in range(k0, k):
+                        _step(env, before, e, b, sch, j)
+                    _copy_state(after, before)
+                    _step(env, after, e, b, sch, k)
+                adjoint_step(k, before, after)
+            del before, after
         if ckpts[s].perm is not None:   # back to the order before this checkpoint's sort
             if spare is None:
                 spare = AdjointState(adj.n, adj.vx.dtype, device=adj.rx.device)
@@ -216,6 +284,7 @@ def kinetic_energy_and_grad(env: FempicEnv, st0: ParticleState, e, b, sch: Sched
     vdt = torch.float64 if env.precision == FEMPIC_FP64 else torch.float32
     adj = AdjointState(st0.n, vdt, device=st0.x.device)
     L = kinetic_energy(env, final, seed=adj)
+    del final   # the reverse sweep needs the checkpoints only
     if group is not None:
         from .shard import allreduce_
         allreduce_(L.view(1), group)
@@ -248,6 +317,7 @@ def current_loss_and_grad(env: FempicEnv, st0: ParticleState, e, b, sch: Schedul
     the whole sharded load."""
     u = u.to(torch.float64).contiguous()
     final, ckpts, L = _forward(env, st0, e, b, sch, sort, u=u)
+    del final
     vdt = torch.float64 if env.precision == FEMPIC_FP64 else torch.float32
     adj = AdjointState(st0.n, vdt, device=st0.x.device)   # the final state does not enter L
     if group is not None:

@@ -102,7 +102,8 @@ def test_step_fraction_variant_and_reports_are_carried(monkeypatch):
     out["errors"] = {"mixed": {"tet_agreement": 1.0}}
     out["large"] = {"jittered64": {"value": 7e9}, "large96": {"value": 1.4e10}}
     out["fp64_rate"] = 5.3e11
-    adj = {"particles": 4_000_000, "counts": (117649, 795024, 1340928, 663552),
+    out["large_adjoint"] = {"memory_plan": {"every": 5, "stash": True}}
+    adj = {"particles": 4_000_000, "counts": (117649, 795024, 1340928, 663552), "steps": 50, "every": 10,
            "mixed": {"forward_particle_steps_per_s": 1.5e10, "reverse_particle_steps_per_s": 6e9}}
     buf = io.StringIO()
     with redirect_stdout(buf):
@@ -117,3 +118,20 @@ def test_step_fraction_variant_and_reports_are_carried(monkeypatch):
     assert a["hbm_frac_reverse"] == pytest.approx(6e9 * a["bytes_per_particle_step_reverse"] / 1e9 /
                                                   d["roofline"]["peak"])
     assert a["bytes_per_particle_step_reverse"] > 232
+    assert d["large_adjoint"] == out["large_adjoint"]
+
+
+def test_reverse_window_bytes_count_each_pass():
+    """bytes_reverse_window: a stash-mode sweep is the recomputed steps plus
+    one state copy per step plus the adjoint-step and segment terms; the
+    recompute mode swaps the stash copies for two copies per step and adds
+    the extra recomputed steps."""
+    counts = (117649, 795024, 1340928, 663552)
+    n, K = 4_000_000, 20
+    fwd = bench.bytes_alg_per_step(n, counts, "mixed")
+    st = bench.bytes_reverse_window(n, counts, "mixed", K, 5, True, K)
+    rc = bench.bytes_reverse_window(n, counts, "mixed", K, 5, False, 60)
+    assert rc - st == pytest.approx(40 * fwd + K * n * 2 * 41)
+    adj_step = n * (40 + 13 + 72)
+    per_step_mesh = 72 * 663552 + 320 * 663552 + 32 * (795024 + 1340928)
+    assert st == K * fwd + K * n * 82 + K * (adj_step + per_step_mesh) + 4 * n * (82 + 72 + 4)

@@ -226,6 +226,33 @@ def test_gradient_with_checkpoint_sorts_equals_unsorted(prec, tol):
     np.testing.assert_allclose(r1, r0, rtol=0, atol=tol * np.abs(r0).max())
 
 
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-13), (MIXED, 2e-6)])
+def test_recompute_mode_equals_stash_mode(prec, tol):
+    """The reverse sweep without a stash (each step's states recomputed from
+    the checkpoint) runs the same adjoint steps on the same states: the
+    particle adjoints are identical and the DoF gradients agree up to the
+    atomics' summation order (FP32 per-tet sums in the mixed form)."""
+    A, FempicEnv, ParticleState = _mods()
+    wl = I.workload_hot_small(n_particles=400)
+    env = FempicEnv.from_mesh(wl.mesh, precision=prec)
+    st0 = ParticleState.from_host(wl.particles, prec, track_crossings=False)
+    env.locate(st0)
+    e = torch.from_numpy(wl.e_tilde).to(env.dof_dtype).cuda()
+    b = torch.from_numpy(wl.b_tilde).to(env.dof_dtype).cuda()
+    res = []
+    for stash in (True, False):
+        sch = A.Schedule(wl.amp, wl.omega0, wl.dt, 10, 4, stash=stash)
+        L, eg, bg, adj = A.kinetic_energy_and_grad(env, st0, e, b, sch)
+        torch.cuda.synchronize()
+        res.append((float(L.item()), eg.cpu().numpy(), bg.cpu().numpy(), adj))
+    (L0, e0, b0, a0), (L1, e1, b1, a1) = res
+    assert abs(L1 - L0) <= 1e-14 * abs(L0)
+    for k in ("rx", "ry", "rz", "vx", "vy", "vz"):
+        assert torch.equal(getattr(a0, k), getattr(a1, k)), k
+    np.testing.assert_allclose(e1, e0, rtol=0, atol=tol * np.abs(e0).max())
+    np.testing.assert_allclose(b1, b0, rtol=0, atol=tol * np.abs(b0).max())
+
+
 # ------------------------------------------------ element-by-element gradients
 def _dof_jvp_chunk(job):
     """Oracle worker (spawned process): <grad L, unit direction> for a chunk
