@@ -3799,50 +3799,43 @@ extern "C" int fempic_profile_read(fempic_env* env, double* ms_out, int64_t* cal
   return FEMPIC_OK;
 }
 
-static int sort_impl(fempic_env* env, const fempic_particles* in, const fempic_particles* out, int32_t* perm,
-                     void* stream) {
-  if (!env || !in || !out) return fail(FEMPIC_EINVAL, "sort: NULL argument");
+// Checks shared by the sort entry points: the two particle sets agree in
+// size, species table and n_cross, do not overlap, and the key and particle
+// counts fit 32-bit counters.  Sets *keys = n_species * (n_tets + 1).
+static int sort_check(const char* name, fempic_env* env, const fempic_particles* in, const fempic_particles* out,
+                      int64_t* keys) {
+  const std::string nm(name);
+  if (!env || !in || !out) return fail(FEMPIC_EINVAL, nm + ": NULL argument");
   int rc = check_particles(in, true);
   if (rc) return rc;
   rc = check_particles(out, true);
   if (rc) return rc;
   if (in->n != out->n || in->n_species != out->n_species || (!in->n_cross) != (!out->n_cross))
-    return fail(FEMPIC_EINVAL, "sort: in/out particle sets differ in size, species or n_cross");
-  if (in->n == 0) return FEMPIC_OK;
-  if (in->x == out->x || in->tet == out->tet) return fail(FEMPIC_EINVAL, "sort: in and out overlap");
-  SortArgs A{};
-  rc = fill_species(in, 1.0, &A.sp);
-  if (rc) return rc;
+    return fail(FEMPIC_EINVAL, nm + ": in/out particle sets differ in size, species or n_cross");
   for (int s = 0; s <= in->n_species; s++)
-    if (in->species_begin[s] != out->species_begin[s]) return fail(FEMPIC_EINVAL, "sort: species tables differ");
-  cudaStream_t st = (cudaStream_t)stream;
+    if (in->species_begin[s] != out->species_begin[s]) return fail(FEMPIC_EINVAL, nm + ": species tables differ");
+  if (in->n > 0 && (in->x == out->x || in->tet == out->tet)) return fail(FEMPIC_EINVAL, nm + ": in and out overlap");
+  *keys = (int64_t)in->n_species * (env->h.nt + 1);
+  if (*keys >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, nm + ": too many (species, tet) keys");
+  if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, nm + ": more than 2^31 particles");
+  return FEMPIC_OK;
+}
+
+// The counting sort by (species, tet) on caller-given scratch: counts and
+// offsets [keys], sums [keys / (2 kScan) + 1].  Stream-ordered.
+static int sort_launch(fempic_env* env, const fempic_particles* in, const fempic_particles* out, int32_t* perm,
+                       int64_t k, int32_t* counts, int32_t* offsets, int32_t* sums, cudaStream_t st) {
+  SortArgs A{};
+  int rc = fill_species(in, 1.0, &A.sp);
+  if (rc) return rc;
   const int64_t nt = env->h.nt;
-  const int64_t k = (int64_t)in->n_species * (nt + 1);
-  if (k >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "sort: too many (species, tet) keys");
-  if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "sort: more than 2^31 particles");
-  if (env->sort_cap < k) {
-    if (env->sort_counts) {
-      FEMPIC_CUDA(cudaStreamSynchronize(st));
-      cudaFree(env->sort_counts);
-      cudaFree(env->sort_offsets);
-      cudaFree(env->sort_sums);
-      env->sort_counts = env->sort_offsets = env->sort_sums = nullptr;
-      env->sort_cap = 0;
-    }
-    FEMPIC_CUDA(dalloc(&env->sort_counts, k));
-    FEMPIC_CUDA(dalloc(&env->sort_offsets, k));
-    FEMPIC_CUDA(dalloc(&env->sort_sums, k / (2 * kScan) + 1));
-    env->sort_cap = k;
-  }
   const int64_t tiles = (k + 2 * kScan - 1) / (2 * kScan);
-  LaunchTimer lt(env, st, FEMPIC_K_SORT);
-  lt.kernels = 5;   // histogram, three scan passes, scatter
-  FEMPIC_CUDA(cudaMemsetAsync(env->sort_counts, 0, k * sizeof(int32_t), st));
-  k_sort_hist<<<blocks_for(in->n), kThreads, 0, st>>>(in->n, in->tet, A.sp, nt, env->sort_counts);
-  k_scan_tiles<<<(unsigned)tiles, kScan, 0, st>>>(k, env->sort_counts, env->sort_offsets, env->sort_sums);
-  k_scan_sums<<<1, kScan, 0, st>>>(tiles, env->sort_sums);
-  k_scan_add<<<blocks_for(k), kThreads, 0, st>>>(k, env->sort_offsets, env->sort_sums);
-  FEMPIC_CUDA(cudaMemsetAsync(env->sort_counts, 0, k * sizeof(int32_t), st));
+  FEMPIC_CUDA(cudaMemsetAsync(counts, 0, k * sizeof(int32_t), st));
+  k_sort_hist<<<blocks_for(in->n), kThreads, 0, st>>>(in->n, in->tet, A.sp, nt, counts);
+  k_scan_tiles<<<(unsigned)tiles, kScan, 0, st>>>(k, counts, offsets, sums);
+  k_scan_sums<<<1, kScan, 0, st>>>(tiles, sums);
+  k_scan_add<<<blocks_for(k), kThreads, 0, st>>>(k, offsets, sums);
+  FEMPIC_CUDA(cudaMemsetAsync(counts, 0, k * sizeof(int32_t), st));
   A.n = in->n;
   A.nt = nt;
   A.vbytes = env->opt.precision == FEMPIC_FP64 ? 8 : 4;
@@ -3864,12 +3857,37 @@ static int sort_impl(fempic_env* env, const fempic_particles* in, const fempic_p
   A.otet = out->tet;
   A.ostatus = out->status;
   A.oncross = out->n_cross;
-  A.offsets = env->sort_offsets;
-  A.cursor = env->sort_counts;
+  A.offsets = offsets;
+  A.cursor = counts;
   A.operm = perm;
   k_sort_scatter<<<blocks_for(in->n), kThreads, 0, st>>>(A);
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
+}
+
+static int sort_impl(fempic_env* env, const fempic_particles* in, const fempic_particles* out, int32_t* perm,
+                     void* stream) {
+  int64_t k = 0;
+  int rc = sort_check("sort", env, in, out, &k);
+  if (rc || in->n == 0) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (env->sort_cap < k) {
+    if (env->sort_counts) {
+      FEMPIC_CUDA(cudaStreamSynchronize(st));
+      cudaFree(env->sort_counts);
+      cudaFree(env->sort_offsets);
+      cudaFree(env->sort_sums);
+      env->sort_counts = env->sort_offsets = env->sort_sums = nullptr;
+      env->sort_cap = 0;
+    }
+    FEMPIC_CUDA(dalloc(&env->sort_counts, k));
+    FEMPIC_CUDA(dalloc(&env->sort_offsets, k));
+    FEMPIC_CUDA(dalloc(&env->sort_sums, k / (2 * kScan) + 1));
+    env->sort_cap = k;
+  }
+  LaunchTimer lt(env, st, FEMPIC_K_SORT);
+  lt.kernels = 5;   // histogram, three scan passes, scatter
+  return sort_launch(env, in, out, perm, k, env->sort_counts, env->sort_offsets, env->sort_sums, st);
 }
 
 extern "C" int fempic_sort(fempic_env* env, const fempic_particles* in, const fempic_particles* out, void* stream) {
@@ -3948,68 +3966,18 @@ int noalloc_scratch(int32_t** out) {
 
 extern "C" int fempic_sort_noalloc(fempic_env* env, const fempic_particles* in, const fempic_particles* out,
                                    void* stream) {
-  if (!env || !in || !out) return fail(FEMPIC_EINVAL, "sort_noalloc: NULL argument");
-  int rc = check_particles(in, true);
-  if (rc) return rc;
-  rc = check_particles(out, true);
-  if (rc) return rc;
-  if (in->n != out->n || in->n_species != out->n_species || (!in->n_cross) != (!out->n_cross))
-    return fail(FEMPIC_EINVAL, "sort_noalloc: in/out particle sets differ in size, species or n_cross");
-  if (in->n == 0) return FEMPIC_OK;
-  if (in->x == out->x || in->tet == out->tet) return fail(FEMPIC_EINVAL, "sort_noalloc: in and out overlap");
-  SortArgs A{};
-  rc = fill_species(in, 1.0, &A.sp);
-  if (rc) return rc;
-  for (int s = 0; s <= in->n_species; s++)
-    if (in->species_begin[s] != out->species_begin[s])
-      return fail(FEMPIC_EINVAL, "sort_noalloc: species tables differ");
-  const int64_t nt = env->h.nt;
-  const int64_t k = (int64_t)in->n_species * (nt + 1);
+  int64_t k = 0;
+  int rc = sort_check("sort_noalloc", env, in, out, &k);
+  if (rc || in->n == 0) return rc;
   if (k > kNoAllocKeys)
     return fail(FEMPIC_EINVAL, "sort_noalloc: n_species * (n_tets + 1) = " + std::to_string(k) +
                                    " exceeds the fixed scratch of " + std::to_string(kNoAllocKeys) +
                                    " keys; use fempic_sort");
-  if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "sort_noalloc: more than 2^31 particles");
   int32_t* base = nullptr;
   rc = noalloc_scratch(&base);
   if (rc) return rc;
-  int32_t* counts = base;
-  int32_t* offsets = base + kNoAllocKeys;
-  int32_t* sums = base + 2 * kNoAllocKeys;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int64_t tiles = (k + 2 * kScan - 1) / (2 * kScan);
-  FEMPIC_CUDA(cudaMemsetAsync(counts, 0, k * sizeof(int32_t), st));
-  k_sort_hist<<<blocks_for(in->n), kThreads, 0, st>>>(in->n, in->tet, A.sp, nt, counts);
-  k_scan_tiles<<<(unsigned)tiles, kScan, 0, st>>>(k, counts, offsets, sums);
-  k_scan_sums<<<1, kScan, 0, st>>>(tiles, sums);
-  k_scan_add<<<blocks_for(k), kThreads, 0, st>>>(k, offsets, sums);
-  FEMPIC_CUDA(cudaMemsetAsync(counts, 0, k * sizeof(int32_t), st));
-  A.n = in->n;
-  A.nt = nt;
-  A.vbytes = env->opt.precision == FEMPIC_FP64 ? 8 : 4;
-  A.x = in->x;
-  A.y = in->y;
-  A.z = in->z;
-  A.vx = in->vx;
-  A.vy = in->vy;
-  A.vz = in->vz;
-  A.tet = in->tet;
-  A.status = in->status;
-  A.ncross = in->n_cross;
-  A.ox = out->x;
-  A.oy = out->y;
-  A.oz = out->z;
-  A.ovx = out->vx;
-  A.ovy = out->vy;
-  A.ovz = out->vz;
-  A.otet = out->tet;
-  A.ostatus = out->status;
-  A.oncross = out->n_cross;
-  A.offsets = offsets;
-  A.cursor = counts;
-  k_sort_scatter<<<blocks_for(in->n), kThreads, 0, st>>>(A);
-  FEMPIC_CUDA(cudaGetLastError());
-  return FEMPIC_OK;
+  return sort_launch(env, in, out, nullptr, k, base, base + kNoAllocKeys, base + 2 * kNoAllocKeys,
+                     (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------ adjoint ABI
