@@ -68,6 +68,7 @@ struct Species {
   int64_t begin[kMaxSpecies + 1];
   double kq[kMaxSpecies];   // (q/m) dt / 2
   double qw[kMaxSpecies];   // q w
+  float kq32[kMaxSpecies];  // kq rounded to FP32 (the mixed push's coefficient)
 };
 
 // Record of a particle that leaves its home tet: written by the common path
@@ -102,6 +103,7 @@ struct PushArgs {
   int32_t* ncross;
   Species sp;
   double dt;
+  float dt32;                   // dt rounded to FP32 (the mixed position update's step)
   int32_t max_cross;
   int32_t wall_mode;
   double lo[3], hi[3];
@@ -898,26 +900,24 @@ __device__ __forceinline__ DF f64_to_df(double r) {
 // like the 24-bit form's integers, and the run head adds the sums, as FP64,
 // to the tet's moment slot with FP64 atomics.
 
-// x / 2^(emax - 177) as an integer, rounded half away from zero, with emax
-// the biased exponent of the warp's largest |x| (bias = 27 - emax): |result|
-// < 2^51, so 32 lanes sum below 2^56.  32-bit operations only: the 24-bit
-// significand is shifted left into a word pair, or rounded right.
-__device__ __forceinline__ long long fx_scaled(float x, int bias) {
-  const unsigned u = __float_as_uint(x);
-  const int ex = (int)((u >> 23) & 0xffu);
-  const unsigned m = (u & 0x7fffffu) | 0x800000u;
-  const int sh = ex + bias;   // <= 27
-  unsigned lo, hi = 0u;
-  if (sh >= 0) {
-    lo = m << sh;
-    hi = __funnelshift_l(m, 0u, (unsigned)sh);
-  } else {
-    const unsigned r = (unsigned)min(-sh, 31);
-    lo = (m + (1u << (r - 1u))) >> r;
-  }
-  if (ex == 0) lo = hi = 0u;   // zero or below 2^-126
-  const long long v = (long long)(((unsigned long long)hi << 32) | lo);
-  return (u >> 31) ? -v : v;
+// Per-warp fixed point, as two 32-bit limbs: with y = x s (s a power of two,
+// so the product is exact) the integer X = round(y 2^25) is held as hi 2^25
+// + lo, hi = floor(y) and lo = round((y - hi) 2^25) in [0, 2^25].  With |y| <
+// 2^25 for the warp's largest |x| (fx_scale), |X| < 2^50, and the sums of a
+// warp's limbs stay below 2^31 in magnitude.  Float operations only: the
+// floor and the two 32-bit conversions.
+__device__ __forceinline__ void fx_limbs(float x, float scale, int& hi, unsigned& lo) {
+  const float y = __fmul_rn(x, scale);
+  const float h = floorf(y);
+  hi = __float2int_rn(h);
+  lo = __float2uint_rn(__fmul_rn(__fsub_rn(y, h), 33554432.0f));   // exact before the rounding
+}
+
+// s = 2^(151 - emax) for a warp whose largest |x| has biased exponent emax
+// (|x| < 2^(emax - 126)), so |y| < 2^25 and X = x 2^(176 - emax).  0 when
+// emax < 24 (every |x| below 2^-103, the values are dropped).
+__device__ __forceinline__ float fx_scale(unsigned emax) {
+  return emax < 24u ? 0.f : __uint_as_float((278u - emax) << 23);
 }
 
 // v 2^e2 as a double, rounded to nearest (ties up), with integer operations
@@ -944,6 +944,8 @@ __device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x
 struct LaneOut {
   long long gh[6];     // 24-bit form: one-segment deposit (home tet), int64
   float mv[9];         // contract form: D (3), u x D as pairs (hi 3, lo 3)
+  int lh[6];           // the six values as 32-bit limbs (hi 2^25 + lo), for the run sums
+  unsigned ll[6];
   int32_t key;         // (home tet, species) run key; negative = no deposit
   int32_t Thome;
   int shome;
@@ -956,6 +958,7 @@ struct LaneOut {
 
 struct CrossList {
   int32_t total;     // records of the current tile
+  long long sums[kThreads / 32][32 * 6];   // per warp: run sums of the deposit, by head lane
 };
 
 __device__ __forceinline__ void lane_init(LaneOut& o, int lane) {
@@ -991,7 +994,7 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   }
   if (T < 0) return;
   const int s = species_of(A.sp, p);
-  const float kq = (float)A.sp.kq[s];
+  const float kq = A.sp.kq32[s];
   const float4* R = A.tetrec + 8 * (int64_t)T;
   const Geo32 G = ld_geo(A.tetrec, T);
   const float4 f0 = __ldg(R + 4), f1 = __ldg(R + 5), f2 = __ldg(R + 6);
@@ -1014,7 +1017,7 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
   const float vn0 = vmx + (vpy * sz - vpz * sy) + kq * Ex;
   const float vn1 = vmy + (vpz * sx - vpx * sz) + kq * Ey;
   const float vn2 = vmz + (vpx * sy - vpy * sx) + kq * Ez;
-  const float dt32 = (float)A.dt;
+  const float dt32 = A.dt32;
   // the FP32 displacement and the FP64 position update (advance's sequence)
   const float D0 = __fmul_rn(dt32, vn0), D1 = __fmul_rn(dt32, vn1), D2 = __fmul_rn(dt32, vn2);
   const double b0 = __dadd_rn(ax, f32_to_f64(D0)), b1 = __dadd_rn(ay, f32_to_f64(D1)),
@@ -1117,7 +1120,7 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
   if (dep_on) {   // deposits on (kernel parameter: the same branch for every lane)
     unsigned eD = 0u, eM = 0u;
     if (!Q24) {
-      // the warp's quanta, then every lane's values as integers
+      // the warp's quanta, then every lane's values as limbs
       unsigned uD = 0u, uM = 0u;
       if (o.key >= 0) {
         uD = max(max(abs_bits(o.mv[0]), abs_bits(o.mv[1])), abs_bits(o.mv[2]));
@@ -1125,41 +1128,71 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
       }
       eD = __reduce_max_sync(full, uD) >> 23;
       eM = __reduce_max_sync(full, uM) >> 23;
-      const int bD = 27 - (int)eD, bM = 27 - (int)eM;
+      const float sD = fx_scale(eD), sM = fx_scale(eM);
 #pragma unroll
       for (int k = 0; k < 3; k++) {
-        o.gh[k] = fx_scaled(o.mv[k], bD);
-        o.gh[3 + k] = fx_scaled(o.mv[3 + k], bM) + fx_scaled(o.mv[6 + k], bM);
+        fx_limbs(o.mv[k], sD, o.lh[k], o.ll[k]);
+        int h2;
+        unsigned l2;
+        fx_limbs(o.mv[3 + k], sM, o.lh[3 + k], o.ll[3 + k]);
+        fx_limbs(o.mv[6 + k], sM, h2, l2);
+        o.lh[3 + k] += h2;
+        o.ll[3 + k] += l2;
       }
     }
+    // exact sums over runs of equal (tet, species) keys (particles are sorted
+    // by tet, so neighbouring lanes usually share one): a segmented
+    // shuffle-down scan, as many rounds as the warp's longest run needs,
+    // leaves each run's sums in its head lane
     const int32_t prev = __shfl_up_sync(full, o.key, 1);
     const bool head = lane == 0 || prev != o.key;
     const unsigned heads = __ballot_sync(full, head);
     const unsigned above = lane == 31 ? 0u : (heads & (~0u << (lane + 1)));
     const int run_end = above ? (__ffs(above) - 2) : 31;
-    // as many shuffle rounds as the warp's longest run needs
     const unsigned longest = __reduce_max_sync(full, head ? (unsigned)(run_end - lane + 1) : 0u);
 #pragma unroll 1
     for (int off = 1; off < (int)longest; off <<= 1) {
+      const bool in = lane + off <= run_end;
 #pragma unroll
       for (int e = 0; e < 6; e++) {
-        const long long v = __shfl_down_sync(full, o.gh[e], off);
-        if (lane + off <= run_end) o.gh[e] += v;
+        if (Q24) {
+          const long long v = __shfl_down_sync(full, o.gh[e], off);
+          if (in) o.gh[e] += v;
+        } else {
+          const int vh = __shfl_down_sync(full, o.lh[e], off);
+          const unsigned vl = __shfl_down_sync(full, o.ll[e], off);
+          if (in) {
+            o.lh[e] += vh;
+            o.ll[e] += vl;
+          }
+        }
       }
     }
+    // the run's lanes share its six slot updates: the head leaves the sums in
+    // the warp's scratch row, lane r of the run takes components r, r + len, ...
+    long long* row = cl.sums[threadIdx.x >> 5];
     if (head && o.key >= 0) {
-      if (Q24) {
-        unsigned long long* base = A.dGq + ((int64_t)o.shome * A.nt + o.Thome) * 8;
 #pragma unroll
-        for (int e = 0; e < 6; e++)
-          if (o.gh[e]) atomicAdd(base + e, (unsigned long long)o.gh[e]);
-      } else {
-        double* base = A.mom + ((int64_t)o.shome * A.nt + o.Thome) * 6;
-#pragma unroll
-        for (int e = 0; e < 6; e++)
-          if (o.gh[e]) atomicAdd(base + e, i64_to_f64(o.gh[e], (int)(e < 3 ? eD : eM) - 177));
+      for (int e = 0; e < 6; e++)
+        row[6 * (lane & 31) + e] = Q24 ? o.gh[e] : (long long)o.lh[e] * 33554432ll + (long long)o.ll[e];
+    }
+    __syncwarp();
+    if (o.key >= 0) {
+      const unsigned below = heads & (0xffffffffu >> (31 - lane));   // heads at or below this lane
+      const int start = 31 - __clz(below);
+      const int len = run_end - start + 1;
+#pragma unroll 1
+      for (int c = lane - start; c < 6; c += len) {
+        const long long v = row[6 * start + c];
+        if (v == 0) continue;
+        if (Q24)
+          atomicAdd(A.dGq + ((int64_t)o.shome * A.nt + o.Thome) * 8 + c, (unsigned long long)v);
+        else   // the run's X sum times 2^(emax - 176)
+          atomicAdd(A.mom + ((int64_t)o.shome * A.nt + o.Thome) * 6 + c,
+                    i64_to_f64(v, (int)(c < 3 ? eD : eM) - 176));
       }
     }
+    __syncwarp();
   }
   const unsigned nf = __reduce_add_sync(full, o.nfrz);
   if (lane == 0 && nf) atomicAdd(A.stats + 1, (unsigned long long)nf);
@@ -1284,7 +1317,7 @@ __device__ __forceinline__ void stage_tile(const PushArgs& A, unsigned char* sta
 #define FEMPIC_USE_TMA 1
 #endif
 #ifndef FEMPIC_TMA_MIN_BLOCKS
-#define FEMPIC_TMA_MIN_BLOCKS 3
+#define FEMPIC_TMA_MIN_BLOCKS 4
 #endif
 template <bool Q24>
 __global__ void __launch_bounds__(kThreads, FEMPIC_TMA_MIN_BLOCKS) k_push_mixed_tma(PushArgs A, int64_t ntiles) {
@@ -1372,7 +1405,7 @@ __device__ __forceinline__ void cross_begin(const PushArgs& A, const CrossRec& r
   c.p = r.p;
   c.T = r.T;
   c.s = species_of(A.sp, r.p);
-  const float dt32 = (float)A.dt;
+  const float dt32 = A.dt32;
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     c.a0[k] = r.a[k];
@@ -1647,8 +1680,8 @@ __device__ __forceinline__ void deposit_piece_df(const PushArgs& A, int s, int32
     e = __fmaf_rn(-u[j].h, w[i].lo, __fmaf_rn(-u[j].l, w[i].hi, e));
     const DF m = df_mul(dS, fast_two_sum(sd.h, e));
     const DF d = df_mul(dS, DF{w[k].hi, w[k].lo});
-    atomicAdd(ms + k, f32_to_f64(d.h));
-    atomicAdd(ms + 3 + k, f32_to_f64(m.h));
+    atomicAdd(ms + k, (double)d.h);   // exact widening (the FP64 pipe is idle here)
+    atomicAdd(ms + 3 + k, (double)m.h);
     lo[k] = d.l;
     lo[3 + k] = m.l;
   }
@@ -1661,12 +1694,12 @@ __device__ __forceinline__ void cross_begin_df(const PushArgs& A, const CrossRec
   c.p = r.p;
   c.T = r.T;
   c.s = species_of(A.sp, r.p);
-  const float dt32 = (float)A.dt;
+  const float dt32 = A.dt32;
 #pragma unroll
   for (int k = 0; k < 3; k++) {
     c.a0[k] = r.a[k];
-    c.b[k] = advance(r.a[k], dt32, r.v[k]);
     c.w[k] = FF{__fmul_rn(dt32, r.v[k]), 0.f};
+    c.b[k] = __dadd_rn(r.a[k], (double)c.w[k].hi);   // advance's value (the widening is exact)
   }
   c.flips = 0u;
   c.S = DF{0.f, 0.f};
@@ -1810,7 +1843,10 @@ __device__ __forceinline__ void cross_finish_df(const PushArgs& A, const CrossSt
 // Same record hand-out as k_cross_q24: one warp per tile region, each loop
 // iteration advances every busy lane by one piece, idle lanes take the
 // tile's next record.
-__global__ void __launch_bounds__(kThreads) k_cross_df(PushArgs A, int64_t ntiles) {
+#ifndef FEMPIC_CROSS_MIN_BLOCKS
+#define FEMPIC_CROSS_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(kThreads, FEMPIC_CROSS_MIN_BLOCKS) k_cross_df(PushArgs A, int64_t ntiles) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -3220,8 +3256,12 @@ static int fill_species(const fempic_particles* p, double dt, Species* sp) {
     if (!(p->m[s] > 0.0)) return fail(FEMPIC_EINVAL, "particles: mass must be > 0");
     sp->kq[s] = ((p->q[s] / p->m[s]) * dt) * 0.5;
     sp->qw[s] = p->q[s] * p->w[s];
+    sp->kq32[s] = (float)sp->kq[s];
   }
-  for (int s = p->n_species; s < kMaxSpecies; s++) sp->kq[s] = sp->qw[s] = 0.0;
+  for (int s = p->n_species; s < kMaxSpecies; s++) {
+    sp->kq[s] = sp->qw[s] = 0.0;
+    sp->kq32[s] = 0.f;
+  }
   return FEMPIC_OK;
 }
 
@@ -3404,6 +3444,7 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
   A.status = p->status;
   A.ncross = p->n_cross;
   A.dt = dt;
+  A.dt32 = (float)dt;
   A.max_cross = env->opt.max_crossings;
   A.wall_mode = env->opt.wall_mode;
   for (int a = 0; a < 3; a++) {
