@@ -922,7 +922,7 @@ def report(args, world, n_p, out, cpu, adj=None):
         "gpu_launches": launches,
         "kernel_ms": {k: v["ms"] for k, v in m["prof"].items() if v["launches"]},
         "kernel_ms_note": "summed CUDA-event time over the timed steps per library call; 'cross' "
-                          "(k_cross_mixed) is part of 'push'",
+                          "(k_cross_df, or k_cross_q24 in the 24-bit variant) is part of 'push'",
         "crossings_per_particle_step": m["stats"]["crossings"] / max(1, n_p * (K + args.warmup)),
         "clocks": m["clocks"],
     }

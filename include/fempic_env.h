@@ -54,6 +54,7 @@ extern "C" {
 #define FEMPIC_EMESH (-3)    /* degenerate (zero-volume) or non-conforming mesh */
 #define FEMPIC_ENOMEM (-4)   /* host or device allocation failed */
 #define FEMPIC_EINCOMPLETE (-5) /* a step did not finish all its particles (fempic_error_count) */
+#define FEMPIC_EBOUNDS (-6)  /* debug build: a mesh-table index was out of range (fempic_error_count) */
 
 /* ---- precision forms ---- */
 #define FEMPIC_FP64 0   /* every step in FP64; velocities f64, DoFs complex128 */
@@ -258,8 +259,9 @@ int fempic_stats(fempic_env* env, int64_t* out4, void* stream);
  * CTA of the staged mixed push gave up its bounded wait (about 1 s) for a
  * bulk copy: the particles of its remaining tiles were then not advanced and
  * their deposit is missing, so the step must be redone from a saved state.
- * fempic_stats keeps the cumulative counters.  Errors: EINVAL, ECUDA,
- * EINCOMPLETE. */
+ * In the debug build it returns FEMPIC_EBOUNDS when a mesh-table index out of
+ * range was skipped (fempic_debug_set_table).  fempic_stats keeps the
+ * cumulative counters.  Errors: EINVAL, ECUDA, EINCOMPLETE, EBOUNDS. */
 int fempic_error_count(fempic_env* env, int64_t* n_bad, void* stream);
 
 /* Test support for the bounded waits (no counterpart in the paper): in the
@@ -271,6 +273,22 @@ int fempic_error_count(fempic_env* env, int64_t* n_bad, void* stream);
  * FEMPIC_EINCOMPLETE: the give-up path runs without any device fault.
  * Host only.  Errors: EINVAL. */
 int fempic_debug_stall(fempic_env* env, int32_t cta, int64_t limit_ns);
+
+/* Debug build support (no counterpart in the paper).  The library's debug
+ * build, libfempic_env_debug.so (compiled with FEMPIC_BOUNDS_CHECK), checks
+ * every index read from a mesh table against its range before it addresses
+ * memory; a bad index is skipped (a DoF reads as zero, a deposit term is
+ * dropped, a walking particle freezes with status LOST) and counted, and the
+ * next fempic_error_count returns FEMPIC_EBOUNDS.  This call overwrites one
+ * entry of a device mesh table so that the checks can be exercised:
+ *   FEMPIC_TABLE_NEIGHBOUR  index = 4 tet + local face (the neighbour table
+ *                           and its copy in the tet record);
+ *   FEMPIC_TABLE_EDGE       index = 6 tet + local edge (the edge-id table).
+ * The release build refuses it (FEMPIC_EINVAL), so a corrupted table never
+ * meets unchecked loads.  Synchronous.  Errors: EINVAL, ECUDA. */
+#define FEMPIC_TABLE_NEIGHBOUR 0
+#define FEMPIC_TABLE_EDGE 1
+int fempic_debug_set_table(fempic_env* env, int32_t table, int64_t index, int32_t value);
 
 /* Deposited-current term of the loss for the adjoint steps (the paper has no
  * adjoint; this differentiates the per-segment deposit g_ij of Sec. II eq.

@@ -1,7 +1,10 @@
 """Build libfempic_env.so in-tree for sm_103a (nvcc + g++, no cmake).
 
 The CUDA translation units and the host mesh builder compile in parallel, then
-nvcc links the shared library next to this file.
+nvcc links the shared library next to this file.  The same sources compiled
+with FEMPIC_BOUNDS_CHECK give the debug build, libfempic_env_debug.so
+(every mesh-table index checked before it addresses memory), built
+alongside in the same parallel job set.
 """
 from __future__ import annotations
 
@@ -15,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfempic_env.so")
+DEBUG_LIB = os.path.join(HERE, "libfempic_env_debug.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES_CU = ["fempic_env.cu", "fempic_downshift.cu"]
@@ -31,9 +35,9 @@ def _nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(DEBUG_LIB)):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(DEBUG_LIB))
     srcs = [os.path.join(CSRC, s) for s in SOURCES_CU + SOURCES_CPP] + HEADERS
     return any(os.path.getmtime(s) > t for s in srcs)
 
@@ -46,18 +50,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC]
     host_flags = ["-fPIC", "-ffp-contract=off", "-fno-fast-math"]
-    jobs, objs = [], []
+    jobs, objs, dobjs = [], [], []
     for s in SOURCES_CU:
-        o = os.path.join(BUILD_DIR, s + ".o")
-        cmd = [nvcc, *ARCH, "-lineinfo", *common, "-Xcompiler", ",".join(host_flags), "-c",
-               os.path.join(CSRC, s), "-o", o]
-        jobs.append(cmd)
-        objs.append(o)
+        for flags, suffix, lst in (([], ".o", objs), (["-DFEMPIC_BOUNDS_CHECK"], ".debug.o", dobjs)):
+            o = os.path.join(BUILD_DIR, s + suffix)
+            cmd = [nvcc, *ARCH, "-lineinfo", *common, *flags, "-Xcompiler", ",".join(host_flags), "-c",
+                   os.path.join(CSRC, s), "-o", o]
+            jobs.append(cmd)
+            lst.append(o)
     for s in SOURCES_CPP:
         o = os.path.join(BUILD_DIR, s + ".o")
         cmd = ["g++", *common, *host_flags, "-c", os.path.join(CSRC, s), "-o", o]
         jobs.append(cmd)
         objs.append(o)
+        dobjs.append(o)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in jobs]
     for c, p in zip(jobs, procs):
         out, _ = p.communicate()
@@ -65,12 +71,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("build failed: " + " ".join(c) + "\n" + out.decode(errors="replace"))
         if verbose and out:
             sys.stdout.write(out.decode(errors="replace"))
-    tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-    if r.returncode != 0:
-        raise RuntimeError("link failed: " + " ".join(link) + "\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
+    for lib, ob in ((LIB, objs), (DEBUG_LIB, dobjs)):
+        tmp = lib + f".tmp{os.getpid()}"
+        link = [nvcc, *ARCH, "-shared", "-o", tmp, *ob]
+        r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        if r.returncode != 0:
+            raise RuntimeError("link failed: " + " ".join(link) + "\n" + r.stdout.decode(errors="replace"))
+        os.replace(tmp, lib)
     return LIB
 
 

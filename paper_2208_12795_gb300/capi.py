@@ -11,7 +11,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfempic_env.so")
+# FEMPIC_LIBRARY selects another build of the same library (the debug build,
+# libfempic_env_debug.so, in the tests of its bounds checks)
+LIB_PATH = os.environ.get("FEMPIC_LIBRARY") or os.path.join(HERE, "libfempic_env.so")
 
 FEMPIC_OK = 0
 FEMPIC_EINVAL = -1
@@ -19,6 +21,9 @@ FEMPIC_ECUDA = -2
 FEMPIC_EMESH = -3
 FEMPIC_ENOMEM = -4
 FEMPIC_EINCOMPLETE = -5
+FEMPIC_EBOUNDS = -6
+FEMPIC_TABLE_NEIGHBOUR = 0
+FEMPIC_TABLE_EDGE = 1
 FEMPIC_FP64 = 0
 FEMPIC_MIXED = 1
 FEMPIC_MIXED_Q24 = 2
@@ -30,7 +35,7 @@ FEMPIC_WALL_ABSORB = 1
 EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_push_step", "fempic_push_step3",
            "fempic_lagrange3",
            "fempic_deposit", "fempic_deposit_local", "fempic_accumulate", "fempic_reset_deposit", "fempic_set_deposit", "fempic_nodal_charge", "fempic_stats",
-           "fempic_error_count", "fempic_debug_stall", "fempic_adjoint_current_weights", "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
+           "fempic_error_count", "fempic_debug_stall", "fempic_debug_set_table", "fempic_adjoint_current_weights", "fempic_push_step_adjoint", "fempic_kinetic_energy", "fempic_sort", "fempic_sort_perm",
            "fempic_adjoint_unpermute", "fempic_sort_noalloc", "fempic_profile_enable", "fempic_profile_read",
            "fempic_measure_fp64_rate", "fempic_last_error", "fempic_env_destroy")
 # Every function declared in include/fempic_downshift.h.
@@ -115,6 +120,7 @@ def load(path: str = LIB_PATH):
         lib.fempic_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_error_count.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_debug_stall.argtypes = [C.c_void_p, C.c_int32, C.c_int64]
+        lib.fempic_debug_set_table.argtypes = [C.c_void_p, C.c_int32, C.c_int64, C.c_int32]
         lib.fempic_adjoint_current_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
         lib.fempic_push_step_adjoint.argtypes = [C.c_void_p, P(fempic_particles), P(fempic_particles),
                                                  P(fempic_envelope), C.c_double, C.c_double, C.c_double,
@@ -225,16 +231,25 @@ def fempic_stats(env, out4, stream=0):
 
 def fempic_error_count(env, stream=0) -> tuple:
     """(return code, particles frozen since the last call); the code is
-    FEMPIC_OK or FEMPIC_EINCOMPLETE (any other code raises)."""
+    FEMPIC_OK, FEMPIC_EINCOMPLETE or FEMPIC_EBOUNDS (any other code raises)."""
     n = C.c_int64(0)
     rc = load().fempic_error_count(env, C.byref(n), stream)
-    if rc not in (FEMPIC_OK, FEMPIC_EINCOMPLETE):
+    if rc not in (FEMPIC_OK, FEMPIC_EINCOMPLETE, FEMPIC_EBOUNDS):
         check(rc, "fempic_error_count")
     return rc, n.value
 
 
 def fempic_debug_stall(env, cta: int, limit_ns: int):
     check(load().fempic_debug_stall(env, int(cta), int(limit_ns)), "fempic_debug_stall")
+
+
+def fempic_debug_set_table(env, table: int, index: int, value: int) -> int:
+    """Return code of fempic_debug_set_table (FEMPIC_EINVAL from the release
+    build); other failures raise."""
+    rc = load().fempic_debug_set_table(env, int(table), int(index), int(value))
+    if rc not in (FEMPIC_OK, FEMPIC_EINVAL):
+        check(rc, "fempic_debug_set_table")
+    return rc
 
 
 def fempic_adjoint_current_weights(env, u, stream=0):

@@ -136,6 +136,28 @@ __device__ __forceinline__ int species_of(const Species& sp, int64_t p) {
   return s;
 }
 
+// ------------------------------------------------------ debug bounds checks
+// The library's debug build (compiled with FEMPIC_BOUNDS_CHECK) checks every
+// index read from a mesh table against its range before it addresses
+// memory: edge and face ids before a DoF load or a deposit, neighbour ids
+// before the walk moves into the neighbour, node ids before a charge is
+// assigned, adjacency slots before the edge pull reads them.  A bad index is
+// counted in stats[3] (fempic_error_count then returns FEMPIC_EBOUNDS) and
+// its access is skipped: a DoF reads as zero, a deposit term is dropped, a
+// walking particle freezes with status LOST.  Nothing traps.  The release
+// build compiles the checks out.
+#ifdef FEMPIC_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+__device__ __forceinline__ bool idx_in(int64_t i, int64_t n, unsigned long long* stats) {
+  if (!kBoundsCheck) return true;
+  if (i >= 0 && i < n) return true;
+  if (stats) atomicAdd(stats + 3, 1ull);
+  return false;
+}
+
 // ---------------------------------------------------------------- location
 // Barycentrics with the fixed FP64 operation order (no contraction), so that
 // point location reproduces exactly across implementations.
@@ -170,6 +192,8 @@ struct LocateArgs {
   int gd[3];
   double ginv[3];
   double lo[3];
+  int64_t nt;                 // bounds checks of the debug build
+  unsigned long long* stats;
 };
 
 __global__ void __launch_bounds__(kThreads) k_locate(LocateArgs A) {
@@ -185,6 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_locate(LocateArgs A) {
     const int64_t e = A.gstart[c + 1];
     for (int64_t i = A.gstart[c]; i < e; i++) {
       const int32_t t = A.gtet[i];
+      if (!idx_in(t, A.nt, A.stats)) continue;
       double lam[4];
       bary_exact(A.geom64 + 12 * (int64_t)t, rx, ry, rz, lam);
       if (lam[0] >= 0.0 && lam[1] >= 0.0 && lam[2] >= 0.0 && lam[3] >= 0.0) {
@@ -225,6 +250,8 @@ struct Levels {
   const C2* e[3];
   const C2* b[3];
   R cre[3], cim[3];
+  int64_t ne, nf;                 // DoF counts (bounds checks of the debug build)
+  unsigned long long* stats;
 };
 
 template <typename R, typename C2, int NL>
@@ -233,23 +260,29 @@ __device__ __forceinline__ void field_coeffs(const V3<R> g[4], const Levels<C2, 
   R eps[6], bet[4];
 #pragma unroll
   for (int e = 0; e < 6; e++) {
-    const C2 d = L.e[0][eid[e]];
-    R acc = L.cre[0] * d.x - L.cim[0] * d.y;
+    R acc = 0;
+    if (idx_in(eid[e], L.ne, L.stats)) {
+      const C2 d = L.e[0][eid[e]];
+      acc = L.cre[0] * d.x - L.cim[0] * d.y;
 #pragma unroll
-    for (int k = 1; k < NL; k++) {
-      const C2 dk = L.e[k][eid[e]];
-      acc += L.cre[k] * dk.x - L.cim[k] * dk.y;
+      for (int k = 1; k < NL; k++) {
+        const C2 dk = L.e[k][eid[e]];
+        acc += L.cre[k] * dk.x - L.cim[k] * dk.y;
+      }
     }
     eps[e] = acc;
   }
 #pragma unroll
   for (int f = 0; f < 4; f++) {
-    const C2 d = L.b[0][fid[f]];
-    R acc = L.cre[0] * d.x - L.cim[0] * d.y;
+    R acc = 0;
+    if (idx_in(fid[f], L.nf, L.stats)) {
+      const C2 d = L.b[0][fid[f]];
+      acc = L.cre[0] * d.x - L.cim[0] * d.y;
 #pragma unroll
-    for (int k = 1; k < NL; k++) {
-      const C2 dk = L.b[k][fid[f]];
-      acc += L.cre[k] * dk.x - L.cim[k] * dk.y;
+      for (int k = 1; k < NL; k++) {
+        const C2 dk = L.b[k][fid[f]];
+        acc += L.cre[k] * dk.x - L.cim[k] * dk.y;
+      }
     }
     bet[f] = acc;
   }
@@ -360,7 +393,7 @@ __device__ __forceinline__ void deposit64(const PushArgs& A, int32_t T, const do
   for (int e = 0; e < 6; e++) {
     const int i = le0(e), j = le1(e);
     const double g = qw * fma(la[i], lb[j], -(la[j] * lb[i]));
-    atomicAdd(A.dG + eid[e], g);
+    if (idx_in(eid[e], A.ne, A.stats)) atomicAdd(A.dG + eid[e], g);
   }
 }
 
@@ -531,6 +564,10 @@ __device__ __forceinline__ bool cross64_advance(const PushArgs& A, CrossState64&
   }
   const int4 nbv = ldg_int4(&A.nb[c.T]);
   const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+  if (nbt >= 0 && !idx_in(nbt, A.nt, A.stats)) {
+    c.st = FEMPIC_P_LOST;
+    return true;
+  }
   if (nbt >= 0) {
     const int4 o4 = ldg_int4(&A.tn[c.T]), n4 = ldg_int4(&A.tn[nbt]);
     const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nn[4] = {n4.x, n4.y, n4.z, n4.w};
@@ -1466,6 +1503,13 @@ __device__ __forceinline__ bool cross_advance(const PushArgs& A, CrossState& c, 
   const int4 nbv = make_int4(__float_as_int(nbf.x), __float_as_int(nbf.y), __float_as_int(nbf.z),
                              __float_as_int(nbf.w));
   const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+  if (nbt >= 0 && !idx_in(nbt, A.nt, A.stats)) {
+    c.st = FEMPIC_P_LOST;
+    c.moved = false;
+#pragma unroll
+    for (int j = 0; j < 4; j++) c.Qa[j] = Qp[j];
+    return true;
+  }
   if (nbt >= 0) {
     // the face map (same record line) says which of this tet's nodes each of
     // the neighbour's nodes is, and which one it enters through
@@ -1764,6 +1808,11 @@ __device__ __forceinline__ bool cross_advance_df(const PushArgs& A, CrossStateDF
   const int4 nbv = make_int4(__float_as_int(nbf.x), __float_as_int(nbf.y), __float_as_int(nbf.z),
                              __float_as_int(nbf.w));
   const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+  if (nbt >= 0 && !idx_in(nbt, A.nt, A.stats)) {
+    c.st = FEMPIC_P_LOST;
+    c.moved = false;
+    return true;
+  }
   if (nbt >= 0) {
     // the face map says which of this tet's nodes each of the neighbour's
     // nodes is, and which one it enters through
@@ -1988,6 +2037,7 @@ struct FinalizeArgs {
   double2* Genv_out;
   double c, s;                   // cos, sin of omega0 t_next
   int32_t local;                 // 1: write dG_out only, leave G_cum (fempic_deposit_local)
+  unsigned long long* stats;     // bounds checks of the debug build
 };
 
 // Deposit finalize, one thread per edge.  The mixed forms pull the edge's
@@ -2009,7 +2059,7 @@ __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
       const unsigned long long* sl = A.dGq + (int64_t)s * A.nt * 8;
       for (int32_t j = j0; j < j1; j++) {
         const int32_t k = A.eslot[j];
-        q += (long long)sl[(int64_t)(k / 6) * 8 + k % 6];
+        if (idx_in(k, 6 * A.nt, A.stats)) q += (long long)sl[(int64_t)(k / 6) * 8 + k % 6];
       }
       d += A.qwscale[s] * (double)q;
     }
@@ -2018,6 +2068,7 @@ __global__ void __launch_bounds__(kThreads) k_deposit_finalize(FinalizeArgs A) {
     const int32_t j0 = A.estart[e], j1 = A.estart[e + 1];
     for (int32_t j = j0; j < j1; j++) {
       const int32_t k = A.eslot[j];
+      if (!idx_in(k, 6 * A.nt, A.stats)) continue;
       const float2 v = reinterpret_cast<const float2*>(A.tetout)[(int64_t)(k / 6) * 6 + k % 6];
       acc = df_add(acc, DF{v.x, v.y});
     }
@@ -2064,6 +2115,8 @@ struct ChargeArgs {
   const float4* tetrec;
   const int4* tn;
   double* rho;
+  int64_t nn;                 // node count and stats: bounds checks of the debug build
+  unsigned long long* stats;
 };
 
 __global__ void __launch_bounds__(kThreads) k_nodal_charge(ChargeArgs A) {
@@ -2085,10 +2138,10 @@ __global__ void __launch_bounds__(kThreads) k_nodal_charge(ChargeArgs A) {
     bary64(A.geom64 + 12 * (int64_t)T, r, lam);
   }
   const int4 n4 = A.tn[T];
-  atomicAdd(A.rho + n4.x, qw * lam[0]);
-  atomicAdd(A.rho + n4.y, qw * lam[1]);
-  atomicAdd(A.rho + n4.z, qw * lam[2]);
-  atomicAdd(A.rho + n4.w, qw * lam[3]);
+  const int32_t nid[4] = {n4.x, n4.y, n4.z, n4.w};
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    if (idx_in(nid[i], A.nn, A.stats)) atomicAdd(A.rho + nid[i], qw * lam[i]);
 }
 
 
@@ -2289,6 +2342,7 @@ struct AdjArgs {
   const double* curw;
   const int4* nb;
   const int4* tn;
+  unsigned long long* stats;   // bounds checks of the debug build
   int32_t max_cross;
   int32_t wall_mode;
   double lo[3], hi[3];
@@ -2453,6 +2507,7 @@ __device__ __noinline__ void dep_loss_grad(const AdjArgs& A, int32_t T0, const d
     if (nc > A.max_cross) break;   // frozen at q: the deposit ended there
     const int4 nbv = ldg_int4(&A.nb[T]);
     const int32_t nbt = kx == 0 ? nbv.x : kx == 1 ? nbv.y : kx == 2 ? nbv.z : nbv.w;
+    if (nbt >= 0 && !idx_in(nbt, A.nt, A.stats)) break;
     if (nbt >= 0) {
       const int4 o4 = ldg_int4(&A.tn[T]), n4 = ldg_int4(&A.tn[nbt]);
       const int32_t on[4] = {o4.x, o4.y, o4.z, o4.w}, nn[4] = {n4.x, n4.y, n4.z, n4.w};
@@ -2731,7 +2786,8 @@ __global__ void __launch_bounds__(kThreads) k_push_adjoint(AdjArgs A) {
 __global__ void __launch_bounds__(kThreads) k_current_weights(int64_t nt, const double* __restrict__ geom64,
                                                                const int4* __restrict__ te,
                                                                const double* __restrict__ u,
-                                                               double* __restrict__ curw) {
+                                                               double* __restrict__ curw, int64_t ne,
+                                                               unsigned long long* stats) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double G[4][3];
@@ -2742,7 +2798,7 @@ __global__ void __launch_bounds__(kThreads) k_current_weights(int64_t nt, const 
 #pragma unroll
   for (int e = 0; e < 6; e++) {
     const int i = le0(e), j = le1(e);
-    const double ue = u[eid[e]];
+    const double ue = idx_in(eid[e], ne, stats) ? u[eid[e]] : 0.0;
     double c[3];
     cross3d(G[i], G[j], c);
 #pragma unroll
@@ -2857,13 +2913,14 @@ __global__ void __launch_bounds__(kThreads) k_dof_grad(int64_t ne, int64_t nf, c
                                                        const int32_t* __restrict__ eslot,
                                                        const int32_t* __restrict__ fslot,
                                                        const double* __restrict__ tadj, double cre, double cim,
-                                                       double* __restrict__ egrad, double* __restrict__ bgrad) {
+                                                       double* __restrict__ egrad, double* __restrict__ bgrad,
+                                                       int64_t nt, unsigned long long* stats) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < ne) {
     double sum = 0.0;
     for (int32_t j = estart[i]; j < estart[i + 1]; j++) {
       const int32_t sl = eslot[j];
-      sum += tadj[(int64_t)(sl / 6) * 10 + sl % 6];
+      if (idx_in(sl, 6 * nt, stats)) sum += tadj[(int64_t)(sl / 6) * 10 + sl % 6];
     }
     if (sum != 0.0) {
       egrad[2 * i] += cre * sum;
@@ -2875,7 +2932,7 @@ __global__ void __launch_bounds__(kThreads) k_dof_grad(int64_t ne, int64_t nf, c
 #pragma unroll
     for (int k = 0; k < 2; k++) {
       const int32_t sl = fslot[2 * i + k];
-      if (sl >= 0) sum += tadj[(int64_t)(sl >> 2) * 10 + 6 + (sl & 3)];
+      if (sl >= 0 && idx_in(sl, 4 * nt, stats)) sum += tadj[(int64_t)(sl >> 2) * 10 + 6 + (sl & 3)];
     }
     if (sum != 0.0) {
       bgrad[2 * i] += cre * sum;
@@ -2990,7 +3047,7 @@ struct fempic_env {
   bool profiling = false;
   int32_t stall_cta = -1;           // fempic_debug_stall (test support)
   unsigned long long stall_ns = 0;
-  unsigned long long seen_frozen = 0, seen_timeouts = 0;   // fempic_error_count baselines
+  unsigned long long seen_frozen = 0, seen_timeouts = 0, seen_bounds = 0;   // fempic_error_count baselines
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
@@ -3282,6 +3339,8 @@ extern "C" int fempic_locate(fempic_env* env, const fempic_particles* p, void* s
   A.geom64 = env->geom64;
   A.gstart = env->gstart;
   A.gtet = env->gtet;
+  A.nt = env->h.nt;
+  A.stats = env->stats;
   for (int a = 0; a < 3; a++) {
     A.gd[a] = env->h.gd[a];
     A.ginv[a] = env->h.ginv[a];
@@ -3402,6 +3461,9 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
   lt.kernels = 1;
   if (mixed) {
     Levels<float2, float> L{};
+    L.ne = env->h.ne;
+    L.nf = env->h.nf;
+    L.stats = env->stats;
     for (int k = 0; k < H.nl; k++) {
       L.e[k] = static_cast<const float2*>(H.e[k]);
       L.b[k] = static_cast<const float2*>(H.b[k]);
@@ -3414,6 +3476,9 @@ static int push_step_impl(fempic_env* env, const fempic_particles* p, const Host
       k_field_f32<3><<<blocks_for(nt), kThreads, 0, st>>>(nt, env->tetrec, env->te, env->tf, L);
   } else {
     Levels<double2, double> L{};
+    L.ne = env->h.ne;
+    L.nf = env->h.nf;
+    L.stats = env->stats;
     for (int k = 0; k < H.nl; k++) {
       L.e[k] = static_cast<const double2*>(H.e[k]);
       L.b[k] = static_cast<const double2*>(H.b[k]);
@@ -3594,6 +3659,7 @@ static int deposit_impl(fempic_env* env, double omega0, double t_next, double* d
   FinalizeArgs A{};
   A.ne = env->h.ne;
   A.nt = env->h.nt;
+  A.stats = env->stats;
   A.mode = prec == FEMPIC_FP64 ? 0 : (prec == FEMPIC_MIXED ? 1 : 2);
   A.ns = env->ns_last;
   for (int s = 0; s < kMaxSpecies; s++) A.qwscale[s] = env->qw_last[s] * 0x1p-48;
@@ -3712,6 +3778,8 @@ extern "C" int fempic_nodal_charge(fempic_env* env, const fempic_particles* p, d
   A.tetrec = env->tetrec;
   A.tn = env->tn;
   A.rho = rho;
+  A.nn = env->h.nn;
+  A.stats = env->stats;
   {
     LaunchTimer lt(env, st, FEMPIC_K_CHARGE);
     k_nodal_charge<<<blocks_for(p->n), kThreads, 0, st>>>(A);
@@ -3736,18 +3804,46 @@ extern "C" int fempic_stats(fempic_env* env, int64_t* out4, void* stream) {
 
 extern "C" int fempic_error_count(fempic_env* env, int64_t* n_bad, void* stream) {
   if (!env || !n_bad) return fail(FEMPIC_EINVAL, "error_count: NULL argument");
-  unsigned long long h[3] = {0, 0, 0};
+  unsigned long long h[4] = {0, 0, 0, 0};
   cudaStream_t st = (cudaStream_t)stream;
-  FEMPIC_CUDA(cudaMemcpyAsync(h, env->stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  FEMPIC_CUDA(cudaMemcpyAsync(h, env->stats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   FEMPIC_CUDA(cudaStreamSynchronize(st));
   *n_bad = (int64_t)(h[1] - env->seen_frozen);
   const unsigned long long gave_up = h[2] - env->seen_timeouts;
+  const unsigned long long bad_idx = h[3] - env->seen_bounds;
   env->seen_frozen = h[1];
   env->seen_timeouts = h[2];
+  env->seen_bounds = h[3];
   if (gave_up)
     return fail(FEMPIC_EINCOMPLETE, "error_count: " + std::to_string(gave_up) +
                                         " staged push CTA(s) gave up waiting for a bulk copy; the particles of "
                                         "their remaining tiles were not advanced and their deposit is missing");
+  if (bad_idx)
+    return fail(FEMPIC_EBOUNDS, "error_count: " + std::to_string(bad_idx) +
+                                    " mesh-table index(es) out of range were skipped (debug build)");
+  return FEMPIC_OK;
+}
+
+extern "C" int fempic_debug_set_table(fempic_env* env, int32_t table, int64_t index, int32_t value) {
+  if (!env) return fail(FEMPIC_EINVAL, "debug_set_table: NULL env");
+  if (!kBoundsCheck)
+    return fail(FEMPIC_EINVAL, "debug_set_table: only the debug build (FEMPIC_BOUNDS_CHECK) accepts it");
+  const int64_t nt = env->h.nt;
+  if (table == FEMPIC_TABLE_NEIGHBOUR) {
+    if (index < 0 || index >= 4 * nt) return fail(FEMPIC_EINVAL, "debug_set_table: neighbour index out of range");
+    // the neighbour table and its copy in the last 16 B of the tet record
+    int32_t* nb = reinterpret_cast<int32_t*>(env->nb);
+    FEMPIC_CUDA(cudaMemcpy(nb + index, &value, sizeof(int32_t), cudaMemcpyHostToDevice));
+    float* rec = reinterpret_cast<float*>(env->tetrec);
+    FEMPIC_CUDA(cudaMemcpy(rec + 32 * (index / 4) + 28 + index % 4, &value, sizeof(int32_t),
+                           cudaMemcpyHostToDevice));
+  } else if (table == FEMPIC_TABLE_EDGE) {
+    if (index < 0 || index >= 6 * nt) return fail(FEMPIC_EINVAL, "debug_set_table: edge index out of range");
+    int32_t* te = reinterpret_cast<int32_t*>(env->te);
+    FEMPIC_CUDA(cudaMemcpy(te + 8 * (index / 6) + index % 6, &value, sizeof(int32_t), cudaMemcpyHostToDevice));
+  } else {
+    return fail(FEMPIC_EINVAL, "debug_set_table: unknown table");
+  }
   return FEMPIC_OK;
 }
 
@@ -4066,6 +4162,9 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
   double cre = envl->amp * std::cos(phi), cim = envl->amp * std::sin(phi);
   if (mixed) {
     Levels<float2, float> L{};
+    L.ne = env->h.ne;
+    L.nf = env->h.nf;
+    L.stats = env->stats;
     L.e[0] = static_cast<const float2*>(envl->e_tilde);
     L.b[0] = static_cast<const float2*>(envl->b_tilde);
     L.cre[0] = (float)cre;
@@ -4075,6 +4174,9 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
     cim = (double)(float)cim;
   } else {
     Levels<double2, double> L{};
+    L.ne = env->h.ne;
+    L.nf = env->h.nf;
+    L.stats = env->stats;
     L.e[0] = static_cast<const double2*>(envl->e_tilde);
     L.b[0] = static_cast<const double2*>(envl->b_tilde);
     L.cre[0] = cre;
@@ -4112,6 +4214,7 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
     A.curw = env->curw_on ? env->curw : nullptr;
     A.nb = env->nb;
     A.tn = env->tn;
+    A.stats = env->stats;
     A.max_cross = env->opt.max_crossings;
     A.wall_mode = env->opt.wall_mode;
     for (int a = 0; a < 3; a++) {
@@ -4142,7 +4245,7 @@ extern "C" int fempic_push_step_adjoint(fempic_env* env, const fempic_particles*
   const int64_t ndof = std::max(env->h.ne, env->h.nf);
   k_dof_grad<<<blocks_for(ndof), kThreads, 0, st>>>(env->h.ne, env->h.nf, env->estart, env->eslot, env->fslot,
                                                      env->tadj, cre, cim, static_cast<double*>(e_grad),
-                                                     static_cast<double*>(b_grad));
+                                                     static_cast<double*>(b_grad), nt, env->stats);
   lt.kernels++;
   FEMPIC_CUDA(cudaGetLastError());
   return FEMPIC_OK;
@@ -4157,7 +4260,8 @@ extern "C" int fempic_adjoint_current_weights(fempic_env* env, const double* u, 
   const int64_t nt = env->h.nt;
   if (!env->curw) FEMPIC_CUDA(dalloc(&env->curw, 6 * nt));
   cudaStream_t st = (cudaStream_t)stream;
-  k_current_weights<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, u, env->curw);
+  k_current_weights<<<blocks_for(nt), kThreads, 0, st>>>(nt, env->geom64, env->te, u, env->curw, env->h.ne,
+                                                          env->stats);
   FEMPIC_CUDA(cudaGetLastError());
   env->curw_on = true;
   return FEMPIC_OK;

@@ -39,6 +39,14 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def test_debug_build_exports_the_same_symbols(lib):
+    """The bounds-checked debug build (FEMPIC_BOUNDS_CHECK) is built beside
+    the release library and loads without a GPU."""
+    dbg = C.CDLL(build.DEBUG_LIB)
+    for name in _declared() + _declared("fempic_downshift.h"):
+        assert hasattr(dbg, name), name
+
+
 def test_downshift_plane_layout_matches_header():
     txt = open(os.path.join(ROOT, "include", "fempic_downshift.h")).read()
     got = {k: int(v) for k, v in re.findall(r"#define FEMPIC_DS_(\w+) (\d+)", txt)}
