@@ -95,6 +95,17 @@ int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds, const femp
                                const fempic_downshift_history* hist, const fempic_envelope* envl,
                                double omega0, double t, double dt, int32_t start, void* stream);
 
+/* Carry a history through a particle sort (the paper keeps particles in no
+ * order; this keeps the downshifted step's history with its particles when
+ * the set is re-sorted by tet for coalescing): for the planes that outlive a
+ * step (FEMPIC_DS_VH .. FEMPIC_DS_VN - 1), out[k][q] = in[k][perm[q]], with
+ * perm the permutation fempic_sort_perm returned for the same sort (perm[q] =
+ * the index before the sort of particle q; a permutation of [0, n), device
+ * int32 [n]).  in and out must not overlap.  Stream-ordered.  Errors:
+ * EINVAL, ECUDA. */
+int fempic_downshift_permute(const fempic_downshift_history* in, const fempic_downshift_history* out,
+                             const int32_t* perm, void* stream);
+
 const char* fempic_downshift_last_error(void);
 void fempic_downshift_destroy(fempic_downshift* ds);
 

@@ -40,7 +40,7 @@ EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_pus
            "fempic_measure_fp64_rate", "fempic_last_error", "fempic_env_destroy")
 # Every function declared in include/fempic_downshift.h.
 DS_EXPORTS = ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift",
-              "fempic_downshift_last_error", "fempic_downshift_destroy")
+              "fempic_downshift_permute", "fempic_downshift_last_error", "fempic_downshift_destroy")
 FEMPIC_DS_VH, FEMPIC_DS_F, FEMPIC_DS_VN, FEMPIC_DS_U, FEMPIC_DS_PLANES = 0, 9, 33, 36, 39
 FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS, \
     FEMPIC_K_ADJOINT = range(8)
@@ -141,11 +141,14 @@ def load(path: str = LIB_PATH):
         lib.fempic_push_step_downshift.argtypes = [C.c_void_p, C.c_void_p, P(fempic_particles),
                                                    P(fempic_downshift_history), P(fempic_envelope), C.c_double,
                                                    C.c_double, C.c_double, C.c_int32, C.c_void_p]
+        lib.fempic_downshift_permute.argtypes = [P(fempic_downshift_history), P(fempic_downshift_history),
+                                                 C.c_void_p, C.c_void_p]
         lib.fempic_downshift_last_error.restype = C.c_char_p
         lib.fempic_downshift_last_error.argtypes = []
         lib.fempic_downshift_destroy.argtypes = [C.c_void_p]
         lib.fempic_downshift_destroy.restype = None
-        for name in ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift"):
+        for name in ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift",
+                     "fempic_downshift_permute"):
             getattr(lib, name).restype = C.c_int
         lib.fempic_last_error.restype = C.c_char_p
         lib.fempic_last_error.argtypes = []
@@ -336,6 +339,12 @@ def fempic_push_step_downshift(env, ds, parts: fempic_particles, hist: fempic_do
     check_ds(load().fempic_push_step_downshift(env, ds, C.byref(parts), C.byref(hist), C.byref(envl),
                                                float(omega0), float(t), float(dt), 1 if start else 0, stream),
              "fempic_push_step_downshift")
+
+
+def fempic_downshift_permute(hist_in: fempic_downshift_history, hist_out: fempic_downshift_history, perm,
+                             stream=0):
+    check_ds(load().fempic_downshift_permute(C.byref(hist_in), C.byref(hist_out), perm, stream),
+             "fempic_downshift_permute")
 
 
 def fempic_downshift_last_error() -> str:

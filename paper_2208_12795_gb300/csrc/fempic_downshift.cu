@@ -362,7 +362,33 @@ static void free_ds(fempic_downshift* d) {
   delete d;
 }
 
+// History planes follow a particle sort: out[k][q] = in[k][perm[q]] for the
+// planes that outlive a step (velocities and envelope samples; the two
+// scratch vectors are rewritten by every step).
+__global__ void __launch_bounds__(kThreads) k_ds_permute(int64_t n, const int32_t* __restrict__ perm,
+                                                          const double* __restrict__ in, double* __restrict__ out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int64_t src = perm[q];
+#pragma unroll 3
+  for (int k = 0; k < FEMPIC_DS_VN; k++) out[k * n + q] = __ldg(in + k * n + src);
+}
+
 extern "C" const char* fempic_downshift_last_error(void) { return g_ds_error.c_str(); }
+
+extern "C" int fempic_downshift_permute(const fempic_downshift_history* in, const fempic_downshift_history* out,
+                                        const int32_t* perm, void* stream) {
+  if (!in || !out || !perm) return fail(FEMPIC_EINVAL, "downshift_permute: NULL argument");
+  if (in->n != out->n || in->n < 0) return fail(FEMPIC_EINVAL, "downshift_permute: sizes differ");
+  if (in->n == 0) return FEMPIC_OK;
+  if (!in->planes || !out->planes || in->planes == out->planes)
+    return fail(FEMPIC_EINVAL, "downshift_permute: NULL or overlapping planes");
+  if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "downshift_permute: more than 2^31 particles");
+  const unsigned blocks = (unsigned)((in->n + kThreads - 1) / kThreads);
+  k_ds_permute<<<blocks, kThreads, 0, (cudaStream_t)stream>>>(in->n, perm, in->planes, out->planes);
+  DS_CUDA(cudaGetLastError());
+  return FEMPIC_OK;
+}
 
 extern "C" void fempic_downshift_destroy(fempic_downshift* ds) { free_ds(ds); }
 

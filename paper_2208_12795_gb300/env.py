@@ -265,7 +265,8 @@ class Downshift:
     env's own step.  Holds the per-tet gather tables and the particles'
     history planes ([FEMPIC_DS_PLANES, n] f64 on the device).  Velocities are
     at integer levels (v^n), not half steps.  The history follows the
-    particle order, so the particle set must not be re-sorted between steps."""
+    particle order: re-sort the set with `sort`, which carries the history
+    through the same permutation (fempic_sort_perm, fempic_downshift_permute)."""
 
     def __init__(self, env: FempicEnv, n: int, device="cuda"):
         if env.precision != FEMPIC_FP64:
@@ -285,6 +286,22 @@ class Downshift:
             self.close()
         except Exception:
             pass
+
+    def sort(self, st: ParticleState, scratch: ParticleState, stream=None):
+        """Sort `st` by (species, tet) through `scratch` (buffers swapped, as
+        FempicEnv.sort does) and carry the history planes along; returns the
+        permutation (perm[q] = index before the sort of particle q)."""
+        perm = torch.empty(st.n, dtype=torch.int32, device=st.x.device)
+        self.env.sort_perm(st, scratch, perm, stream=stream)
+        st.swap(scratch)
+        spare = getattr(self, "_spare", None)
+        if spare is None or spare.shape != self.planes.shape:
+            spare = torch.empty_like(self.planes)
+        hin = capi.fempic_downshift_history(st.n, _ptr(self.planes))
+        hout = capi.fempic_downshift_history(st.n, _ptr(spare))
+        capi.fempic_downshift_permute(hin, hout, _ptr(perm), _stream(stream))
+        self.planes, self._spare = spare, self.planes
+        return perm
 
     def step(self, st: ParticleState, e_dof: torch.Tensor, b_dof: torch.Tensor, amp: float, omega0: float,
              t: float, dt: float, stream=None):
