@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--particles", type=int, default=10_000_000)
-    ap.add_argument("--sort-every", type=int, default=8)
+    ap.add_argument("--sort-every", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true", help="skip the side-by-side FP64 form")
     ap.add_argument("--no-q24", action="store_true", help="skip the 24-bit mixed variant")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -957,24 +957,6 @@ __device__ __forceinline__ float fx_scale(unsigned emax) {
   return emax < 24u ? 0.f : __uint_as_float((278u - emax) << 23);
 }
 
-// v 2^e2 as a double, rounded to nearest (ties up), with integer operations
-// only; |v| < 2^62.
-__device__ __forceinline__ double i64_to_f64(long long v, int e2) {
-  if (v == 0) return 0.0;
-  const unsigned long long sgn = v < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-  const int lz = __clzll((long long)a);
-  a <<= lz;                                          // leading one at bit 63
-  unsigned long long mant = (a >> 11) + ((a >> 10) & 1ull);
-  int e = 63 - lz + e2;
-  if (mant >> 53) {
-    mant >>= 1;
-    e++;
-  }
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) |
-                                          (mant & 0xfffffffffffffull)));
-}
-
 __device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
 
 // Per-lane result of the common path, consumed by the warp epilogue.
@@ -996,6 +978,7 @@ struct LaneOut {
 struct CrossList {
   int32_t total;     // records of the current tile
   long long sums[kThreads / 32][32 * 6];   // per warp: run sums of the deposit, by head lane
+  int32_t keys[kThreads / 32][32];         // per warp: run keys, by head lane
 };
 
 __device__ __forceinline__ void lane_init(LaneOut& o, int lane) {
@@ -1103,6 +1086,8 @@ __device__ __forceinline__ void mixed_particle(const PushArgs& A, int64_t p, int
     o.v[1] = vn1;
     o.v[2] = vn2;
     o.T = T;
+    // joins its tet's run with zero values, so that the run is not split
+    o.key = T * kMaxSpecies + s;
     return;
   }
   if (Q24) {
@@ -1205,29 +1190,34 @@ __device__ __forceinline__ void mixed_warp_epilogue(const PushArgs& A, int64_t p
         }
       }
     }
-    // the run's lanes share its six slot updates: the head leaves the sums in
-    // the warp's scratch row, lane r of the run takes components r, r + len, ...
-    long long* row = cl.sums[threadIdx.x >> 5];
-    if (head && o.key >= 0) {
+    // the slot updates: each head leaves its run's sums and key in the warp's
+    // scratch rows, and the warp's (run, component) pairs are spread over its
+    // lanes, 32 per round (one round for up to 5 runs)
+    const int w = threadIdx.x >> 5;
+    long long* row = cl.sums[w];
+    const bool dep = o.key >= 0;
+    if (head && dep) {
 #pragma unroll
       for (int e = 0; e < 6; e++)
-        row[6 * (lane & 31) + e] = Q24 ? o.gh[e] : (long long)o.lh[e] * 33554432ll + (long long)o.ll[e];
+        row[6 * lane + e] = Q24 ? o.gh[e] : (long long)o.lh[e] * 33554432ll + (long long)o.ll[e];
+      cl.keys[w][lane] = o.key;
     }
+    const unsigned dheads = heads & __ballot_sync(full, dep);
     __syncwarp();
-    if (o.key >= 0) {
-      const unsigned below = heads & (0xffffffffu >> (31 - lane));   // heads at or below this lane
-      const int start = 31 - __clz(below);
-      const int len = run_end - start + 1;
+    const int npairs = 6 * __popc(dheads);
 #pragma unroll 1
-      for (int c = lane - start; c < 6; c += len) {
-        const long long v = row[6 * start + c];
-        if (v == 0) continue;
-        if (Q24)
-          atomicAdd(A.dGq + ((int64_t)o.shome * A.nt + o.Thome) * 8 + c, (unsigned long long)v);
-        else   // the run's X sum times 2^(emax - 176)
-          atomicAdd(A.mom + ((int64_t)o.shome * A.nt + o.Thome) * 6 + c,
-                    i64_to_f64(v, (int)(c < 3 ? eD : eM) - 176));
-      }
+    for (int j = lane; j < npairs; j += 32) {
+      const int r = j / 6, c = j - 6 * r;
+      const int start = (int)__fns(dheads, 0, r + 1);
+      const long long v = row[6 * start + c];
+      if (v == 0) continue;
+      const int32_t key = cl.keys[w][start];
+      const int64_t slot = (int64_t)(key & (kMaxSpecies - 1)) * A.nt + (key / kMaxSpecies);
+      if (Q24)
+        atomicAdd(A.dGq + slot * 8 + c, (unsigned long long)v);
+      else   // the run's X sum times 2^(emax - 176)
+        atomicAdd(A.mom + slot * 6 + c,   // the hardware conversion: a few lanes per run, the FP64 pipe has room
+                  (double)v * __longlong_as_double((long long)((int)(c < 3 ? eD : eM) - 176 + 1023) << 52));
     }
     __syncwarp();
   }
