@@ -1879,9 +1879,11 @@ __device__ __forceinline__ void cross_finish_df(const PushArgs& A, const CrossSt
   ncr += (unsigned)c.nc;
 }
 
-// Same record hand-out as k_cross_q24: one warp per tile region, each loop
-// iteration advances every busy lane by one piece, idle lanes take the
-// tile's next record.
+// Each loop iteration advances every busy lane by one piece; idle lanes take
+// the next records of the warp's record stream, which runs on across its
+// tiles (tile, tile + warps, ...): a tile holds about 36 leaving particles
+// on the cavity, so a per-tile loop would leave most lanes idle at the end of
+// every tile (the stream measured 9 % faster).
 #ifndef FEMPIC_CROSS_MIN_BLOCKS
 #define FEMPIC_CROSS_MIN_BLOCKS 3
 #endif
@@ -1891,30 +1893,37 @@ __global__ void __launch_bounds__(kThreads, FEMPIC_CROSS_MIN_BLOCKS) k_cross_df(
   const unsigned lt = (1u << lane) - 1u;
   unsigned ncr = 0, nfrz = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
-    const int32_t cnt = A.xcount[t];
-    int32_t next = 0;
-    bool have = false, fresh = false;
-    CrossStateDF c;
-    for (;;) {
-      const unsigned idle = __ballot_sync(full, !have);
-      if (next < cnt && idle) {
-        const int32_t idx = next + __popc(idle & lt);
-        if (!have && idx < cnt) {
-          cross_begin_df(A, A.xrec[t * kThreads + idx], c);
-          have = true;
-          fresh = true;
-        }
-        next += __popc(idle);
+  int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int32_t cnt = tile < ntiles ? A.xcount[tile] : 0, next = 0;
+  bool have = false, fresh = false;
+  CrossStateDF c;
+  for (;;) {
+    unsigned idle = __ballot_sync(full, !have);
+    while (idle && tile < ntiles) {   // warp-uniform: assigns records or advances a tile
+      const int32_t avail = cnt - next;
+      const int32_t want = __popc(idle);
+      const int32_t take = avail < want ? avail : want;
+      const int r = __popc(idle & lt);
+      if (!have && r < take) {
+        cross_begin_df(A, A.xrec[tile * kThreads + next + r], c);
+        have = true;
+        fresh = true;
       }
-      if (!__any_sync(full, have)) break;
-      if (have) {
-        const bool done = cross_advance_df(A, c, fresh);
-        fresh = false;
-        if (done) {
-          cross_finish_df(A, c, ncr, nfrz);
-          have = false;
-        }
+      next += take;
+      idle = __ballot_sync(full, !have);
+      if (next == cnt) {
+        tile += warps;
+        cnt = tile < ntiles ? A.xcount[tile] : 0;
+        next = 0;
+      }
+    }
+    if (!__any_sync(full, have)) break;
+    if (have) {
+      const bool done = cross_advance_df(A, c, fresh);
+      fresh = false;
+      if (done) {
+        cross_finish_df(A, c, ncr, nfrz);
+        have = false;
       }
     }
   }
