@@ -1587,12 +1587,13 @@ __device__ __forceinline__ void cross_finish(const PushArgs& A, const CrossState
   ncr += (unsigned)c.nc;
 }
 
-// Crossing pass of the 24-bit form: one warp per 256-particle tile region of
-// the record queue.  Each loop iteration advances every busy lane by one
-// face; a lane whose particle is done takes the tile's next record, so a
-// particle that crosses many faces (a fast beam particle) does not hold 31
-// idle lanes.  Records of one tile come from neighbouring tets, so the
-// warp's tet records and deposit slots stay in cache.
+// Crossing pass of the 24-bit form.  Each warp takes a stream of tile
+// regions of the record queue (tile, tile + warps, ...); each loop iteration
+// advances every busy lane by one face, and a lane whose particle is done
+// takes the stream's next record, so neither a particle that crosses many
+// faces (a fast beam particle) nor the end of a tile holds idle lanes.
+// Records of one tile come from neighbouring tets, so the warp's tet records
+// and deposit slots stay in cache.
 constexpr int kCrossWarpsPerSm = 64;
 
 __global__ void __launch_bounds__(kThreads) k_cross_q24(PushArgs A, int64_t ntiles) {
@@ -1601,30 +1602,37 @@ __global__ void __launch_bounds__(kThreads) k_cross_q24(PushArgs A, int64_t ntil
   const unsigned lt = (1u << lane) - 1u;
   unsigned ncr = 0, nfrz = 0;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += warps) {
-    const int32_t cnt = A.xcount[t];
-    int32_t next = 0;
-    bool have = false, fresh = false;
-    CrossState c;
-    for (;;) {
-      const unsigned idle = __ballot_sync(full, !have);
-      if (next < cnt && idle) {
-        const int32_t idx = next + __popc(idle & lt);
-        if (!have && idx < cnt) {
-          cross_begin(A, A.xrec[t * kThreads + idx], c);
-          have = true;
-          fresh = true;
-        }
-        next += __popc(idle);
+  int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int32_t cnt = tile < ntiles ? A.xcount[tile] : 0, next = 0;
+  bool have = false, fresh = false;
+  CrossState c;
+  for (;;) {
+    unsigned idle = __ballot_sync(full, !have);
+    while (idle && tile < ntiles) {   // warp-uniform: assigns records or advances a tile
+      const int32_t avail = cnt - next;
+      const int32_t want = __popc(idle);
+      const int32_t take = avail < want ? avail : want;
+      const int r = __popc(idle & lt);
+      if (!have && r < take) {
+        cross_begin(A, A.xrec[tile * kThreads + next + r], c);
+        have = true;
+        fresh = true;
       }
-      if (!__any_sync(full, have)) break;
-      if (have) {
-        const bool done = cross_advance(A, c, fresh);
-        fresh = false;
-        if (done) {
-          cross_finish(A, c, ncr, nfrz);
-          have = false;
-        }
+      next += take;
+      idle = __ballot_sync(full, !have);
+      if (next == cnt) {
+        tile += warps;
+        cnt = tile < ntiles ? A.xcount[tile] : 0;
+        next = 0;
+      }
+    }
+    if (!__any_sync(full, have)) break;
+    if (have) {
+      const bool done = cross_advance(A, c, fresh);
+      fresh = false;
+      if (done) {
+        cross_finish(A, c, ncr, nfrz);
+        have = false;
       }
     }
   }
