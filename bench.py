@@ -116,13 +116,15 @@ def bytes_reverse_window(n_p, counts, form, steps, every, stash, recompute_steps
     return b
 
 
-def bytes_alg_per_step_downshift(n_p, counts):
-    """Algorithmic bytes of one downshifted FP64 step: the FP64 particle
-    state and the history the rule needs (v^{n-1..n-3}: 72 B; the complex
-    E~ and B~ samples of levels n-1 and n-2: 192 B), each read and written,
-    plus the mesh and DoF terms of the FP64 step."""
+def bytes_alg_per_step_downshift(n_p, counts, form="fp64"):
+    """Algorithmic bytes of one downshifted step: the particle state and the
+    history the rule needs (v^{n-1..n-3}: 9 values; the complex E~ and B~
+    samples of levels n-1 and n-2: 24 values; f64 in the FP64 form, 264 B,
+    f32 in the mixed forms, 132 B), each read and written, plus the mesh and
+    DoF terms of the step."""
     nn, ne, nf, nt = counts
-    return n_p * 2 * (52 + 264) + 72 * nt + 24 * nn + (16 + 8) * ne + 16 * nf
+    s_p, s_h, s_dof = (52, 264, 16) if form == "fp64" else (40, 132, 8)
+    return n_p * 2 * (s_p + s_h) + 72 * nt + 24 * nn + (s_dof + 8) * ne + s_dof * nf
 
 
 def measured_peaks():
@@ -621,21 +623,21 @@ def run_ours(args):
     env.close()
 
     # The downshifted integrator (Sec. III-D: M/L velocity rule, AB4
-    # positions) on the FP64 form, device resident, after the other legs; the
-    # set is re-sorted on the step's cadence with the history planes carried
-    # through the same permutation (Downshift.sort).
-    if not args.no_downshift and args.workload == "cube48":
-        env_d = FempicEnv.from_mesh(mesh, precision=0)
-        st_d = particle_state(0)
+    # positions) on the FP64 form and on the contract mixed form, device
+    # resident, after the other legs; the set is re-sorted on its cadence with
+    # the history planes carried through the same permutation (Downshift.sort).
+    def downshift_leg(prec):
+        env_d = FempicEnv.from_mesh(mesh, precision=prec)
+        st_d = particle_state(prec)
         env_d.locate(st_d)
         env_d.sort(st_d, st_d.empty_like())
         ds = Downshift(env_d, st_d.n)
         scratch_d = st_d.empty_like()
-        # a re-sort also gathers the 33 history planes (528 B per particle),
-        # against a 6.6 ms step: every 4x the push step's cadence
+        # a re-sort also gathers the 33 history planes, against a step of
+        # several ms: every 4x the push step's cadence
         ds_sort = 4 * args.sort_every
-        e_d = torch.from_numpy(wl.e_tilde).to(torch.complex128).cuda()
-        b_d = torch.from_numpy(wl.b_tilde).to(torch.complex128).cuda()
+        e_d = torch.from_numpy(wl.e_tilde).to(env_d.dof_dtype).cuda()
+        b_d = torch.from_numpy(wl.b_tilde).to(env_d.dof_dtype).cuda()
         dG_d = torch.zeros(env_d.n_edges, dtype=torch.float64, device="cuda")
 
         def step_ds(n):
@@ -672,24 +674,30 @@ def run_ours(args):
         env_ms = pr["field"]["ms"] + pr["push"]["ms"]
         sort_ms = pr["sort"]["ms"]
         counts_d = (env_d.n_nodes, env_d.n_edges, env_d.n_faces, env_d.n_tets)
-        b_ds = bytes_alg_per_step_downshift(n_p, counts_d)
+        form = "fp64" if prec == 0 else "mixed"
+        b_ds = bytes_alg_per_step_downshift(n_p, counts_d, form)
         t_step = ms_d / args.steps / 1e3
-        out["downshift"] = {
+        rec = {
             "value": n_p * world * args.steps / (ms_d / 1e3), "unit": "particle-steps/s",
             "ms_per_step": ms_d / args.steps,
             "env_step_ms_per_step": env_ms / args.steps,
             "downshift_kernels_ms_per_step": (ms_d - env_ms - sort_ms - pr["finalize"]["ms"]) / args.steps,
             "sort_ms_per_step": sort_ms / args.steps,
-            "sort_every": 4 * args.sort_every,
+            "sort_every": ds_sort,
             "algorithmic_bytes_per_step": b_ds,
             "hbm_frac_of_step": b_ds / t_step / 1e9 / measured_peaks()[0],
-            "what": "fempic_push_step_downshift (FP64): envelope samples + M/L velocity rule + AB4 "
-                    "(k_ds_pre), the env's FP64 step under a zero field for tracking/deposit, wall "
-                    "mirrors of the history (k_ds_post); re-sorted with the history carried along "
-                    "(sort_ms_per_step: the particle sort; the plane gather is in the step time)"}
+            "what": f"fempic_push_step_downshift ({'FP64' if prec == 0 else 'contract mixed form: FP32 rule, samples and history'}): "
+                    "envelope samples + M/L velocity rule + AB4 (k_ds_pre), the env's step under a zero field "
+                    "for tracking/deposit, wall mirrors of the history (k_ds_post); re-sorted with the history "
+                    "carried along (sort_ms_per_step: the particle sort; the plane gather is in the step time)"}
         ds.close()
         env_d.close()
         del st_d, ds, scratch_d
+        return rec
+
+    if not args.no_downshift and args.workload == "cube48":
+        out["downshift"] = downshift_leg(0)
+        out["downshift_mixed"] = downshift_leg(1)
 
     adj = None if (args.no_adjoint or args.workload != "cube48") else adjoint_window(rank)
     if args.workload == "cube48" and not args.no_errors:
@@ -989,6 +997,8 @@ def report(args, world, n_p, out, cpu, adj=None):
         rec["levels3"] = m["levels3"]
     if "downshift" in out:
         rec["downshift"] = out["downshift"]
+    if "downshift_mixed" in out:
+        rec["downshift_mixed"] = out["downshift_mixed"]
     if adj is not None:
         # HBM fractions of the gradient window: forward steps on the forward
         # algorithmic bytes, the reverse sweep on bytes_reverse_window

@@ -1,7 +1,9 @@
 /*
  * fempic_downshift.h -- C ABI of the downshifted particle integrator of
  * Sec. III-D (Ramachandran et al., "An Envelope Tracking Approach for
- * Particle in Cell Simulations"), on the FP64 form of fempic_env.h.
+ * Particle in Cell Simulations"), on the FP64 form of fempic_env.h and on its
+ * FP32-mixed forms (the rule, the samples and the history in FP32, positions
+ * in FP64, the segment tracked and deposited by the env's mixed step).
  *
  * Over one particle step [t_n, t_n + dt] the Lorentz force is integrated with
  * the fast carrier treated analytically: the slowly varying envelope samples
@@ -44,8 +46,9 @@ extern "C" {
 typedef struct fempic_downshift fempic_downshift;   /* opaque: per-tet geometry, edge and face
                                                        ids, and the per-tet envelope coefficients */
 
-/* History planes of a particle set: one device f64 array [FEMPIC_DS_PLANES][n]
- * (plane-major, particle index fastest), owned by the caller:
+/* History planes of a particle set: one device array [FEMPIC_DS_PLANES][n]
+ * (plane-major, particle index fastest), f64 for an FP64-form env and f32
+ * (f32 = 1) for a mixed-form env, owned by the caller:
  *   FEMPIC_DS_VH + 3*i + a     v^{n-1-i} along axis a, i = 0, 1, 2
  *   FEMPIC_DS_F  + 12*l + c    envelope sample of level n-1-l, l = 0, 1:
  *                              c = 0..2 Re E~, 3..5 Im E~, 6..8 Re B~, 9..11 Im B~
@@ -59,7 +62,8 @@ typedef struct fempic_downshift fempic_downshift;   /* opaque: per-tet geometry,
 
 typedef struct {
   int64_t n;                 /* particles (same as the particle set) */
-  double* planes;            /* device f64 [FEMPIC_DS_PLANES][n] */
+  void* planes;              /* device [FEMPIC_DS_PLANES][n], f64 or f32 */
+  int32_t f32;               /* 1: f32 planes (mixed-form env), 0: f64 (FP64-form env) */
 } fempic_downshift_history;
 
 /* Build the gather tables (FP64 barycentric geometry, tet edges and faces)
@@ -77,8 +81,11 @@ int fempic_downshift_create(const fempic_mesh_desc* mesh, fempic_downshift** out
 int fempic_downshift_weights(double t, double dt, double omega0, double* w_out);
 
 /* One downshifted step from t to t + dt of every particle with tet >= 0, on
- * an env created with FEMPIC_FP64 from the mesh of ds: envelope samples at
- * r^n (Whitney sums of envl's complex128 DoFs times envl->amp = a(t), built
+ * an env created from the mesh of ds: with FEMPIC_FP64, f64 velocities and
+ * history and complex128 DoFs; with FEMPIC_MIXED or FEMPIC_MIXED_Q24, f32
+ * velocities and history and complex64 DoFs (the per-tet coefficients are
+ * built in FP64 and rounded once; samples, rule and AB4 in FP32).  Envelope
+ * samples at r^n (Whitney sums of envl's DoFs times envl->amp = a(t), built
  * per tet as the affine form E~ = E0 + d x W, B~ = B0 + beta d), the
  * velocity rule, the AB4 segment tracked and deposited into the env's dG
  * (added to, not cleared), the history shifted.  start = 1 fills the history
@@ -87,10 +94,11 @@ int fempic_downshift_weights(double t, double dt, double omega0, double* w_out);
  * Particles with tet < 0 keep their state.  The per-tet coefficients live in
  * ds, so steps of one ds that overlap on the GPU (different streams) race;
  * give each concurrent particle set its own ds.  Errors: EINVAL (NULL,
- * sizes, species, scalars, an env not in the FP64 form), ECUDA, and any
+ * sizes, species, scalars, a history of the other form), ECUDA, and any
  * error of the env's step.  Every argument is checked on the host before
  * the first launch, so an EINVAL leaves the particles and the history
- * untouched. */
+ * untouched (a history whose f32 flag does not match the env's form is an
+ * EINVAL too). */
 int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds, const fempic_particles* p,
                                const fempic_downshift_history* hist, const fempic_envelope* envl,
                                double omega0, double t, double dt, int32_t start, void* stream);

@@ -80,7 +80,7 @@ class fempic_envelope3(C.Structure):
 
 
 class fempic_downshift_history(C.Structure):
-    _fields_ = [("n", C.c_int64), ("planes", C.c_void_p)]
+    _fields_ = [("n", C.c_int64), ("planes", C.c_void_p), ("f32", C.c_int32)]
 
 
 class FempicError(RuntimeError):

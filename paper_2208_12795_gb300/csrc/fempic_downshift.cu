@@ -1,6 +1,6 @@
-// Downshifted particle integrator of Sec. III-D on the FP64 form: the
-// velocity rule with the carrier integrated analytically (M and L weights)
-// and AB4 positions.  Per step: k_ds_field (per-tet envelope coefficients),
+// Downshifted particle integrator of Sec. III-D on the FP64 form and the
+// FP32-mixed forms: the velocity rule with the carrier integrated
+// analytically (M and L weights) and AB4 positions.  Per step: k_ds_field (per-tet envelope coefficients),
 // k_ds_pre (sample, velocity rule, AB4 velocity, history shift), the env's
 // own FP64 step under a zero field (tracking, walls, deposit of the AB4
 // segment), then k_ds_post (wall mirrors of the velocity history).
@@ -48,19 +48,22 @@ struct DsArgs {
   const double* x;
   const double* y;
   const double* z;
-  double* vx;
-  double* vy;
-  double* vz;
+  void* vx;                     // f64 (FP64 form) or f32 (mixed forms) velocities
+  void* vy;
+  void* vz;
   const int32_t* tet;
-  double* h;                    // history planes [FEMPIC_DS_PLANES][n]
+  void* h;                      // history planes [FEMPIC_DS_PLANES][n], the velocity type
   int64_t nt;
   const double* geom;           // [nt][12]: x0, grad l1, grad l2, grad l3
   const double* coef;           // [nt][20]: per-tet envelope coefficients of this step (k_ds_field)
+  const float* coef32;          // mixed forms: the same in FP32
   int32_t ns;
   int32_t start;
   int64_t begin[kMaxSpecies + 1];
   double qm[kMaxSpecies];
   double w[24];                 // M^r[3], M^i[3], L^r[3][3], L^i[3][3]
+  float qm32[kMaxSpecies];      // mixed forms: the same rounded to FP32
+  float w32[24];
 };
 
 __device__ __forceinline__ int species_of(const DsArgs& A, int64_t p) {
@@ -70,7 +73,8 @@ __device__ __forceinline__ int species_of(const DsArgs& A, int64_t p) {
   return s;
 }
 
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+template <typename R>
+__device__ __forceinline__ void cross3(const R a[3], const R b[3], R o[3]) {
   o[0] = a[1] * b[2] - a[2] * b[1];
   o[1] = a[2] * b[0] - a[0] * b[2];
   o[2] = a[0] * b[1] - a[1] * b[0];
@@ -85,12 +89,13 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 //     B0 = 2 sum over the faces (0, j, k) of b~_f g_j x g_k,
 //     beta = 2 sum_f b~_f det[g_i, g_j, g_k].
 // coef[20 t ..]: Re (E0, W, B0, beta), then Im (E0, W, B0, beta), times a(t).
+template <typename C2>
 __global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double* __restrict__ geom,
                                                        const int32_t* __restrict__ te,
                                                        const int32_t* __restrict__ tf,
-                                                       const double2* __restrict__ e,
-                                                       const double2* __restrict__ b, double amp,
-                                                       double* __restrict__ coef) {
+                                                       const C2* __restrict__ e,
+                                                       const C2* __restrict__ b, double amp,
+                                                       double* __restrict__ coef, float* __restrict__ coef32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const double* G = geom + 12 * t;
@@ -107,7 +112,8 @@ __global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double*
 #pragma unroll
   for (int k = 0; k < 6; k++) {
     const int i = le0(k), j = le1(k);
-    const double2 c = e[te[6 * t + k]];
+    const C2 cc = e[te[6 * t + k]];
+    const double2 c = make_double2((double)cc.x, (double)cc.y);
     double gji[3];
     cross3(g[j], g[i], gji);
 #pragma unroll
@@ -123,7 +129,8 @@ __global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double*
 #pragma unroll
   for (int f = 0; f < 4; f++) {
     const int i = lf(f, 0), j = lf(f, 1), k = lf(f, 2);
-    const double2 c = b[tf[4 * t + f]];
+    const C2 cc = b[tf[4 * t + f]];
+    const double2 c = make_double2((double)cc.x, (double)cc.y);
     double gjk[3];
     cross3(g[j], g[k], gjk);
     const double det = g[i][0] * gjk[0] + g[i][1] * gjk[1] + g[i][2] * gjk[2];
@@ -140,27 +147,44 @@ __global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double*
   double2* out = reinterpret_cast<double2*>(coef + 20 * t);
 #pragma unroll
   for (int c = 0; c < 10; c++) out[c] = make_double2(amp * o[2 * c], amp * o[2 * c + 1]);
+  if (coef32) {
+    float2* o32 = reinterpret_cast<float2*>(coef32 + 20 * t);
+#pragma unroll
+    for (int c = 0; c < 10; c++) o32[c] = make_float2((float)(amp * o[2 * c]), (float)(amp * o[2 * c + 1]));
+  }
 }
 
 // The envelope sample at r in tet T from the per-tet coefficients:
-// out[12] = Re E~, Im E~, Re B~, Im B~.
+// out[12] = Re E~, Im E~, Re B~, Im B~.  The mixed forms take d = r - x0 from
+// one FP64 subtraction, rounded to FP32, and evaluate in FP32.
+template <typename R>
 __device__ __forceinline__ void envelope_at(const DsArgs& A, int32_t T, double rx, double ry, double rz,
-                                            double out[12]) {
+                                            R out[12]) {
   const double* G = A.geom + 12 * (int64_t)T;
-  const double d[3] = {rx - __ldg(G), ry - __ldg(G + 1), rz - __ldg(G + 2)};
-  const double2* C = reinterpret_cast<const double2*>(A.coef + 20 * (int64_t)T);
-  double c[20];
+  const R d[3] = {(R)(rx - __ldg(G)), (R)(ry - __ldg(G + 1)), (R)(rz - __ldg(G + 2))};
+  R c[20];
+  if (sizeof(R) == 8) {
+    const double2* C = reinterpret_cast<const double2*>(A.coef + 20 * (int64_t)T);
 #pragma unroll
-  for (int i = 0; i < 10; i++) {
-    const double2 v = __ldg(C + i);
-    c[2 * i] = v.x;
-    c[2 * i + 1] = v.y;
+    for (int i = 0; i < 10; i++) {
+      const double2 v = __ldg(C + i);
+      c[2 * i] = (R)v.x;
+      c[2 * i + 1] = (R)v.y;
+    }
+  } else {
+    const float2* C = reinterpret_cast<const float2*>(A.coef32 + 20 * (int64_t)T);
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+      const float2 v = __ldg(C + i);
+      c[2 * i] = (R)v.x;
+      c[2 * i + 1] = (R)v.y;
+    }
   }
 #pragma unroll
   for (int part = 0; part < 2; part++) {
-    const double* q = c + 10 * part;
-    double dw[3];
-    cross3(d, q + 3, dw);
+    const R* q = c + 10 * part;
+    R dw[3];
+    cross3<R>(d, q + 3, dw);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
       out[3 * part + a] = q[a] + dw[a];
@@ -172,12 +196,16 @@ __device__ __forceinline__ void envelope_at(const DsArgs& A, int32_t T, double r
 // Before the env's step: the envelope sample at r^n, the velocity rule, the
 // AB4 velocity u (left in v for the env's zero-field step to track), the new
 // velocity and u kept in the scratch planes, and the history shifted.
+template <typename R>
 __global__ void __launch_bounds__(kThreads) k_ds_pre(DsArgs A) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= A.n) return;
   const int64_t n = A.n;
-  double* H = A.h;
-  const double v0[3] = {A.vx[p], A.vy[p], A.vz[p]};
+  R* H = static_cast<R*>(A.h);
+  R* vxp = static_cast<R*>(A.vx);
+  R* vyp = static_cast<R*>(A.vy);
+  R* vzp = static_cast<R*>(A.vz);
+  const R v0[3] = {vxp[p], vyp[p], vzp[p]};
   const int32_t T = A.tet[p];
   if (T < 0 || T >= A.nt) {   // inactive: the state is kept (the env's step flags an out-of-range tet)
 #pragma unroll
@@ -187,9 +215,9 @@ __global__ void __launch_bounds__(kThreads) k_ds_pre(DsArgs A) {
     }
     return;
   }
-  double cur[12];
-  envelope_at(A, T, A.x[p], A.y[p], A.z[p], cur);
-  double vh[3][3], f1[12], f2[12];
+  R cur[12];
+  envelope_at<R>(A, T, A.x[p], A.y[p], A.z[p], cur);
+  R vh[3][3], f1[12], f2[12];
   if (A.start) {
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -208,34 +236,34 @@ __global__ void __launch_bounds__(kThreads) k_ds_pre(DsArgs A) {
       f2[c] = H[(FEMPIC_DS_F + 12 + c) * n + p];
     }
   }
-  const double* S[3] = {cur, f1, f2};
-  const double* V[3] = {v0, vh[0], vh[1]};
-  const double* Mr = A.w;
-  const double* Mi = A.w + 3;
-  const double* Lr = A.w + 6;
-  const double* Li = A.w + 15;
-  double dv[3] = {0.0, 0.0, 0.0};
+  const R* S[3] = {cur, f1, f2};
+  const R* V[3] = {v0, vh[0], vh[1]};
+  // weights from the kernel parameters: M^r at 0, M^i at 3, L^r at 6, L^i at 15
+  auto wt = [&](int i) -> R { return sizeof(R) == 8 ? (R)A.w[i] : (R)A.w32[i]; };
+  R dv[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int k = 0; k < 3; k++)
 #pragma unroll
-    for (int a = 0; a < 3; a++) dv[a] += S[k][a] * Mr[k] + S[k][3 + a] * Mi[k];
+    for (int a = 0; a < 3; a++) dv[a] += S[k][a] * wt(k) + S[k][3 + a] * wt(3 + k);
 #pragma unroll
   for (int j = 0; j < 3; j++) {
-    double C[3] = {0.0, 0.0, 0.0};
+    R C[3] = {R(0), R(0), R(0)};
 #pragma unroll
     for (int k = 0; k < 3; k++)
 #pragma unroll
-      for (int a = 0; a < 3; a++) C[a] += S[k][6 + a] * Lr[3 * j + k] + S[k][9 + a] * Li[3 * j + k];
-    double vc[3];
-    cross3(V[j], C, vc);
+      for (int a = 0; a < 3; a++) C[a] += S[k][6 + a] * wt(6 + 3 * j + k) + S[k][9 + a] * wt(15 + 3 * j + k);
+    R vc[3];
+    cross3<R>(V[j], C, vc);
 #pragma unroll
     for (int a = 0; a < 3; a++) dv[a] += vc[a];
   }
-  const double qm = A.qm[species_of(A, p)];
-  double u[3];
+  const int s = species_of(A, p);
+  const R qm = sizeof(R) == 8 ? (R)A.qm[s] : (R)A.qm32[s];
+  const R ab[4] = {(R)kAB4[0], (R)kAB4[1], (R)kAB4[2], (R)kAB4[3]};
+  R u[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    u[a] = kAB4[0] * v0[a] + kAB4[1] * vh[0][a] + kAB4[2] * vh[1][a] + kAB4[3] * vh[2][a];
+    u[a] = ab[0] * v0[a] + ab[1] * vh[0][a] + ab[2] * vh[1][a] + ab[3] * vh[2][a];
     H[(FEMPIC_DS_VN + a) * n + p] = v0[a] + qm * dv[a];
     H[(FEMPIC_DS_U + a) * n + p] = u[a];
     H[(FEMPIC_DS_VH + 6 + a) * n + p] = vh[1][a];
@@ -247,31 +275,32 @@ __global__ void __launch_bounds__(kThreads) k_ds_pre(DsArgs A) {
     H[(FEMPIC_DS_F + 12 + c) * n + p] = f1[c];
     H[(FEMPIC_DS_F + c) * n + p] = cur[c];
   }
-  A.vx[p] = u[0];
-  A.vy[p] = u[1];
-  A.vz[p] = u[2];
+  vxp[p] = u[0];
+  vyp[p] = u[1];
+  vzp[p] = u[2];
 }
 
 // After the env's step: an axis in which the tracked velocity came back
 // negated was mirrored by a wall (an odd number of times; a zero component
 // cannot reach a wall), so the new velocity and the velocity history are
 // mirrored in it; then v <- v^{n+1}.
+template <typename R>
 __global__ void __launch_bounds__(kThreads) k_ds_post(DsArgs A) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= A.n) return;
   const int64_t n = A.n;
-  double* H = A.h;
-  double* vp[3] = {A.vx, A.vy, A.vz};
+  R* H = static_cast<R*>(A.h);
+  R* vp[3] = {static_cast<R*>(A.vx), static_cast<R*>(A.vy), static_cast<R*>(A.vz)};
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const double va = vp[a][p];
-    const double u = H[(FEMPIC_DS_U + a) * n + p];
-    double vn = H[(FEMPIC_DS_VN + a) * n + p];
-    if (u != 0.0 && va == -u) {
+    const R va = vp[a][p];
+    const R u = H[(FEMPIC_DS_U + a) * n + p];
+    R vn = H[(FEMPIC_DS_VN + a) * n + p];
+    if (u != R(0) && va == -u) {
       vn = -vn;
 #pragma unroll
       for (int i = 0; i < 3; i++) {
-        double& h = H[(FEMPIC_DS_VH + 3 * i + a) * n + p];
+        R& h = H[(FEMPIC_DS_VH + 3 * i + a) * n + p];
         h = -h;
       }
     }
@@ -351,6 +380,7 @@ struct fempic_downshift {
   int32_t* te = nullptr;
   int32_t* tf = nullptr;
   double* coef = nullptr;       // [nt][20]
+  float* coef32 = nullptr;      // mixed forms: [nt][20] in FP32 (allocated on first use)
 };
 
 static void free_ds(fempic_downshift* d) {
@@ -359,14 +389,16 @@ static void free_ds(fempic_downshift* d) {
   cudaFree(d->te);
   cudaFree(d->tf);
   cudaFree(d->coef);
+  cudaFree(d->coef32);
   delete d;
 }
 
 // History planes follow a particle sort: out[k][q] = in[k][perm[q]] for the
 // planes that outlive a step (velocities and envelope samples; the two
 // scratch vectors are rewritten by every step).
+template <typename R>
 __global__ void __launch_bounds__(kThreads) k_ds_permute(int64_t n, const int32_t* __restrict__ perm,
-                                                          const double* __restrict__ in, double* __restrict__ out) {
+                                                          const R* __restrict__ in, R* __restrict__ out) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int64_t src = perm[q];
@@ -383,9 +415,16 @@ extern "C" int fempic_downshift_permute(const fempic_downshift_history* in, cons
   if (in->n == 0) return FEMPIC_OK;
   if (!in->planes || !out->planes || in->planes == out->planes)
     return fail(FEMPIC_EINVAL, "downshift_permute: NULL or overlapping planes");
+  if (in->f32 != out->f32 || (in->f32 != 0 && in->f32 != 1))
+    return fail(FEMPIC_EINVAL, "downshift_permute: plane types differ");
   if (in->n >= (int64_t(1) << 31)) return fail(FEMPIC_EINVAL, "downshift_permute: more than 2^31 particles");
   const unsigned blocks = (unsigned)((in->n + kThreads - 1) / kThreads);
-  k_ds_permute<<<blocks, kThreads, 0, (cudaStream_t)stream>>>(in->n, perm, in->planes, out->planes);
+  if (in->f32)
+    k_ds_permute<float><<<blocks, kThreads, 0, (cudaStream_t)stream>>>(
+        in->n, perm, static_cast<const float*>(in->planes), static_cast<float*>(out->planes));
+  else
+    k_ds_permute<double><<<blocks, kThreads, 0, (cudaStream_t)stream>>>(
+        in->n, perm, static_cast<const double*>(in->planes), static_cast<double*>(out->planes));
   DS_CUDA(cudaGetLastError());
   return FEMPIC_OK;
 }
@@ -442,9 +481,10 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
       !std::isfinite(envl->amp))
     return fail(FEMPIC_EINVAL, "push_step_downshift: non-finite scalar or dt <= 0");
   if (start != 0 && start != 1) return fail(FEMPIC_EINVAL, "push_step_downshift: start must be 0 or 1");
-  if (fempic::env_precision(env) != FEMPIC_FP64)
-    return fail(FEMPIC_EINVAL, "push_step_downshift: the env must use the FP64 form (f64 velocities, "
-                               "complex128 DoFs)");
+  const bool mixed = fempic::env_precision(env) != FEMPIC_FP64;
+  if (hist->f32 != (mixed ? 1 : 0))
+    return fail(FEMPIC_EINVAL, "push_step_downshift: history planes must be f64 for an FP64-form env and f32 "
+                               "for a mixed-form env (fempic_downshift_history.f32)");
   // the env step it runs checks its arguments only after this step has
   // launched its own kernels: run those checks first, so that an error
   // leaves the particles and the history untouched
@@ -468,6 +508,7 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
     if (s > 0 && A.begin[s] < A.begin[s - 1]) return fail(FEMPIC_EINVAL, "push_step_downshift: species ranges decrease");
     if (!(p->m[s] > 0.0) || !std::isfinite(p->q[s])) return fail(FEMPIC_EINVAL, "push_step_downshift: q, m");
     A.qm[s] = p->q[s] / p->m[s];
+    A.qm32[s] = (float)A.qm[s];
   }
   if (A.begin[p->n_species] < A.begin[p->n_species - 1])
     return fail(FEMPIC_EINVAL, "push_step_downshift: species ranges decrease");
@@ -475,9 +516,9 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
   A.x = p->x;
   A.y = p->y;
   A.z = p->z;
-  A.vx = static_cast<double*>(p->vx);
-  A.vy = static_cast<double*>(p->vy);
-  A.vz = static_cast<double*>(p->vz);
+  A.vx = p->vx;
+  A.vy = p->vy;
+  A.vz = p->vz;
   A.tet = p->tet;
   A.h = hist->planes;
   A.nt = ds->nt;
@@ -485,13 +526,29 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
   A.coef = ds->coef;
   A.start = start;
   compute_weights(t, dt, omega0, A.w);
+  for (int i = 0; i < 24; i++) A.w32[i] = (float)A.w[i];
+  if (mixed && !ds->coef32) {
+    if (cudaMalloc(&ds->coef32, sizeof(float) * 20 * (size_t)ds->nt) != cudaSuccess) {
+      cudaGetLastError();
+      ds->coef32 = nullptr;
+      return fail(FEMPIC_ENOMEM, "push_step_downshift: device allocation");
+    }
+  }
+  A.coef32 = ds->coef32;
   cudaStream_t st = (cudaStream_t)stream;
-  k_ds_field<<<blocks_for(ds->nt), kThreads, 0, st>>>(ds->nt, ds->geom, ds->te, ds->tf,
-                                                        static_cast<const double2*>(envl->e_tilde),
-                                                        static_cast<const double2*>(envl->b_tilde), envl->amp,
-                                                        ds->coef);
-  DS_CUDA(cudaGetLastError());
-  k_ds_pre<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  if (mixed) {   // complex64 DoFs; FP32 velocities, samples and history
+    k_ds_field<float2><<<blocks_for(ds->nt), kThreads, 0, st>>>(
+        ds->nt, ds->geom, ds->te, ds->tf, static_cast<const float2*>(envl->e_tilde),
+        static_cast<const float2*>(envl->b_tilde), envl->amp, ds->coef, ds->coef32);
+    DS_CUDA(cudaGetLastError());
+    k_ds_pre<float><<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  } else {
+    k_ds_field<double2><<<blocks_for(ds->nt), kThreads, 0, st>>>(
+        ds->nt, ds->geom, ds->te, ds->tf, static_cast<const double2*>(envl->e_tilde),
+        static_cast<const double2*>(envl->b_tilde), envl->amp, ds->coef, nullptr);
+    DS_CUDA(cudaGetLastError());
+    k_ds_pre<double><<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  }
   DS_CUDA(cudaGetLastError());
   // the AB4 segment: the env's own step under a zero field tracks, reflects
   // or absorbs and deposits r^n -> r^n + dt u
@@ -499,7 +556,10 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
   zero.amp = 0.0;
   const int rc = fempic_push_step(env, p, &zero, omega0, t, dt, stream);
   if (rc != FEMPIC_OK) return fail(rc, std::string("push_step_downshift: env step: ") + fempic_last_error());
-  k_ds_post<<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  if (mixed)
+    k_ds_post<float><<<blocks_for(p->n), kThreads, 0, st>>>(A);
+  else
+    k_ds_post<double><<<blocks_for(p->n), kThreads, 0, st>>>(A);
   DS_CUDA(cudaGetLastError());
   return FEMPIC_OK;
 }

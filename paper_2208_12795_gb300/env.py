@@ -257,7 +257,8 @@ class FempicEnv:
 
 
 class Downshift:
-    """The downshifted integrator of Sec. III-D on an FP64-form env.
+    """The downshifted integrator of Sec. III-D on an env of any form (the
+    mixed forms keep velocities, envelope samples and history in FP32).
 
     Velocity rule with the carrier integrated analytically over each step (M
     and L weights on the newest three envelope samples) and fourth-order
@@ -269,11 +270,11 @@ class Downshift:
     through the same permutation (fempic_sort_perm, fempic_downshift_permute)."""
 
     def __init__(self, env: FempicEnv, n: int, device="cuda"):
-        if env.precision != FEMPIC_FP64:
-            raise capi.FempicError("the downshifted integrator runs on the FP64 form")
         self.env = env
+        self.f32 = env.precision != FEMPIC_FP64   # mixed forms: f32 velocities, samples and history
         self.h = capi.fempic_downshift_create(_mesh_desc(*env._mesh))
-        self.planes = torch.zeros((capi.FEMPIC_DS_PLANES, n), dtype=torch.float64, device=device)
+        dt = torch.float32 if self.f32 else torch.float64
+        self.planes = torch.zeros((capi.FEMPIC_DS_PLANES, n), dtype=dt, device=device)
         self.started = False
 
     def close(self):
@@ -297,8 +298,8 @@ class Downshift:
         spare = getattr(self, "_spare", None)
         if spare is None or spare.shape != self.planes.shape:
             spare = torch.empty_like(self.planes)
-        hin = capi.fempic_downshift_history(st.n, _ptr(self.planes))
-        hout = capi.fempic_downshift_history(st.n, _ptr(spare))
+        hin = capi.fempic_downshift_history(st.n, _ptr(self.planes), int(self.f32))
+        hout = capi.fempic_downshift_history(st.n, _ptr(spare), int(self.f32))
         capi.fempic_downshift_permute(hin, hout, _ptr(perm), _stream(stream))
         self.planes, self._spare = spare, self.planes
         return perm
@@ -307,13 +308,14 @@ class Downshift:
              t: float, dt: float, stream=None):
         """One step from t to t + dt; amp = a(t).  The first call fills the history."""
         env = self.env
-        if e_dof.dtype != torch.complex128 or b_dof.dtype != torch.complex128:
-            raise capi.FempicError("DoFs must be complex128 on the FP64 form")
+        cdt, vdt = (torch.complex64, torch.float32) if self.f32 else (torch.complex128, torch.float64)
+        if e_dof.dtype != cdt or b_dof.dtype != cdt:
+            raise capi.FempicError(f"DoFs must be {cdt} on this env's form")
         if e_dof.numel() != env.n_edges or b_dof.numel() != env.n_faces or not e_dof.is_cuda or not b_dof.is_cuda:
             raise capi.FempicError("DoF arrays must be device tensors of length n_edges / n_faces")
-        if st.vx.dtype != torch.float64 or st.n != self.planes.shape[1]:
-            raise capi.FempicError("velocities must be float64 and the history sized for this particle set")
-        hist = capi.fempic_downshift_history(st.n, _ptr(self.planes))
+        if st.vx.dtype != vdt or st.n != self.planes.shape[1]:
+            raise capi.FempicError(f"velocities must be {vdt} and the history sized for this particle set")
+        hist = capi.fempic_downshift_history(st.n, _ptr(self.planes), int(self.f32))
         envl = capi.fempic_envelope(_ptr(e_dof), _ptr(b_dof), float(amp))
         capi.fempic_push_step_downshift(env.h, self.h, st.cstruct(), hist, envl, omega0, t, dt,
                                         not self.started, _stream(stream))
