@@ -196,8 +196,13 @@ __device__ __forceinline__ void envelope_at(const DsArgs& A, int32_t T, double r
 // Before the env's step: the envelope sample at r^n, the velocity rule, the
 // AB4 velocity u (left in v for the env's zero-field step to track), the new
 // velocity and u kept in the scratch planes, and the history shifted.
+// The FP32 instance streams the history planes and is bound by HBM latency:
+// it is held to 80 registers so that 3 blocks of 256 stay resident per SM
+// (128 registers left 2, and the step 4% slower).  The FP64 instance is bound
+// by the FP64 pipe and keeps the compiler's allocation (a minimum of 0 leaves
+// it unconstrained; 1 let it grow to 204 registers and one block per SM).
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_ds_pre(DsArgs A) {
+__global__ void __launch_bounds__(kThreads, sizeof(R) == 4 ? 3 : 0) k_ds_pre(DsArgs A) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= A.n) return;
   const int64_t n = A.n;
