@@ -117,6 +117,20 @@ int fempic_downshift_permute(const fempic_downshift_history* in, const fempic_do
 const char* fempic_downshift_last_error(void);
 void fempic_downshift_destroy(fempic_downshift* ds);
 
+/* Debug build support (no counterpart in the paper).  In the debug build
+ * (libfempic_env_debug.so, FEMPIC_BOUNDS_CHECK) the per-tet field pass of
+ * fempic_push_step_downshift checks every edge and face id it reads from this
+ * handle's tables before it addresses e_tilde / b_tilde; an out-of-range id
+ * is skipped (that DoF reads as zero) and counted in the env's bounds
+ * counter, so the next fempic_error_count on that env returns
+ * FEMPIC_EBOUNDS.  This call overwrites one entry of this handle's device
+ * tables so that the checks can be exercised:
+ *   FEMPIC_TABLE_EDGE  index = 6 tet + local edge (edge ids, [nt][6]);
+ *   FEMPIC_TABLE_FACE  index = 4 tet + local face (face ids, [nt][4]).
+ * The release build refuses it (FEMPIC_EINVAL), so a corrupted table never
+ * meets unchecked loads.  Synchronous.  Errors: EINVAL, ECUDA. */
+int fempic_downshift_debug_set_table(fempic_downshift* ds, int32_t table, int64_t index, int32_t value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -260,7 +260,8 @@ int fempic_stats(fempic_env* env, int64_t* out4, void* stream);
  * bulk copy: the particles of its remaining tiles were then not advanced and
  * their deposit is missing, so the step must be redone from a saved state.
  * In the debug build it returns FEMPIC_EBOUNDS when a mesh-table index out of
- * range was skipped (fempic_debug_set_table).  fempic_stats keeps the
+ * range was skipped (fempic_debug_set_table; the downshifted step's own
+ * tables, fempic_downshift_debug_set_table, count here too).  fempic_stats keeps the
  * cumulative counters.  Errors: EINVAL, ECUDA, EINCOMPLETE, EBOUNDS. */
 int fempic_error_count(fempic_env* env, int64_t* n_bad, void* stream);
 
@@ -284,10 +285,13 @@ int fempic_debug_stall(fempic_env* env, int32_t cta, int64_t limit_ns);
  *   FEMPIC_TABLE_NEIGHBOUR  index = 4 tet + local face (the neighbour table
  *                           and its copy in the tet record);
  *   FEMPIC_TABLE_EDGE       index = 6 tet + local edge (the edge-id table).
+ * FEMPIC_TABLE_FACE (index = 4 tet + local face, the face-id table) is
+ * accepted by fempic_downshift_debug_set_table only.
  * The release build refuses it (FEMPIC_EINVAL), so a corrupted table never
  * meets unchecked loads.  Synchronous.  Errors: EINVAL, ECUDA. */
 #define FEMPIC_TABLE_NEIGHBOUR 0
 #define FEMPIC_TABLE_EDGE 1
+#define FEMPIC_TABLE_FACE 2
 int fempic_debug_set_table(fempic_env* env, int32_t table, int64_t index, int32_t value);
 
 /* Deposited-current term of the loss for the adjoint steps (the paper has no

@@ -24,6 +24,7 @@ FEMPIC_EINCOMPLETE = -5
 FEMPIC_EBOUNDS = -6
 FEMPIC_TABLE_NEIGHBOUR = 0
 FEMPIC_TABLE_EDGE = 1
+FEMPIC_TABLE_FACE = 2
 FEMPIC_FP64 = 0
 FEMPIC_MIXED = 1
 FEMPIC_MIXED_Q24 = 2
@@ -40,7 +41,8 @@ EXPORTS = ("fempic_env_create", "fempic_env_query", "fempic_locate", "fempic_pus
            "fempic_measure_fp64_rate", "fempic_last_error", "fempic_env_destroy")
 # Every function declared in include/fempic_downshift.h.
 DS_EXPORTS = ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift",
-              "fempic_downshift_permute", "fempic_downshift_last_error", "fempic_downshift_destroy")
+              "fempic_downshift_permute", "fempic_downshift_last_error", "fempic_downshift_destroy",
+              "fempic_downshift_debug_set_table")
 FEMPIC_DS_VH, FEMPIC_DS_F, FEMPIC_DS_VN, FEMPIC_DS_U, FEMPIC_DS_PLANES = 0, 9, 33, 36, 39
 FEMPIC_K_LOCATE, FEMPIC_K_FIELD, FEMPIC_K_PUSH, FEMPIC_K_FINALIZE, FEMPIC_K_CHARGE, FEMPIC_K_SORT, FEMPIC_K_CROSS, \
     FEMPIC_K_ADJOINT = range(8)
@@ -147,8 +149,9 @@ def load(path: str = LIB_PATH):
         lib.fempic_downshift_last_error.argtypes = []
         lib.fempic_downshift_destroy.argtypes = [C.c_void_p]
         lib.fempic_downshift_destroy.restype = None
+        lib.fempic_downshift_debug_set_table.argtypes = [C.c_void_p, C.c_int32, C.c_int64, C.c_int32]
         for name in ("fempic_downshift_create", "fempic_downshift_weights", "fempic_push_step_downshift",
-                     "fempic_downshift_permute"):
+                     "fempic_downshift_permute", "fempic_downshift_debug_set_table"):
             getattr(lib, name).restype = C.c_int
         lib.fempic_last_error.restype = C.c_char_p
         lib.fempic_last_error.argtypes = []
@@ -353,3 +356,12 @@ def fempic_downshift_last_error() -> str:
 
 def fempic_downshift_destroy(ds):
     load().fempic_downshift_destroy(ds)
+
+
+def fempic_downshift_debug_set_table(ds, table: int, index: int, value: int) -> int:
+    """Return code of fempic_downshift_debug_set_table (FEMPIC_EINVAL from the
+    release build); other failures raise."""
+    rc = load().fempic_downshift_debug_set_table(ds, int(table), int(index), int(value))
+    if rc not in (FEMPIC_OK, FEMPIC_EINVAL):
+        check_ds(rc, "fempic_downshift_debug_set_table")
+    return rc

@@ -43,6 +43,22 @@ __host__ __device__ constexpr int le0(int e) { return e < 3 ? 0 : (e < 5 ? 1 : 2
 __host__ __device__ constexpr int le1(int e) { return e < 3 ? e + 1 : (e == 3 ? 2 : 3); }
 __host__ __device__ constexpr int lf(int f, int i) { return i < f ? i : i + 1; }
 
+// Debug build (FEMPIC_BOUNDS_CHECK): an edge or face id read from this unit's
+// tables is checked against its range before it addresses a DoF array; an
+// out-of-range id is counted in the env's bounds counter (reported by
+// fempic_error_count) and its DoF reads as zero.
+#ifdef FEMPIC_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+__device__ __forceinline__ bool ds_idx_in(int64_t i, int64_t n, unsigned long long* stats) {
+  if (!kBoundsCheck) return true;
+  if (i >= 0 && i < n) return true;
+  if (stats) atomicAdd(stats + 3, 1ull);
+  return false;
+}
+
 struct DsArgs {
   int64_t n;
   const double* x;
@@ -94,7 +110,8 @@ __global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double*
                                                        const int32_t* __restrict__ te,
                                                        const int32_t* __restrict__ tf,
                                                        const C2* __restrict__ e,
-                                                       const C2* __restrict__ b, double amp,
+                                                       const C2* __restrict__ b, int64_t ne, int64_t nf,
+                                                       unsigned long long* stats, double amp,
                                                        double* __restrict__ coef, float* __restrict__ coef32) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nt) return;
@@ -112,8 +129,12 @@ __global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double*
 #pragma unroll
   for (int k = 0; k < 6; k++) {
     const int i = le0(k), j = le1(k);
-    const C2 cc = e[te[6 * t + k]];
-    const double2 c = make_double2((double)cc.x, (double)cc.y);
+    const int32_t id = te[6 * t + k];
+    double2 c = make_double2(0.0, 0.0);
+    if (ds_idx_in(id, ne, stats)) {
+      const C2 cc = e[id];
+      c = make_double2((double)cc.x, (double)cc.y);
+    }
     double gji[3];
     cross3(g[j], g[i], gji);
 #pragma unroll
@@ -129,8 +150,12 @@ __global__ void __launch_bounds__(kThreads) k_ds_field(int64_t nt, const double*
 #pragma unroll
   for (int f = 0; f < 4; f++) {
     const int i = lf(f, 0), j = lf(f, 1), k = lf(f, 2);
-    const C2 cc = b[tf[4 * t + f]];
-    const double2 c = make_double2((double)cc.x, (double)cc.y);
+    const int32_t id = tf[4 * t + f];
+    double2 c = make_double2(0.0, 0.0);
+    if (ds_idx_in(id, nf, stats)) {
+      const C2 cc = b[id];
+      c = make_double2((double)cc.x, (double)cc.y);
+    }
     double gjk[3];
     cross3(g[j], g[k], gjk);
     const double det = g[i][0] * gjk[0] + g[i][1] * gjk[1] + g[i][2] * gjk[2];
@@ -436,6 +461,25 @@ extern "C" int fempic_downshift_permute(const fempic_downshift_history* in, cons
 
 extern "C" void fempic_downshift_destroy(fempic_downshift* ds) { free_ds(ds); }
 
+extern "C" int fempic_downshift_debug_set_table(fempic_downshift* ds, int32_t table, int64_t index,
+                                                int32_t value) {
+  if (!ds) return fail(FEMPIC_EINVAL, "downshift_debug_set_table: NULL handle");
+  if (!kBoundsCheck)
+    return fail(FEMPIC_EINVAL, "downshift_debug_set_table: only the debug build (FEMPIC_BOUNDS_CHECK) accepts it");
+  int32_t* dst = nullptr;
+  if (table == FEMPIC_TABLE_EDGE) {
+    if (index < 0 || index >= 6 * ds->nt) return fail(FEMPIC_EINVAL, "downshift_debug_set_table: edge index out of range");
+    dst = ds->te + index;
+  } else if (table == FEMPIC_TABLE_FACE) {
+    if (index < 0 || index >= 4 * ds->nt) return fail(FEMPIC_EINVAL, "downshift_debug_set_table: face index out of range");
+    dst = ds->tf + index;
+  } else {
+    return fail(FEMPIC_EINVAL, "downshift_debug_set_table: unknown table");
+  }
+  DS_CUDA(cudaMemcpy(dst, &value, sizeof(int32_t), cudaMemcpyHostToDevice));
+  return FEMPIC_OK;
+}
+
 extern "C" int fempic_downshift_create(const fempic_mesh_desc* mesh, fempic_downshift** out) {
   if (!mesh || !out) return fail(FEMPIC_EINVAL, "downshift_create: NULL argument");
   *out = nullptr;
@@ -544,13 +588,15 @@ extern "C" int fempic_push_step_downshift(fempic_env* env, fempic_downshift* ds,
   if (mixed) {   // complex64 DoFs; FP32 velocities, samples and history
     k_ds_field<float2><<<blocks_for(ds->nt), kThreads, 0, st>>>(
         ds->nt, ds->geom, ds->te, ds->tf, static_cast<const float2*>(envl->e_tilde),
-        static_cast<const float2*>(envl->b_tilde), envl->amp, ds->coef, ds->coef32);
+        static_cast<const float2*>(envl->b_tilde), ds->ne, ds->nf, fempic::env_stats(env), envl->amp, ds->coef,
+        ds->coef32);
     DS_CUDA(cudaGetLastError());
     k_ds_pre<float><<<blocks_for(p->n), kThreads, 0, st>>>(A);
   } else {
     k_ds_field<double2><<<blocks_for(ds->nt), kThreads, 0, st>>>(
         ds->nt, ds->geom, ds->te, ds->tf, static_cast<const double2*>(envl->e_tilde),
-        static_cast<const double2*>(envl->b_tilde), envl->amp, ds->coef, nullptr);
+        static_cast<const double2*>(envl->b_tilde), ds->ne, ds->nf, fempic::env_stats(env), envl->amp, ds->coef,
+        nullptr);
     DS_CUDA(cudaGetLastError());
     k_ds_pre<double><<<blocks_for(p->n), kThreads, 0, st>>>(A);
   }

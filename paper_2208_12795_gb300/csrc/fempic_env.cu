@@ -3652,6 +3652,8 @@ extern "C" int fempic_push_step3(fempic_env* env, const fempic_particles* p, con
 namespace fempic {
 int env_precision(const fempic_env* env) { return env->opt.precision; }
 
+unsigned long long* env_stats(fempic_env* env) { return env->stats; }
+
 int validate_push_step(const fempic_particles* p, const fempic_envelope* envl, double omega0, double t,
                        double dt) {
   if (!envl) return fail(FEMPIC_EINVAL, "push_step: NULL envelope");

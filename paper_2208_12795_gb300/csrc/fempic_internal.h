@@ -49,6 +49,12 @@ inline int grid_cell(double x, double lo, double ginv, int gd) {
 // Precision form of an env (FEMPIC_FP64 or FEMPIC_MIXED).
 int env_precision(const fempic_env* env);
 
+// The env's device status counters (fempic_stats order).  In the debug
+// build (FEMPIC_BOUNDS_CHECK) slot 3 counts mesh-table indices found out of
+// range and skipped; kernels of other translation units that read mesh
+// tables count there too, so that fempic_error_count reports them.
+unsigned long long* env_stats(fempic_env* env);
+
 // Every host-side argument check of fempic_push_step, without device work:
 // FEMPIC_OK or the code and message fempic_push_step would return.
 int validate_push_step(const fempic_particles* p, const fempic_envelope* envl, double omega0, double t,

@@ -64,6 +64,7 @@ def test_downshift_null_arguments_rejected_on_host(lib):
     w = (C.c_double * 24)()
     assert lib.fempic_downshift_weights(0.0, -1.0, 1.0, w) == capi.FEMPIC_EINVAL
     assert lib.fempic_downshift_weights(float("nan"), 1.0, 1.0, w) == capi.FEMPIC_EINVAL
+    assert lib.fempic_downshift_debug_set_table(None, capi.FEMPIC_TABLE_EDGE, 0, 0) == capi.FEMPIC_EINVAL
     lib.fempic_downshift_destroy(None)   # safe on NULL
 
 
