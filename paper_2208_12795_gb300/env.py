@@ -264,7 +264,8 @@ class Downshift:
     and L weights on the newest three envelope samples) and fourth-order
     Adams-Bashforth positions; the segment is tracked and deposited by the
     env's own step.  Holds the per-tet gather tables and the particles'
-    history planes ([FEMPIC_DS_PLANES, n] f64 on the device).  Velocities are
+    history planes ([FEMPIC_DS_PLANES, n] on the device: f64 on an FP64 env,
+    f32 on a mixed one).  Velocities are
     at integer levels (v^n), not half steps.  The history follows the
     particle order: re-sort the set with `sort`, which carries the history
     through the same permutation (fempic_sort_perm, fempic_downshift_permute)."""
