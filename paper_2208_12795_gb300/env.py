@@ -265,10 +265,10 @@ class Downshift:
     Adams-Bashforth positions; the segment is tracked and deposited by the
     env's own step.  Holds the per-tet gather tables and the particles'
     history planes ([FEMPIC_DS_PLANES, n] on the device: f64 on an FP64 env,
-    f32 on a mixed one).  Velocities are
-    at integer levels (v^n), not half steps.  The history follows the
-    particle order: re-sort the set with `sort`, which carries the history
-    through the same permutation (fempic_sort_perm, fempic_downshift_permute)."""
+    f32 on a mixed one).  Velocities are at integer levels (v^n), not half
+    steps.  The history follows the particle order: re-sort the set with
+    `sort`, which carries the history through the same permutation
+    (fempic_sort_perm, fempic_downshift_permute)."""
 
     def __init__(self, env: FempicEnv, n: int, device="cuda"):
         self.env = env
