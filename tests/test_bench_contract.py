@@ -80,6 +80,11 @@ def test_downshift_algorithmic_bytes():
     # FP64 state (52 B) plus the history the rule needs: 3 past velocities
     # (72 B) and 2 past complex E~, B~ samples (192 B), each read and written
     assert b == 10_000_000 * 2 * (52 + 3 * 24 + 2 * 12 * 8) + 72 * nt + 24 * nn + 24 * ne + 16 * nf
+    # mixed forms: FP32 velocities (state 40 B), the same history in FP32
+    # (132 B), complex64 DoFs
+    bm = bench.bytes_alg_per_step_downshift(10_000_000, counts, "mixed")
+    assert bm == 10_000_000 * 2 * (40 + 3 * 12 + 2 * 12 * 4) + 72 * nt + 24 * nn + 16 * ne + 8 * nf
+    assert bm / 10_000_000 == pytest.approx(351.4, abs=0.05)
 
 
 def test_algorithmic_bytes_per_step_match_the_stated_formula():
